@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Throughput of the Stokes-preconditioned Newton hot path on one GB300.
+
+Metric: Jacobian-vector products per second of the BEFE step + tangent at
+48 x 65 x 48 (plane Couette, Re = 400, dt = 100, box 2pi/1.14 x 2 x 2pi/2.5).
+One timed step = one pass of the hot path over one batch: set the
+linearisation point (one full FP64 BEFE step plus the total fields on the
+grid) and apply the tangent step to 256 seeded unit directions (batched).
+Inputs are larger than L2 (256 directions x 1.55 MB), so no flush is needed.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the comparison arm; it is deliberately slow).
+Under torchrun every rank runs its own 256 directions (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY, NZ = 48, 65, 48
+RE, DT = 400.0, 100.0
+LX, LZ = 2 * math.pi / 1.14, 2 * math.pi / 2.5
+BASE_SEED, DIR_SEED0 = 1001, 2000
+METRIC = "JVPs/s (BEFE step+tangent) at 48x65x48"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--ndir", type=int, default=256)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ----------------------------------------------------------------- workload sizes
+def dims():
+    kx, kz = (NX - 1) // 3, (NZ - 1) // 3
+    mx, mz = 2 * kx + 1, kz + 1
+    return kx, kz, mx, mz, NY
+
+
+def n_unique():
+    kx, kz, mx, mz, ny = dims()
+    return (kx + 1) * mz + kx * (mz - 1)
+
+
+def kernel_bytes(stage, n_dir, esz):
+    """Algorithmic HBM bytes of one launch (each datum read or written once)."""
+    kx, kz, mx, mz, ny = dims()
+    mm = mx * mz
+    state = 3 * mm * ny * 16
+    if stage == "k_yinv":
+        return n_dir * (state + 6 * ny * mm * esz)
+    if stage == "k_xz":
+        return n_dir * 9 * ny * mm * esz + 6 * ny * NX * NZ * esz // 2
+    if stage == "k_solve":
+        n = ny - 1
+        op = (n // 2 + 1) * (n - 1) + (n // 2) * (n - 1) + (n // 2 + 1) * (n // 2) + (n // 2) * (n // 2 - 1)
+        return n_dir * (3 * ny * mm * esz + 2 * state) + n_unique() * op * 8
+    return 0
+
+
+def kernel_flops(stage, n_dir):
+    """Algorithmic floating-point operations of one launch (FFT: 5 n log2 n)."""
+    kx, kz, mx, mz, ny = dims()
+    mm = mx * mz
+    nh = (ny - 1) // 2 + 1
+    if stage == "k_yinv":
+        return n_dir * mm * 5 * nh * ny * 4
+    if stage == "k_xz":
+        fx = 5 * NX * math.log2(NX)
+        fz = 5 * NZ * math.log2(NZ)
+        per_plane = (6 + 3) * mz * fx + (6 + 3) * (NX // 2) * fz + NX * NZ * 30
+        return n_dir * ny * per_plane
+    if stage == "k_solve":
+        n = ny - 1
+        op = (n // 2 + 1) * (n - 1) + (n // 2) * (n - 1) + (n // 2 + 1) * (n // 2) + (n // 2) * (n // 2 - 1)
+        return n_dir * n_unique() * (3 * (n - 1) * nh * 4 + op * 4 + ny * nh * 4)
+    return 0
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- oracle arm
+def oracle_jvps(budget_s, max_jvps=None):
+    """Time the FP64 oracle's tangent step on host cores: (JVPs/s, count, seconds)."""
+    import seeded_inputs as si
+    from oracle.couette import Couette
+    g = Couette(NX, NY, NZ, lx=LX, lz=LZ, re=RE, dt=DT)
+    u = g.seed_state(*si.couette_random_coeffs(BASE_SEED, NX, NY, NZ), 0.1)
+    base = g.base(u)
+    d0 = g.seed_state(*si.couette_random_coeffs(DIR_SEED0, NX, NY, NZ), 1.0)
+    g.jvp(base, d0)  # factor the per-mode systems once (setup, untimed)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        d = g.seed_state(*si.couette_random_coeffs(DIR_SEED0 + n, NX, NY, NZ), 1.0)
+        g.jvp(base, d)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_jvps and n >= max_jvps):
+            return n / el, n, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count()
+    per_step = 2
+    times = []
+    for i in range(args.warmup + args.steps):
+        rate, n, el = oracle_jvps(0.0, max_jvps=per_step)
+        if i >= args.warmup:
+            times.append(el)
+    tot = sum(times)
+    value = per_step * args.steps / tot
+    out = {"metric": METRIC, "value": value, "unit": "JVP/s", "impl": "reference", "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "plane Couette 48x65x48 Re=400 dt=100, FP64 oracle tangent", "ndir_per_step": per_step},
+           "cpu_baseline": {"value": value, "unit": "JVP/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{per_step} tangent steps per timed step at 48x65x48 (one base state)"},
+           "e2e": {"value": value, "unit": "JVP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ----------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_1804_05087_gb300 as sp
+    import seeded_inputs as si
+
+    prec = sp.SP_MIXED if args.prec == "mixed" else sp.SP_FP64
+    esz = 8 if args.prec == "mixed" else 16
+    nd = args.ndir
+    ctx = sp.Context(sp.Config(NX, NY, NZ, lx=LX, lz=LZ, re=RE, dt=DT, prec=prec, max_batch=nd))
+    # seeded inputs, built on the device by the library
+    def seeded(seed, amp):
+        a, b, c = si.couette_random_coeffs(seed, NX, NY, NZ)
+        U = ctx.zeros()
+        tr = [torch.from_numpy(x).cuda() for x in (a, b, c)]
+        return ctx.sp_seed_state(*tr, amp, U)
+    U = seeded(BASE_SEED, 0.1)
+    D = ctx.zeros(nd)
+    for i in range(nd):
+        D[i].copy_(seeded(DIR_SEED0 + rank * nd + i, 1.0))
+    OUT = ctx.zeros(nd)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.sp_set_base(U)
+        ctx.sp_jvp(D, OUT)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    ctx.sp_trace_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    trace = ctx.sp_trace_read()
+    ctx.sp_trace_enable(False)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nd * args.steps / (ms * 1e-3)
+    launches = int(sum(v[1] for v in trace.values()))
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        hD = D.cpu().pin_memory()
+        hU = U.cpu().pin_memory()
+        hO = torch.empty_like(hD).pin_memory()
+        dD, dU = torch.empty_like(D), torch.empty_like(U)
+
+        def step_e2e():
+            dU.copy_(hU, non_blocking=True)
+            dD.copy_(hD, non_blocking=True)
+            ctx.sp_set_base(dU)
+            ctx.sp_jvp(dD, OUT)
+            hO.copy_(OUT, non_blocking=True)
+        for _ in range(3):
+            step_e2e()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_e2e()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms_e], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms_e = float(t.item())
+        e2e = {"value": world * nd * args.steps / (ms_e * 1e-3), "unit": "JVP/s",
+               "h2d_bytes_per_step": hD.numel() * 16 + hU.numel() * 16, "d2h_bytes_per_step": hO.numel() * 16}
+
+    # roofline of the dominant kernel (live CUDA-event durations)
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        peaks = json.load(f)
+    dom = max(("k_yinv", "k_xz", "k_solve"), key=lambda k: trace[k][0])
+    dom_ms, dom_n = trace[dom]
+    avg_s = dom_ms / dom_n * 1e-3
+    ndir_launch = nd  # every tangent launch processes the whole batch
+    # the set_base launches (one state) are also in the family: count their share
+    bytes_l = kernel_bytes(dom, ndir_launch, esz)
+    flops_l = kernel_flops(dom, ndir_launch)
+    gbs = bytes_l / avg_s / 1e9
+    tfs = flops_l / avg_s / 1e12
+    hbm = peaks["hbm_gbs"]
+    fp64_peak = 1.25  # TFLOP/s, nominal FP64 (no FP64 entry in MEASURED_PEAKS.json)
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+    alu_peak = fp64_peak if (args.prec == "fp64" or dom == "k_solve") else fp32_peak
+    if gbs / hbm >= tfs / alu_peak:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        roof = {"bound": "alu", "achieved": tfs, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfs / alu_peak,
+                "peak_source": "nominal FP64 1.25 TFLOP/s" if alu_peak == fp64_peak
+                else "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+    roof.update({"kernel": dom, "traffic": None, "avg_launch_ms": dom_ms / dom_n,
+                 "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
+                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in trace.items()}})
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n, el = oracle_jvps(12.0)
+        cpu = {"value": rate, "unit": "JVP/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n} FP64 oracle tangent steps at 48x65x48 in {el:.1f} s (after its one-time LU setup)"}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "JVP/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32+f64" if args.prec == "mixed" else "f64", "data": "synthetic",
+               "config": {"workload": "plane Couette 48x65x48, Re=400, dt=100, box 2pi/1.14 x 2 x 2pi/2.5; "
+                                      "per step: set_base + tangent on 256 seeded unit directions",
+                          "grid": [NX, NY, NZ], "ndir_per_gpu": nd, "precision": args.prec,
+                          "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

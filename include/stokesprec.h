@@ -1,0 +1,188 @@
+/*
+ * stokesprec.h -- C ABI of the GB300 library for the hot path of
+ * Stokes-preconditioned Newton (Tuckerman, Langham & Willis, arXiv:1804.05087).
+ *
+ * The method (Sec. 2) looks for roots of G(U) = B_dt(U) - U, where one
+ * Backwards-Euler/Forwards-Euler step B_dt = (I - dt L)^-1 (I + dt N) is taken
+ * with a very large dt (Eqs. befe, mycalc, Gstokes). Newton's method solves
+ * G_U du = G(U) by matrix-free GMRES (Eqs. linear, biglin, Kspace), so the hot
+ * path is the action of G_U: one linearised BEFE step (Eq. finitediff and the
+ * linearisation N -> N_U that precedes it).
+ *
+ * Geometry: plane Couette flow, Fourier in x and z, Chebyshev in y (Sec. 3.2).
+ * The state is the deviation u = U - y e_x from laminar flow (Sec. 3.1).
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions shared by every entry point
+ *
+ * State layout (device memory, owned by the caller): interleaved complex
+ *   double [3][MX][MZ][NY] per state, component (u, v, w) slowest, then the
+ *   x-wavenumber index in FFT order (0..Kx, -Kx..-1), then iz = 0..Kz, then
+ *   the Chebyshev degree n = 0..N fastest. Kx = (Nx-1)/3, Kz = (Nz-1)/3 (2/3
+ *   rule), MX = 2Kx+1, MZ = Kz+1, NY = Ny = N+1. A state holds
+ *   sp_state_len() doubles (2 per complex coefficient). Batches of states are
+ *   stored back to back.
+ * Real fields: the kz = 0 plane is stored for both ix and -ix. Every map
+ *   reads its input through the projection onto Hermitian-consistent states
+ *   (mean of an entry and the conjugate of its mirror) and writes an exactly
+ *   Hermitian-consistent output.
+ * Inner product (norms, GMRES, adjoint): <a,b> = sum over stored coefficients
+ *   of w(iz) Re(conj(a) b), with w(0) = 1 and w(iz>0) = 2.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream). Calls
+ *   are asynchronous on it unless stated otherwise; pointers must stay valid
+ *   until the work completes.
+ * Errors: every call returns an sp_status; sp_last_error() gives a message.
+ *   No call traps or aborts the process. Invalid arguments return SP_EINVAL
+ *   before any work is enqueued.
+ * Threads: a context may be used by one host thread at a time.
+ */
+#ifndef STOKESPREC_H
+#define STOKESPREC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sp_ctx sp_ctx;
+
+typedef enum {
+  SP_OK = 0,
+  SP_EINVAL = 1,    /* bad argument or unsupported size                      */
+  SP_ENOMEM = 2,    /* device allocation at create time failed               */
+  SP_ECUDA = 3,     /* a CUDA runtime call failed (message in last_error)    */
+  SP_ENOTCONV = 4,  /* Newton stopped before |G| < tol                       */
+  SP_ETIMEOUT = 5,  /* a bounded device wait expired                         */
+  SP_ENAN = 6       /* non-finite value detected                             */
+} sp_status;
+
+typedef enum {
+  SP_FP64 = 0,      /* every stage in double precision                       */
+  SP_MIXED = 1      /* transforms and products in float, solve/residual in double */
+} sp_prec;
+
+typedef struct {
+  int nx, ny, nz;   /* physical grid: Nx x Ny x Nz, Nx and Nz even, Ny odd    */
+  double lx, lz;    /* box lengths in x and z (walls at y = -1, +1)          */
+  double re;        /* Reynolds number, nu = 1/re                            */
+  double dt;        /* the single BEFE step dt = T (Eq. Gstokes)             */
+  int prec;         /* sp_prec: precision of the tangent (sp_jvp, sp_vjp)    */
+  int max_batch;    /* largest n_dir a single internal pass handles (>= 1);
+                       larger batches are processed in passes of this size   */
+} sp_config;
+
+/* ---- lifetime ----------------------------------------------------------- */
+
+/* Build a context: checks the sizes, precomputes the transform tables and the
+ * per-mode Stokes solution operators (Sec. 3.2: exact direct inversions per
+ * Fourier mode) and allocates the device workspaces. Uses the current CUDA
+ * device. Synchronous. On failure *out is NULL. */
+sp_status sp_create(const sp_config* cfg, sp_ctx** out);
+sp_status sp_destroy(sp_ctx* ctx);
+/* Message of the last failure on ctx; with ctx == NULL, the message of the last
+ * failed sp_create on the calling thread. Never NULL. */
+const char* sp_last_error(const sp_ctx* ctx);
+
+/* Number of doubles in one state (2 * 3 * MX * MZ * NY). */
+size_t sp_state_len(const sp_ctx* ctx);
+/* Retained ranges: kx_max = Kx, kz_max = Kz, ny = N + 1. */
+sp_status sp_dims(const sp_ctx* ctx, int* kx_max, int* kz_max, int* ny);
+
+/* ---- seeded initial states ---------------------------------------------- */
+
+/* Build a divergence-free, no-slip perturbation from random shape series.
+ * ra, rb, rc: device complex double [MX][MZ][NY] (the layout above without
+ * the component axis): per mode v = (1-y^2)^2 sum ra_n T_n and wall-normal
+ * vorticity eta = (1-y^2) sum rb_n T_n, then u = i(kx Dv - kz eta)/k^2,
+ * w = i(kz Dv + kx eta)/k^2; mode (0,0): u = (1-y^2) sum rb_n T_n,
+ * w = (1-y^2) sum rc_n T_n, v = 0. The result is scaled to norm `amp`.
+ * ra must vanish for n > N-4 and rb, rc for n > N-2. Synchronous. */
+sp_status sp_seed_state(sp_ctx* ctx, const double* ra, const double* rb,
+                        const double* rc, double amp, double* U, void* stream);
+
+/* ---- the BEFE step and its derivatives ---------------------------------- */
+
+/* G = B_dt(U) - U, one BEFE step (Eqs. befe, Gstokes), always in FP64:
+ * N(U) = (U + y e_x) x (curl U - e_z) pseudospectrally on the Nx x Ny x Nz grid
+ * (2/3-dealiased in x and z), then per Fourier mode the Chebyshev-tau Stokes
+ * problem (1/dt - nu lap) u_new + grad p = U/dt + N(U), div u_new = 0 for every
+ * Chebyshev coefficient, u_new(+-1) = 0; G = u_new - U. U and G: one state
+ * each (may not alias). */
+sp_status sp_step(sp_ctx* ctx, const double* U, double* G, void* stream);
+
+/* Set the linearisation point: stores U, the total fields (U + y e_x,
+ * curl U - e_z) on the grid for sp_jvp/sp_vjp, and G(U) for sp_jvp_fd. */
+sp_status sp_set_base(sp_ctx* ctx, const double* U, void* stream);
+
+/* Jdu = G_U du for n_dir directions (batched, back to back): the linearised
+ * step with N -> N_U = U_tot x omega(du) + du x Omega_tot and homogeneous
+ * boundary data (Sec. 2). Precision: cfg.prec. Needs sp_set_base. */
+sp_status sp_jvp(sp_ctx* ctx, const double* du, double* Jdu, int n_dir, void* stream);
+
+/* JTr = G_U^* r for n_dir vectors: the adjoint of sp_jvp in the inner product
+ * above (the transpose of every stage, in reverse). Precision: cfg.prec. */
+sp_status sp_vjp(sp_ctx* ctx, const double* r, double* JTr, int n_dir, void* stream);
+
+/* Finite-difference action [G(U + eps du) - G(U)]/eps (Eq. finitediff) for
+ * n_dir directions, FP64, with eps = 1e-7 (1 + |U|)/|du| per direction.
+ * Needs sp_set_base. Synchronous (reads the norms on the host). */
+sp_status sp_jvp_fd(sp_ctx* ctx, const double* du, double* Jdu, int n_dir, void* stream);
+
+/* ---- vector operations in the inner product above ---------------------- */
+
+/* out[i] = <a_i, b_i> for i < n (states back to back), FP64. Synchronous. */
+sp_status sp_inner(sp_ctx* ctx, const double* a, const double* b, int n,
+                   double* out_host, void* stream);
+
+/* ---- tracing ------------------------------------------------------------- */
+
+/* Per-kernel timing. While enabled, every kernel the library launches is
+ * bracketed by two CUDA events recorded on the call's stream, accumulated per
+ * kernel family (the stage indices below). Enabling resets the totals. */
+enum { SP_STAGE_YINV = 0,   /* k_yinv of the tangent / adjoint         */
+       SP_STAGE_XZ = 1,     /* k_xz: x/z FFTs and the tangent product  */
+       SP_STAGE_SOLVE = 2,  /* k_solve of the tangent / adjoint        */
+       SP_STAGE_STEP = 3,   /* every kernel of sp_step and sp_set_base */
+       SP_STAGE_VEC = 4,    /* vector kernels (norms, axpy, seeding)   */
+       SP_NSTAGE = 5 };
+sp_status sp_trace_enable(sp_ctx* ctx, int on);
+/* Waits for the recorded events, then writes the accumulated milliseconds and
+ * launch counts of the n (<= SP_NSTAGE) first stages. Host arrays. */
+sp_status sp_trace_read(sp_ctx* ctx, double* ms, long long* launches, int n);
+
+/* ---- Newton-GMRES-hookstep ------------------------------------------------ */
+
+typedef struct {
+  int max_newton;     /* Newton iterations cap                               */
+  int max_krylov;     /* GMRES dimension cap K (no restarts)                 */
+  double tol;         /* stop when |G(U)| < tol                              */
+  double eta;         /* GMRES stops at residual <= eta |G(U)| (Sec. 3.6)    */
+  double delta0;      /* initial trust radius (<= 0: 0.1 max(|U|, 1))        */
+  int use_fd;         /* 1: Jacobian actions by Eq. finitediff, 0: tangent   */
+} sp_newton_opts;
+
+typedef struct {
+  int newton_iters;   /* Newton steps taken                                   */
+  int total_jvps;     /* Jacobian actions (GMRES iterations) over all steps  */
+  int total_steps;    /* BEFE steps of G itself (residuals, hookstep trials) */
+  double norm_F;      /* final |G(U)|                                        */
+  double norm_F0;     /* initial |G(U)|                                      */
+  double t_action_ms; /* time in Jacobian actions (first term of Eq. CPU)    */
+  double t_orth_ms;   /* time in orthogonalisation (second term of Eq. CPU)  */
+  double t_total_ms;
+} sp_newton_report;
+
+/* Newton-GMRES with hookstep (Sec. 2, Sec. 3.2): U_inout holds the initial
+ * guess and receives the result. Synchronous. Returns SP_ENOTCONV if the
+ * iteration cap is reached with |G| >= tol (U_inout still holds the last
+ * accepted iterate). */
+sp_status sp_newton_gmres(sp_ctx* ctx, double* U_inout, const sp_newton_opts* opts,
+                          sp_newton_report* report, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STOKESPREC_H */

@@ -1,0 +1,227 @@
+"""Python binding of the stokesprec C ABI (include/stokesprec.h).
+
+Argument marshalling only: every step of the BEFE map, its tangent, adjoint
+and the Newton-GMRES vector work runs in the CUDA library
+``_lib/libstokesprec.so``. PyTorch provides device memory and streams.
+There is no CPU fallback: importing the binding without the built library
+raises immediately.
+
+States are complex128 CUDA tensors of shape [..., 3, MX, MZ, NY] (component,
+x-wavenumber in FFT order, z-wavenumber 0..Kz, Chebyshev degree), contiguous.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libstokesprec.so")
+
+SP_FP64 = 0
+SP_MIXED = 1
+_STATUS = {0: "SP_OK", 1: "SP_EINVAL", 2: "SP_ENOMEM", 3: "SP_ECUDA", 4: "SP_ENOTCONV",
+           5: "SP_ETIMEOUT", 6: "SP_ENAN"}
+
+
+class SpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("lz", ctypes.c_double), ("re", ctypes.c_double),
+                ("dt", ctypes.c_double), ("prec", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
+class _NewtonOpts(ctypes.Structure):
+    _fields_ = [("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int), ("tol", ctypes.c_double),
+                ("eta", ctypes.c_double), ("delta0", ctypes.c_double), ("use_fd", ctypes.c_int)]
+
+
+class _NewtonReport(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("total_jvps", ctypes.c_int), ("total_steps", ctypes.c_int),
+                ("norm_F", ctypes.c_double), ("norm_F0", ctypes.c_double), ("t_action_ms", ctypes.c_double),
+                ("t_orth_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"stokesprec library not built ({LIB_PATH} missing); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, D, I, V = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+    sig = {
+        "sp_create": ([ctypes.POINTER(_Config), ctypes.POINTER(ctypes.c_void_p)], I),
+        "sp_destroy": ([P], I),
+        "sp_last_error": ([P], ctypes.c_char_p),
+        "sp_state_len": ([P], ctypes.c_size_t),
+        "sp_dims": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "sp_seed_state": ([P, P, P, P, D, P, V], I),
+        "sp_step": ([P, P, P, V], I),
+        "sp_set_base": ([P, P, V], I),
+        "sp_jvp": ([P, P, P, I, V], I),
+        "sp_vjp": ([P, P, P, I, V], I),
+        "sp_jvp_fd": ([P, P, P, I, V], I),
+        "sp_inner": ([P, P, P, I, ctypes.POINTER(D), V], I),
+        "sp_newton_gmres": ([P, P, ctypes.POINTER(_NewtonOpts), ctypes.POINTER(_NewtonReport), V], I),
+        "sp_trace_enable": ([P, I], I),
+        "sp_trace_read": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), I], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+#: names every build must export (the declarations of include/stokesprec.h)
+EXPORTS = ("sp_create", "sp_destroy", "sp_last_error", "sp_state_len", "sp_dims", "sp_seed_state",
+           "sp_step", "sp_set_base", "sp_jvp", "sp_vjp", "sp_jvp_fd", "sp_inner", "sp_newton_gmres",
+           "sp_trace_enable", "sp_trace_read")
+STAGES = ("k_yinv", "k_xz", "k_solve", "step", "vector")
+
+
+@dataclass
+class Config:
+    nx: int
+    ny: int
+    nz: int
+    lx: float = 2 * 3.141592653589793 / 1.14
+    lz: float = 2 * 3.141592653589793 / 2.5
+    re: float = 400.0
+    dt: float = 100.0
+    prec: int = SP_FP64
+    max_batch: int = 1
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Context:
+    """One configuration: plans, operators and workspaces on the current GPU."""
+
+    def __init__(self, cfg: Config):
+        self.cfg = cfg
+        c = _Config(cfg.nx, cfg.ny, cfg.nz, cfg.lx, cfg.lz, cfg.re, cfg.dt, cfg.prec, cfg.max_batch)
+        h = ctypes.c_void_p()
+        st = _lib.sp_create(ctypes.byref(c), ctypes.byref(h))
+        if st != 0:
+            raise SpError(st, _lib.sp_last_error(None).decode())
+        self._h = h
+        kx, kz, ny = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _lib.sp_dims(h, ctypes.byref(kx), ctypes.byref(kz), ctypes.byref(ny))
+        self.Kx, self.Kz, self.NY = kx.value, kz.value, ny.value
+        self.MX, self.MZ = 2 * self.Kx + 1, self.Kz + 1
+        self.state_len = int(_lib.sp_state_len(h))
+        self.shape = (3, self.MX, self.MZ, self.NY)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.sp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            raise SpError(st, _lib.sp_last_error(self._h).decode())
+
+    def _ptr(self, t: torch.Tensor, count: int = None):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError("expected a CUDA tensor")
+        if t.dtype != torch.complex128 or not t.is_contiguous():
+            raise TypeError("expected a contiguous complex128 tensor")
+        n = t.numel() * 2
+        if n % self.state_len:
+            raise ValueError(f"tensor size {t.numel()} is not a whole number of states")
+        if count is not None and n != count * self.state_len:
+            raise ValueError("tensor holds the wrong number of states")
+        return ctypes.c_void_p(t.data_ptr()), n // self.state_len
+
+    def zeros(self, n=None, device="cuda"):
+        shape = self.shape if n is None else (n,) + self.shape
+        return torch.zeros(shape, dtype=torch.complex128, device=device)
+
+    # ------------------------------------------------------------ the ABI
+    def sp_seed_state(self, ra, rb, rc, amp, U, stream=None):
+        for t in (ra, rb, rc):
+            if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous() \
+                    or t.numel() * 6 != self.state_len:
+                raise ValueError("random shapes must be complex128 [MX][MZ][NY] CUDA tensors")
+        pu, _ = self._ptr(U, 1)
+        self._check(_lib.sp_seed_state(self._h, ctypes.c_void_p(ra.data_ptr()), ctypes.c_void_p(rb.data_ptr()),
+                                       ctypes.c_void_p(rc.data_ptr()), float(amp), pu, _stream(stream)))
+        return U
+
+    def sp_step(self, U, G, stream=None):
+        pu, _ = self._ptr(U, 1)
+        pg, _ = self._ptr(G, 1)
+        self._check(_lib.sp_step(self._h, pu, pg, _stream(stream)))
+        return G
+
+    def sp_set_base(self, U, stream=None):
+        pu, _ = self._ptr(U, 1)
+        self._check(_lib.sp_set_base(self._h, pu, _stream(stream)))
+
+    def sp_jvp(self, du, out, stream=None):
+        pd, n = self._ptr(du)
+        po, _ = self._ptr(out, n)
+        self._check(_lib.sp_jvp(self._h, pd, po, n, _stream(stream)))
+        return out
+
+    def sp_vjp(self, r, out, stream=None):
+        pr, n = self._ptr(r)
+        po, _ = self._ptr(out, n)
+        self._check(_lib.sp_vjp(self._h, pr, po, n, _stream(stream)))
+        return out
+
+    def sp_jvp_fd(self, du, out, stream=None):
+        pd, n = self._ptr(du)
+        po, _ = self._ptr(out, n)
+        self._check(_lib.sp_jvp_fd(self._h, pd, po, n, _stream(stream)))
+        return out
+
+    def sp_inner(self, a, b, stream=None):
+        pa, n = self._ptr(a)
+        pb, _ = self._ptr(b, n)
+        out = (ctypes.c_double * n)()
+        self._check(_lib.sp_inner(self._h, pa, pb, n, out, _stream(stream)))
+        return list(out)
+
+    def sp_trace_enable(self, on=True):
+        self._check(_lib.sp_trace_enable(self._h, 1 if on else 0))
+
+    def sp_trace_read(self):
+        """{stage: (total ms, launches)} accumulated since sp_trace_enable."""
+        n = len(STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        self._check(_lib.sp_trace_read(self._h, ms, cnt, n))
+        return {STAGES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+    def sp_newton_gmres(self, U, max_newton=20, max_krylov=30, tol=1e-10, eta=1e-3, delta0=0.0,
+                        use_fd=False, stream=None):
+        pu, _ = self._ptr(U, 1)
+        o = _NewtonOpts(max_newton, max_krylov, tol, eta, delta0, 1 if use_fd else 0)
+        r = _NewtonReport()
+        st = _lib.sp_newton_gmres(self._h, pu, ctypes.byref(o), ctypes.byref(r), _stream(stream))
+        rep = {k: getattr(r, k) for k, _ in _NewtonReport._fields_}
+        rep["converged"] = st == 0
+        if st not in (0, 4):
+            self._check(st)
+        return rep

@@ -1,0 +1,944 @@
+// CUDA kernels of the BEFE step, its tangent and the vector operations.
+//
+// One step (Sec. 2, Eq. befe) in Fourier x,z / Chebyshev y is three kernels:
+//   k_yinv : per Fourier mode, Chebyshev coefficients -> values at the
+//            Gauss-Lobatto points of u, v, w and of the vorticity (curl taken
+//            in spectral space: i kx, i kz and the coefficient derivative),
+//            written plane-major so that each y-plane is contiguous.
+//   k_xz   : per y-plane, the inverse x/z FFTs of the six fields, the
+//            pointwise product (U_tot x Omega_tot for the step,
+//            U_tot x omega + u x Omega_tot for the tangent), and the forward
+//            FFTs truncated to the 2/3-rule modes (pseudospectral products,
+//            Sec. 3.2).
+//   k_solve: per Fourier mode, values -> Chebyshev coefficients, the
+//            right-hand side u/dt + N, the Chebyshev-tau Stokes solve through
+//            the precomputed per-mode operators, and G = u_new - u.
+// T is the real type of the transforms and the product (double or float);
+// the solve and everything after it are double.
+#include <cstdio>
+
+#include "sp_internal.h"
+
+namespace {
+
+constexpr int kThreadsXZ = 256;
+constexpr int kThreadsYinv = 256;
+constexpr int kThreadsSolve = 128;
+constexpr int kTileYinv = 16;   // modes per k_yinv block
+constexpr int kTileSolve = 4;   // modes per k_solve block
+
+// ------------------------------------------------------------------ FFT
+// Batched complex FFT of length pl.n in shared memory, Stockham
+// decimation-in-time with radices 2, 3 and 4. Stage s combines p = radix[s]
+// sub-transforms of length L (product of the earlier radices):
+//   out[(t0 + L d) R' + b'] = sum_c (w_n^{c t0 R'} in[t0 R + b' + R' c]) w_p^{c d}
+// with R = n/L, R' = R/p, w_m = exp(sgn 2 pi i / m). The first stage reads its
+// input through `load(b, e)` (element e of transform b), the last stage hands
+// its outputs to `store(b, e, v)`; the stages in between ping-pong between s0
+// and s1 (layout [element][batch]). Ends with __syncthreads().
+template <typename T, class LoadF, class StoreF>
+__device__ void fft_batch(const FftPlan& pl, int nb, const C2<T>* __restrict__ tw, T sgn,
+                          C2<T>* s0, C2<T>* s1, LoadF load, StoreF store) {
+  const int n = pl.n;
+  const T h3 = (T)0.86602540378443864676;  // sqrt(3)/2
+  int L = 1;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int p = pl.radix[s];
+    const int R = n / L, Rp = R / p;
+    const int nbf = n / p;
+    const C2<T>* src = (s & 1) ? s0 : s1;
+    C2<T>* dst = (s & 1) ? s1 : s0;
+    const bool first = (s == 0), last = (s == pl.nst - 1);
+    for (int idx = threadIdx.x; idx < nb * nbf; idx += blockDim.x) {
+      const int b = idx % nb;
+      const int bf = idx / nb;
+      const int t0 = bf / Rp, bp = bf - t0 * Rp;
+      C2<T> x[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c < p) {
+          const int e = t0 * R + bp + Rp * c;
+          x[c] = first ? load(b, e) : src[e * nb + b];
+        }
+      }
+      if (t0 != 0) {
+#pragma unroll
+        for (int c = 1; c < 4; ++c) {
+          if (c < p) {
+            C2<T> w = tw[(c * t0 * Rp) % n];
+            if (sgn > (T)0) w.y = -w.y;
+            x[c] = x[c] * w;
+          }
+        }
+      }
+      C2<T> y[4];
+      if (p == 2) {
+        y[0] = x[0] + x[1];
+        y[1] = x[0] - x[1];
+      } else if (p == 3) {
+        C2<T> t1 = x[1] + x[2];
+        C2<T> t2 = mul_is(x[1] - x[2], sgn * h3);
+        C2<T> m = x[0] - scl(t1, (T)0.5);
+        y[0] = x[0] + t1;
+        y[1] = m + t2;
+        y[2] = m - t2;
+      } else {
+        C2<T> a = x[0] + x[2], bb = x[0] - x[2];
+        C2<T> c = x[1] + x[3], d = mul_is(x[1] - x[3], sgn);
+        y[0] = a + c;
+        y[2] = a - c;
+        y[1] = bb + d;
+        y[3] = bb - d;
+      }
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        if (d < p) {
+          const int e = (t0 + L * d) * Rp + bp;
+          if (last) store(b, e, y[d]);
+          else dst[e * nb + b] = y[d];
+        }
+      }
+    }
+    __syncthreads();
+    L *= p;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ C2<T> ld_c2(const C2<T>* p) { return *p; }
+__device__ __forceinline__ C2<double> ld_c2(const C2<double>* p) {
+  double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return mk(v.x, v.y);
+}
+__device__ __forceinline__ C2<float> ld_c2(const C2<float>* p) {
+  float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return mk(v.x, v.y);
+}
+
+// ------------------------------------------------------------ k_yinv
+struct YinvArgs {
+  int Mm, MZ, MX, Kx, NY, N, NH, jchunk;
+  double alpha, beta;
+};
+
+// in : [dir][3][Mm][NY] complex double (the boundary state layout)
+// out: [dir][6][NY][Mm] complex T, fields u, v, w, wx, wy, wz
+template <typename T>
+__global__ void __launch_bounds__(kThreadsYinv) k_yinv(const double2* __restrict__ in,
+                                                      C2<T>* __restrict__ out,
+                                                      const T* __restrict__ Th,
+                                                      const T* __restrict__ TDh, YinvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* sc = reinterpret_cast<C2<T>*>(smem_raw);  // [3][NY][TM]
+  const int TM = kTileYinv;
+  const int m0 = blockIdx.x * TM;
+  const int dir = blockIdx.z;
+  const int NY = a.NY, Mm = a.Mm;
+  const double2* src = in + (size_t)dir * 3 * Mm * NY;
+  for (int idx = threadIdx.x; idx < 3 * TM * NY; idx += blockDim.x) {
+    const int c = idx / (TM * NY);
+    const int rem = idx - c * TM * NY;
+    const int t = rem / NY, n = rem - t * NY;
+    const int m = m0 + t;
+    C2<T> v = mk((T)0, (T)0);
+    if (m < Mm) {
+      double2 d = __ldg(src + ((size_t)c * Mm + m) * NY + n);
+      v = mk((T)d.x, (T)d.y);
+    }
+    sc[(c * NY + n) * TM + t] = v;
+  }
+  __syncthreads();
+  const int j_lo = blockIdx.y * a.jchunk;
+  const int j_hi = min(a.NH, j_lo + a.jchunk);
+  const int items = TM * (j_hi - j_lo);
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int t = it % TM;
+    const int jh = j_lo + it / TM;
+    const int m = m0 + t;
+    if (m >= Mm) continue;
+    C2<T> Eu = mk((T)0, (T)0), Ou = Eu, Ev = Eu, Ov = Eu, Ew = Eu, Ow = Eu;
+    C2<T> EDu = Eu, ODu = Eu, EDw = Eu, ODw = Eu;
+    const T* trow = Th + (size_t)jh * NY;
+    const T* drow = TDh + (size_t)jh * NY;
+    int n = 0;
+    for (; n + 1 < NY; n += 2) {
+      const T t0 = trow[n], t1 = trow[n + 1];
+      const T d0 = drow[n], d1 = drow[n + 1];
+      const C2<T> u0 = sc[(0 * NY + n) * TM + t], u1 = sc[(0 * NY + n + 1) * TM + t];
+      const C2<T> v0 = sc[(1 * NY + n) * TM + t], v1 = sc[(1 * NY + n + 1) * TM + t];
+      const C2<T> w0 = sc[(2 * NY + n) * TM + t], w1 = sc[(2 * NY + n + 1) * TM + t];
+      Eu = Eu + scl(u0, t0); Ou = Ou + scl(u1, t1);
+      Ev = Ev + scl(v0, t0); Ov = Ov + scl(v1, t1);
+      Ew = Ew + scl(w0, t0); Ow = Ow + scl(w1, t1);
+      EDu = EDu + scl(u0, d0); ODu = ODu + scl(u1, d1);
+      EDw = EDw + scl(w0, d0); ODw = ODw + scl(w1, d1);
+    }
+    if (n < NY) {  // NY odd: last (even) degree
+      const T t0 = trow[n], d0 = drow[n];
+      const C2<T> u0 = sc[(0 * NY + n) * TM + t];
+      const C2<T> v0 = sc[(1 * NY + n) * TM + t];
+      const C2<T> w0 = sc[(2 * NY + n) * TM + t];
+      Eu = Eu + scl(u0, t0); Ev = Ev + scl(v0, t0); Ew = Ew + scl(w0, t0);
+      EDu = EDu + scl(u0, d0); EDw = EDw + scl(w0, d0);
+    }
+    const int pos = m / a.MZ, iz = m - pos * a.MZ;
+    const int ix = pos <= a.Kx ? pos : pos - a.MX;
+    const T kx = (T)(a.alpha * ix), kz = (T)(a.beta * iz);
+    C2<T>* o = out + (size_t)dir * 6 * NY * Mm;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int j = side == 0 ? jh : a.N - jh;
+      if (side == 1 && j == jh) break;
+      const T sg = side == 0 ? (T)1 : (T)-1;
+      // T_n(-y) = (-1)^n T_n(y); T_n'(-y) = (-1)^(n+1) T_n'(y)
+      const C2<T> u = Eu + scl(Ou, sg), v = Ev + scl(Ov, sg), w = Ew + scl(Ow, sg);
+      const C2<T> Du = scl(EDu, sg) + ODu, Dw = scl(EDw, sg) + ODw;
+      const C2<T> ox = Dw - mul_is(v, kz);
+      const C2<T> oy = mul_is(u, kz) - mul_is(w, kx);
+      const C2<T> oz = mul_is(v, kx) - Du;
+      const size_t base = (size_t)j * Mm + m;
+      o[0 * (size_t)NY * Mm + base] = u;
+      o[1 * (size_t)NY * Mm + base] = v;
+      o[2 * (size_t)NY * Mm + base] = w;
+      o[3 * (size_t)NY * Mm + base] = ox;
+      o[4 * (size_t)NY * Mm + base] = oy;
+      o[5 * (size_t)NY * Mm + base] = oz;
+    }
+  }
+}
+
+// -------------------------------------------------------------- k_xz
+template <typename T>
+struct XzArgs {
+  const C2<T>* in6;   // [dir][6][NY][Mm]
+  C2<T>* out3;        // [dir][3][NY][Mm]
+  T* base;            // [6][NY][nx][nz] (read for the tangent, written for BASE)
+  const C2<T>* twx;   // [nx] exp(-2 pi i k/nx)
+  const C2<T>* twz;
+  const double* yv;   // [NY] Gauss-Lobatto points
+  FftPlan px, pz;
+  int nx, nz, NY, Mm, MX, MZ, Kx, Kz;
+  int rp, cx;         // row pairs per z chunk, columns per x chunk
+  int FS, RS;         // field and row strides of the plane buffer G
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* stwx = reinterpret_cast<C2<T>*>(smem_raw);
+  C2<T>* stwz = stwx + a.nx;
+  C2<T>* G = stwz + a.nz;                       // [nx][6][FS] (row stride RS)
+  C2<T>* S = G + (size_t)a.nx * a.RS;           // scratch
+  const int j = blockIdx.x;
+  const int dir = blockIdx.y;
+  const int nx = a.nx, nz = a.nz, MZ = a.MZ, Kx = a.Kx, Kz = a.Kz;
+  const int FS = a.FS, RS = a.RS;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) stwx[i] = ld_c2(a.twx + i);
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) stwz[i] = ld_c2(a.twz + i);
+  __syncthreads();
+  const C2<T> zero = mk((T)0, (T)0);
+  const size_t planeMm = (size_t)a.NY * a.Mm;
+  const C2<T>* in6 = a.in6 + (size_t)dir * 6 * planeMm + (size_t)j * a.Mm;
+
+  // ---- phase 1: inverse FFT along x of every (field, iz) column
+  {
+    const int ncol = 6 * MZ;
+    for (int c0 = 0; c0 < ncol; c0 += a.cx) {
+      const int nb = min(a.cx, ncol - c0);
+      auto load = [&](int b, int e) -> C2<T> {
+        const int col = c0 + b;
+        const int f = col / MZ, iz = col - f * MZ;
+        int pos;
+        if (e <= Kx) pos = e;
+        else if (e >= nx - Kx) pos = e - nx + a.MX;
+        else return zero;
+        return ld_c2(in6 + (size_t)f * planeMm + pos * MZ + iz);
+      };
+      auto store = [&](int b, int e, C2<T> v) {
+        const int col = c0 + b;
+        const int f = col / MZ, iz = col - f * MZ;
+        G[e * RS + f * FS + iz] = v;
+      };
+      fft_batch<T>(a.px, nb, stwx, (T)1, S, S + (size_t)a.cx * nx, load, store);
+    }
+  }
+
+  // ---- phase 2: per pair of x-rows, c2r along z, product, r2c along z
+  const T yj = (T)a.yv[j];
+  const int rp = a.rp;
+  C2<T>* P0 = S;
+  C2<T>* P1 = S + (size_t)6 * rp * nz;
+  C2<T>* Q = S + (size_t)12 * rp * nz;
+  C2<T>* R = S + (size_t)18 * rp * nz;
+  const size_t nxz = (size_t)nx * nz;
+  for (int q0 = 0; q0 < nx / 2; q0 += rp) {
+    const int nq = min(rp, nx / 2 - q0);
+    {
+      const int nb = 6 * nq;
+      auto load = [&](int b, int e) -> C2<T> {
+        const int qq = b / 6, f = b - qq * 6;
+        const int x0 = 2 * (q0 + qq);
+        const C2<T>* g0 = G + x0 * RS + f * FS;
+        const C2<T>* g1 = g0 + RS;
+        if (e == 0) return mk(g0[0].x, g1[0].x);
+        if (e <= Kz) {
+          const C2<T> A = g0[e], B = g1[e];
+          return mk(A.x - B.y, A.y + B.x);
+        }
+        if (e >= nz - Kz) {
+          const C2<T> A = g0[nz - e], B = g1[nz - e];
+          return mk(A.x + B.y, B.x - A.y);
+        }
+        return zero;
+      };
+      auto store = [&](int b, int e, C2<T> v) { Q[e * nb + b] = v; };
+      fft_batch<T>(a.pz, nb, stwz, (T)1, P0, P1, load, store);
+    }
+    // pointwise products on the two rows of each pair
+    {
+      const int nb6 = 6 * nq, nb3 = 3 * nq;
+      for (int it = threadIdx.x; it < nq * nz; it += blockDim.x) {
+        const int qq = it / nz, k = it - qq * nz;
+        const int x0 = 2 * (q0 + qq);
+        C2<T> fv[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) fv[f] = Q[k * nb6 + qq * 6 + f];
+        T res[2][3];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          T F[6];
+#pragma unroll
+          for (int f = 0; f < 6; ++f) F[f] = r ? fv[f].y : fv[f].x;
+          const size_t gidx = (size_t)j * nxz + (size_t)(x0 + r) * nz + k;
+          if (MODE == XZ_BASE) {
+            F[0] += yj;
+            F[5] -= (T)1;
+#pragma unroll
+            for (int f = 0; f < 6; ++f) a.base[(size_t)f * a.NY * nxz + gidx] = F[f];
+          } else if (MODE == XZ_STEP) {
+            const T U0 = F[0] + yj, U1 = F[1], U2 = F[2];
+            const T O0 = F[3], O1 = F[4], O2 = F[5] - (T)1;
+            res[r][0] = U1 * O2 - U2 * O1;
+            res[r][1] = U2 * O0 - U0 * O2;
+            res[r][2] = U0 * O1 - U1 * O0;
+          } else {
+            T B[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) B[f] = a.base[(size_t)f * a.NY * nxz + gidx];
+            // U_tot x omega + u x Omega_tot
+            res[r][0] = (B[1] * F[5] - B[2] * F[4]) + (F[1] * B[5] - F[2] * B[4]);
+            res[r][1] = (B[2] * F[3] - B[0] * F[5]) + (F[2] * B[3] - F[0] * B[5]);
+            res[r][2] = (B[0] * F[4] - B[1] * F[3]) + (F[0] * B[4] - F[1] * B[3]);
+          }
+        }
+        if (MODE != XZ_BASE) {
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) R[k * nb3 + qq * 3 + cc] = mk(res[0][cc], res[1][cc]);
+        }
+      }
+      __syncthreads();
+    }
+    if (MODE != XZ_BASE) {
+      const int nb = 3 * nq;
+      auto load = [&](int b, int e) -> C2<T> { return R[e * nb + b]; };
+      auto store = [&](int b, int e, C2<T> v) { Q[e * nb + b] = v; };
+      fft_batch<T>(a.pz, nb, stwz, (T)-1, P0, P1, load, store);
+      // separate the two real rows: A(k) = (X(k) + conj X(-k))/2, B(k) = (X(k) - conj X(-k))/(2i)
+      for (int it = threadIdx.x; it < nb * MZ; it += blockDim.x) {
+        const int iz = it / nb, b = it - iz * nb;
+        const int qq = b / 3, cc = b - qq * 3;
+        const int x0 = 2 * (q0 + qq);
+        const C2<T> X = Q[iz * nb + b];
+        const C2<T> Xm = Q[((nz - iz) % nz) * nb + b];
+        const C2<T> A = scl(X + conj2(Xm), (T)0.5);
+        const C2<T> D = X - conj2(Xm);
+        G[x0 * RS + cc * FS + iz] = A;
+        G[(x0 + 1) * RS + cc * FS + iz] = mk(D.y * (T)0.5, -D.x * (T)0.5);
+      }
+      __syncthreads();
+    }
+  }
+  if (MODE == XZ_BASE) return;
+
+  // ---- phase 3: forward FFT along x, keep the 2/3-rule modes
+  {
+    const T inv = (T)(1.0 / ((double)nx * (double)nz));
+    C2<T>* out = a.out3 + (size_t)dir * 3 * planeMm + (size_t)j * a.Mm;
+    const int ncol = 3 * MZ;
+    for (int c0 = 0; c0 < ncol; c0 += a.cx) {
+      const int nb = min(a.cx, ncol - c0);
+      auto load = [&](int b, int e) -> C2<T> {
+        const int col = c0 + b;
+        const int cc = col / MZ, iz = col - cc * MZ;
+        return G[e * RS + cc * FS + iz];
+      };
+      auto store = [&](int b, int e, C2<T> v) {
+        int pos;
+        if (e <= Kx) pos = e;
+        else if (e >= nx - Kx) pos = e - nx + a.MX;
+        else return;
+        const int col = c0 + b;
+        const int cc = col / MZ, iz = col - cc * MZ;
+        out[(size_t)cc * planeMm + pos * MZ + iz] = scl(v, inv);
+      };
+      fft_batch<T>(a.px, nb, stwx, (T)-1, S, S + (size_t)a.cx * nx, load, store);
+    }
+  }
+}
+
+// ------------------------------------------------------------ k_solve
+struct SolveArgs {
+  const double* ops;
+  const double* Cfh_d;
+  const float* Cfh_f;
+  int n_unique, Mm, MX, MZ, Kx, NY, N, NH;
+  int cv, rb0, rb1, off_v0, off_v1, off_h0, off_h1, op_stride;
+  double alpha, beta, inv_dt;
+};
+
+__device__ __forceinline__ void unique_to_mode(int u, int Kx, int MZ, int* pos, int* iz) {
+  const int first = (Kx + 1) * MZ;
+  if (u < first) {
+    *pos = u / MZ;
+    *iz = u - *pos * MZ;
+  } else {
+    const int v = u - first;
+    *pos = Kx + 1 + v / (MZ - 1);
+    *iz = 1 + v % (MZ - 1);
+  }
+}
+
+// in3: [dir][3][NY][Mm] complex T (values of N at the Gauss-Lobatto points)
+// du : [dir][3][Mm][NY] complex double; out: same layout (G = u_new - u)
+template <typename T>
+__global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict__ in3,
+                                                         const double2* __restrict__ du,
+                                                         double2* __restrict__ out, SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int TM = kTileSolve;
+  const int NY = a.NY, N = a.N, NH = a.NH, Mm = a.Mm, MZ = a.MZ;
+  const int NR = N - 1;  // tau rows 0..N-2
+  C2<T>* svals = reinterpret_cast<C2<T>*>(smem_raw);                    // [3][NY][TM]
+  double2* sdu = reinterpret_cast<double2*>(svals + 3 * NY * TM + (3 * NY * TM) % 2);  // [3][TM][NY]
+  double2* sf = sdu + 3 * TM * NY;            // [3][TM][NR]
+  double2* srv = sf + 3 * TM * NR;            // [TM][2][cv]
+  double2* sfb = srv + TM * 2 * a.cv;         // [TM][NR]
+  double2* sfw = sfb + TM * NR;               // [TM][NR] (mean mode w)
+  double2* sv = sfw + TM * NR;                // [TM][NY]
+  double2* sb = sv + TM * NY;                 // [TM][NY]
+  __shared__ int s_pos[kTileSolve], s_iz[kTileSolve], s_u[kTileSolve];
+  const int u0 = blockIdx.x * TM;
+  const int dir = blockIdx.y;
+  if (threadIdx.x < TM) {
+    const int u = u0 + threadIdx.x;
+    int pos = 0, iz = 0;
+    if (u < a.n_unique) unique_to_mode(u, a.Kx, MZ, &pos, &iz);
+    s_pos[threadIdx.x] = pos;
+    s_iz[threadIdx.x] = iz;
+    s_u[threadIdx.x] = u;
+  }
+  __syncthreads();
+  const C2<T>* vin = in3 + (size_t)dir * 3 * NY * Mm;
+  const double2* dsrc = du + (size_t)dir * 3 * Mm * NY;
+  // phase A: load values and the (Hermitian-projected) input state
+  for (int idx = threadIdx.x; idx < 3 * NY * TM; idx += blockDim.x) {
+    const int t = idx % TM;
+    const int jc = idx / TM;  // c*NY + j
+    const int c = jc / NY, jj = jc - c * NY;
+    C2<T> v = mk((T)0, (T)0);
+    if (s_u[t] < a.n_unique) v = ld_c2(vin + ((size_t)c * NY + jj) * Mm + s_pos[t] * MZ + s_iz[t]);
+    svals[idx] = v;
+  }
+  for (int idx = threadIdx.x; idx < 3 * TM * NY; idx += blockDim.x) {
+    const int n = idx % NY;
+    const int t = (idx / NY) % TM;
+    const int c = idx / (NY * TM);
+    double2 v = make_double2(0.0, 0.0);
+    if (s_u[t] < a.n_unique) {
+      const int pos = s_pos[t], iz = s_iz[t];
+      v = __ldg(dsrc + ((size_t)c * Mm + pos * MZ + iz) * NY + n);
+      if (iz == 0) {
+        const int mpos = pos == 0 ? 0 : a.MX - pos;
+        const double2 w = __ldg(dsrc + ((size_t)c * Mm + mpos * MZ) * NY + n);
+        v = make_double2(0.5 * (v.x + w.x), 0.5 * (v.y - w.y));
+      }
+    }
+    sdu[(c * TM + t) * NY + n] = v;
+  }
+  __syncthreads();
+  // phase B: forward Chebyshev transform of N (rows 0..N-2) and the RHS u/dt + N
+  for (int idx = threadIdx.x; idx < 3 * TM * NR; idx += blockDim.x) {
+    const int t = idx % TM;
+    const int n = (idx / TM) % NR;
+    const int c = idx / (TM * NR);
+    C2<T> acc = mk((T)0, (T)0);
+    const C2<T>* col = svals + (c * NY) * TM + t;
+    if (sizeof(T) == 8) {
+      const double* cf = a.Cfh_d + (size_t)n * NH;
+      if ((n & 1) == 0) {
+        for (int jj = 0; jj < NH - 1; ++jj) {
+          const C2<T> s = col[jj * TM] + col[(N - jj) * TM];
+          acc = acc + scl(s, (T)cf[jj]);
+        }
+        acc = acc + scl(col[(NH - 1) * TM], (T)cf[NH - 1]);
+      } else {
+        for (int jj = 0; jj < NH - 1; ++jj) {
+          const C2<T> s = col[jj * TM] - col[(N - jj) * TM];
+          acc = acc + scl(s, (T)cf[jj]);
+        }
+      }
+    } else {
+      const float* cf = a.Cfh_f + (size_t)n * NH;
+      if ((n & 1) == 0) {
+        for (int jj = 0; jj < NH - 1; ++jj) {
+          const C2<T> s = col[jj * TM] + col[(N - jj) * TM];
+          acc = acc + scl(s, (T)cf[jj]);
+        }
+        acc = acc + scl(col[(NH - 1) * TM], (T)cf[NH - 1]);
+      } else {
+        for (int jj = 0; jj < NH - 1; ++jj) {
+          const C2<T> s = col[jj * TM] - col[(N - jj) * TM];
+          acc = acc + scl(s, (T)cf[jj]);
+        }
+      }
+    }
+    const double2 d = sdu[(c * TM + t) * NY + n];
+    double2 f = make_double2((double)acc.x + d.x * a.inv_dt, (double)acc.y + d.y * a.inv_dt);
+    if (s_pos[t] == 0 && s_iz[t] == 0) f.y = 0.0;
+    sf[(c * TM + t) * NR + n] = f;
+  }
+  __syncthreads();
+  // phase C: rotate to the components along / across the wavevector
+  const int rv0 = N / 2, rv1 = N / 2 - 1;  // f_v rows of parity 0 / 1
+  for (int idx = threadIdx.x; idx < TM * NR; idx += blockDim.x) {
+    const int t = idx / NR, n = idx - t * NR;
+    const int pos = s_pos[t], iz = s_iz[t];
+    const int ix = pos <= a.Kx ? pos : pos - a.MX;
+    const double kx = a.alpha * ix, kz = a.beta * iz;
+    const double2 fx = sf[(0 * TM + t) * NR + n];
+    const double2 fy = sf[(1 * TM + t) * NR + n];
+    const double2 fz = sf[(2 * TM + t) * NR + n];
+    if (pos == 0 && iz == 0) {
+      sfb[t * NR + n] = fx;
+      sfw[t * NR + n] = fz;
+      continue;
+    }
+    const double k = sqrt(kx * kx + kz * kz), ik = 1.0 / k;
+    const double2 fa = make_double2((kx * fx.x + kz * fz.x) * ik, (kx * fx.y + kz * fz.y) * ik);
+    const double2 fb = make_double2((-kz * fx.x + kx * fz.x) * ik, (-kz * fx.y + kx * fz.y) * ik);
+    const double2 fta = make_double2(fa.y, -fa.x);  // -i f_a
+    sfb[t * NR + n] = fb;
+    const int P = n & 1;
+    srv[(t * 2 + P) * a.cv + n / 2] = fy;                  // f_v row n -> V_P
+    const int Pa = 1 - P;                                   // f~_a row n -> V_{1-P}
+    srv[(t * 2 + Pa) * a.cv + (Pa == 0 ? rv0 : rv1) + n / 2] = fta;
+  }
+  __syncthreads();
+  // phase D: apply the per-mode operators (FP64)
+  for (int idx = threadIdx.x; idx < TM * NY; idx += blockDim.x) {
+    const int t = idx / NY, n = idx - t * NY;
+    if (s_u[t] >= a.n_unique) continue;
+    const double* op = a.ops + (size_t)s_u[t] * a.op_stride;
+    const int Q = n & 1, row = n >> 1;
+    const bool mean = (s_pos[t] == 0 && s_iz[t] == 0);
+    // Helmholtz (b, or the mean u and w)
+    const int rb = Q == 0 ? a.rb0 : a.rb1;
+    const double* H = op + (Q == 0 ? a.off_h0 : a.off_h1) + (size_t)row * rb;
+    double2 accb = make_double2(0.0, 0.0), accw = accb;
+    for (int cidx = 0; cidx < rb; ++cidx) {
+      const double h = __ldg(H + cidx);
+      const double2 fb = sfb[t * NR + Q + 2 * cidx];
+      accb.x += h * fb.x;
+      accb.y += h * fb.y;
+      if (mean) {
+        const double2 fw = sfw[t * NR + Q + 2 * cidx];
+        accw.x += h * fw.x;
+        accw.y += h * fw.y;
+      }
+    }
+    sb[t * NY + n] = accb;
+    if (mean) {
+      sv[t * NY + n] = accw;
+      continue;
+    }
+    const double* V = op + (Q == 0 ? a.off_v0 : a.off_v1) + (size_t)row * a.cv;
+    const double2* r = srv + (t * 2 + Q) * a.cv;
+    double2 accv = make_double2(0.0, 0.0);
+    for (int cidx = 0; cidx < a.cv; ++cidx) {
+      const double vv = __ldg(V + cidx);
+      accv.x += vv * r[cidx].x;
+      accv.y += vv * r[cidx].y;
+    }
+    sv[t * NY + n] = accv;
+  }
+  __syncthreads();
+  // phase E: a = (i/k) D v, back-rotation, G = u_new - u, Hermitian output
+  double2* dst = out + (size_t)dir * 3 * Mm * NY;
+  for (int idx = threadIdx.x; idx < TM * NY; idx += blockDim.x) {
+    const int t = idx / NY, n = idx - t * NY;
+    if (s_u[t] >= a.n_unique) continue;
+    const int pos = s_pos[t], iz = s_iz[t];
+    double2 un, vn, wn;
+    if (pos == 0 && iz == 0) {
+      un = make_double2(sb[t * NY + n].x, 0.0);
+      wn = make_double2(sv[t * NY + n].x, 0.0);
+      vn = make_double2(0.0, 0.0);
+    } else {
+      const int ix = pos <= a.Kx ? pos : pos - a.MX;
+      const double kx = a.alpha * ix, kz = a.beta * iz;
+      const double k = sqrt(kx * kx + kz * kz), ik = 1.0 / k;
+      double2 dv = make_double2(0.0, 0.0);
+      for (int p = n + 1; p < NY; p += 2) {
+        const double2 vp = sv[t * NY + p];
+        dv.x += 2.0 * p * vp.x;
+        dv.y += 2.0 * p * vp.y;
+      }
+      if (n == 0) { dv.x *= 0.5; dv.y *= 0.5; }
+      const double2 an = make_double2(-dv.y * ik, dv.x * ik);  // (i/k) Dv
+      const double2 bn = sb[t * NY + n];
+      un = make_double2((kx * an.x - kz * bn.x) * ik, (kx * an.y - kz * bn.y) * ik);
+      wn = make_double2((kz * an.x + kx * bn.x) * ik, (kz * an.y + kx * bn.y) * ik);
+      vn = sv[t * NY + n];
+    }
+    const double2 res[3] = {un, vn, wn};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double2 d = sdu[(c * TM + t) * NY + n];
+      double2 g = make_double2(res[c].x - d.x, res[c].y - d.y);
+      if (pos == 0 && iz == 0) g.y = 0.0;
+      dst[((size_t)c * Mm + pos * MZ + iz) * NY + n] = g;
+      if (iz == 0 && pos != 0) {
+        dst[((size_t)c * Mm + (a.MX - pos) * MZ) * NY + n] = make_double2(g.x, -g.y);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ seeding
+struct SeedArgs {
+  int Mm, MX, MZ, Kx, NY;
+  double alpha, beta;
+};
+
+// (1 - y^2) T_n = T_n/2 - T_{n+2}/4 - T_{|n-2|}/4, applied in coefficient space
+__device__ void mul_bump(const double2* in, double2* out, int NY) {
+  for (int m = 0; m < NY; ++m) out[m] = make_double2(0.0, 0.0);
+  for (int n = 0; n < NY; ++n) {
+    const double2 a = in[n];
+    out[n].x += 0.5 * a.x; out[n].y += 0.5 * a.y;
+    if (n + 2 < NY) { out[n + 2].x -= 0.25 * a.x; out[n + 2].y -= 0.25 * a.y; }
+    const int q = n >= 2 ? n - 2 : 2 - n;
+    if (q < NY) { out[q].x -= 0.25 * a.x; out[q].y -= 0.25 * a.y; }
+  }
+}
+
+// one block per mode; the series are short, so one thread does the arithmetic
+// on shared-memory copies (3 NY complex values)
+__global__ void k_seed(const double2* ra, const double2* rb, const double2* rc, double2* U,
+                       SeedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = blockIdx.x;
+  if (m >= a.Mm || threadIdx.x != 0) return;
+  const int NY = a.NY;
+  double2* t1 = reinterpret_cast<double2*>(smem_raw);
+  double2* v = t1 + NY;
+  double2* eta = v + NY;
+  const int pos = m / a.MZ, iz = m - pos * a.MZ;
+  const int ix = pos <= a.Kx ? pos : pos - a.MX;
+  const double kx = a.alpha * ix, kz = a.beta * iz, k2 = kx * kx + kz * kz;
+  double2* Uu = U + (size_t)(0 * a.Mm + m) * NY;
+  double2* Uv = U + (size_t)(1 * a.Mm + m) * NY;
+  double2* Uw = U + (size_t)(2 * a.Mm + m) * NY;
+  if (pos == 0 && iz == 0) {
+    mul_bump(rb + (size_t)m * NY, v, NY);
+    mul_bump(rc + (size_t)m * NY, eta, NY);
+    for (int n = 0; n < NY; ++n) {
+      Uu[n] = make_double2(v[n].x, 0.0);
+      Uv[n] = make_double2(0.0, 0.0);
+      Uw[n] = make_double2(eta[n].x, 0.0);
+    }
+    return;
+  }
+  mul_bump(ra + (size_t)m * NY, t1, NY);
+  mul_bump(t1, v, NY);
+  mul_bump(rb + (size_t)m * NY, eta, NY);
+  // Dv by the backward recurrence c_n b_n = b_{n+2} + 2 (n+1) v_{n+1}
+  double2 bnext = make_double2(0.0, 0.0), bnext2 = make_double2(0.0, 0.0);  // b_{n+1}, b_{n+2}
+  for (int n = NY - 1; n >= 0; --n) {
+    double2 bn = make_double2(0.0, 0.0);
+    if (n + 1 < NY) {
+      bn.x = bnext2.x + 2.0 * (n + 1) * v[n + 1].x;
+      bn.y = bnext2.y + 2.0 * (n + 1) * v[n + 1].y;
+    }
+    if (n == 0) { bn.x *= 0.5; bn.y *= 0.5; }
+    t1[n] = bn;  // t1 now holds Dv
+    bnext2 = bnext;
+    bnext = bn;
+  }
+  const double ik2 = 1.0 / k2;
+  for (int n = 0; n < NY; ++n) {
+    const double2 dv = t1[n], e = eta[n];
+    // u = i (kx Dv - kz eta)/k^2, w = i (kz Dv + kx eta)/k^2
+    const double ur = kx * dv.x - kz * e.x, ui = kx * dv.y - kz * e.y;
+    const double wr = kz * dv.x + kx * e.x, wi = kz * dv.y + kx * e.y;
+    Uu[n] = make_double2(-ui * ik2, ur * ik2);
+    Uv[n] = v[n];
+    Uw[n] = make_double2(-wi * ik2, wr * ik2);
+  }
+}
+
+// ------------------------------------------------------------ vectors
+__global__ void k_axpby(double* out, double a, const double* x, double b, const double* y, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = a * x[i] + (y ? b * y[i] : 0.0);
+}
+
+__global__ void k_scale(double* x, double s, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] *= s;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? red[lane] : 0.0;
+  if (wid == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// weighted inner products of rows of V (k states) with w; partials [k][gridDim.x]
+__global__ void k_multi_inner(const double2* V, int k, size_t ncplx, const double2* w, int NY, int MZ,
+                              double* partials) {
+  const int i = blockIdx.y;
+  const double2* vi = V + (size_t)i * ncplx;
+  double acc = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ncplx; e += (size_t)gridDim.x * blockDim.x) {
+    const int iz = (int)((e / NY) % MZ);
+    const double2 a = vi[e], b = w[e];
+    const double d = a.x * b.x + a.y * b.y;
+    acc += iz == 0 ? d : 2.0 * d;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[(size_t)i * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void k_multi_axpy(const double* V, int k, size_t n, const double* h, double* w) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double acc = w[e];
+    for (int i = 0; i < k; ++i) acc -= h[i] * V[(size_t)i * n + e];
+    w[e] = acc;
+  }
+}
+
+__global__ void k_f64_to_f32(const double* a, float* b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+int grid_for(size_t n, int threads, int sms) {
+  size_t g = (n + threads - 1) / threads;
+  size_t cap = (size_t)sms * 8;
+  return (int)(g < cap ? (g == 0 ? 1 : g) : cap);
+}
+
+}  // namespace
+
+// ================================================================ launchers
+static size_t xz_smem_bytes(const sp_ctx* c, int esize, int rp, int cx) {
+  const int FS = c->MZ + 1, RS = 6 * FS;
+  size_t scr = (size_t)2 * cx * c->nx;
+  size_t zs = (size_t)21 * rp * c->nz;
+  if (zs > scr) scr = zs;
+  return (size_t)esize * 2 * ((size_t)c->nx + c->nz + (size_t)c->nx * RS + scr);
+}
+
+// pick the largest chunking that fits the shared-memory budget
+static bool xz_config(const sp_ctx* c, int esize, int* rp, int* cx, size_t* bytes) {
+  // prefer two resident blocks per SM (about 113 KB each), else one (up to 220 KB)
+  for (size_t budget : {(size_t)113 * 1024, (size_t)220 * 1024}) {
+  for (int r = 4; r >= 1; --r) {
+    int scr_c = 21 * r * c->nz;
+    int x = scr_c / (2 * c->nx);
+    if (x < 1) x = 1;
+    if (x > 6 * c->MZ) x = 6 * c->MZ;
+    size_t b = xz_smem_bytes(c, esize, r, x);
+    if (b <= budget) {
+      *rp = r;
+      *cx = x;
+      *bytes = b;
+      return true;
+    }
+  }
+  }
+  return false;
+}
+
+bool sp_xz_fits(sp_ctx* c) {
+  bool ok64 = xz_config(c, 8, &c->xz_rp64, &c->xz_cx64, &c->smem_xz64);
+  bool ok32 = xz_config(c, 4, &c->xz_rp32, &c->xz_cx32, &c->smem_xz32);
+  if (!ok64) c->smem_xz64 = 0;
+  return ok32;
+}
+
+cudaError_t launch_yinv(const sp_ctx* c, bool fp32, const double* in, void* out6, int n_dir,
+                        cudaStream_t st) {
+  YinvArgs a;
+  a.Mm = c->Mm; a.MZ = c->MZ; a.MX = c->MX; a.Kx = c->Kx; a.NY = c->NY; a.N = c->N; a.NH = c->NH;
+  a.alpha = c->alpha; a.beta = c->beta;
+  const int tiles = (c->Mm + kTileYinv - 1) / kTileYinv;
+  int jsplit = 1;
+  while (tiles * jsplit * n_dir < c->sm_count && jsplit < c->NH) ++jsplit;
+  a.jchunk = (c->NH + jsplit - 1) / jsplit;
+  dim3 grid(tiles, (c->NH + a.jchunk - 1) / a.jchunk, n_dir);
+  if (fp32) {
+    size_t sm = (size_t)3 * c->NY * kTileYinv * sizeof(C2<float>);
+    cudaFuncSetAttribute(k_yinv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_yinv<float><<<grid, kThreadsYinv, sm, st>>>(reinterpret_cast<const double2*>(in),
+                                                  reinterpret_cast<C2<float>*>(out6), c->Th_f, c->TDh_f, a);
+  } else {
+    size_t sm = (size_t)3 * c->NY * kTileYinv * sizeof(C2<double>);
+    cudaFuncSetAttribute(k_yinv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_yinv<double><<<grid, kThreadsYinv, sm, st>>>(reinterpret_cast<const double2*>(in),
+                                                   reinterpret_cast<C2<double>*>(out6), c->Th, c->TDh, a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+static cudaError_t launch_xz_t(const sp_ctx* c, const void* in6, void* out3, T* base, const C2<T>* twx,
+                               const C2<T>* twz, int rp, int cx, size_t smem, int n_dir, cudaStream_t st) {
+  XzArgs<T> a;
+  a.in6 = reinterpret_cast<const C2<T>*>(in6);
+  a.out3 = reinterpret_cast<C2<T>*>(out3);
+  a.base = base;
+  a.twx = twx;
+  a.twz = twz;
+  a.yv = c->yv;
+  a.px = c->px;
+  a.pz = c->pz;
+  a.nx = c->nx; a.nz = c->nz; a.NY = c->NY; a.Mm = c->Mm; a.MX = c->MX; a.MZ = c->MZ;
+  a.Kx = c->Kx; a.Kz = c->Kz;
+  a.rp = rp; a.cx = cx;
+  a.FS = c->MZ + 1;
+  a.RS = 6 * a.FS;
+  cudaFuncSetAttribute(k_xz<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(c->NY, n_dir);
+  k_xz<T, MODE><<<grid, kThreadsXZ, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, void* out3, int n_dir,
+                      cudaStream_t st) {
+  if (fp32) {
+    const C2<float>* tx = reinterpret_cast<const C2<float>*>(c->twx_f);
+    const C2<float>* tz = reinterpret_cast<const C2<float>*>(c->twz_f);
+    if (mode == XZ_TANGENT)
+      return launch_xz_t<float, XZ_TANGENT>(c, in6, out3, c->base32, tx, tz, c->xz_rp32, c->xz_cx32,
+                                            c->smem_xz32, n_dir, st);
+    return cudaErrorInvalidValue;  // the step and the base are always FP64
+  }
+  if (c->smem_xz64 == 0) return cudaErrorInvalidConfiguration;
+  const C2<double>* tx = reinterpret_cast<const C2<double>*>(c->twx);
+  const C2<double>* tz = reinterpret_cast<const C2<double>*>(c->twz);
+  switch (mode) {
+    case XZ_STEP:
+      return launch_xz_t<double, XZ_STEP>(c, in6, out3, nullptr, tx, tz, c->xz_rp64, c->xz_cx64,
+                                          c->smem_xz64, n_dir, st);
+    case XZ_TANGENT:
+      return launch_xz_t<double, XZ_TANGENT>(c, in6, out3, c->base64, tx, tz, c->xz_rp64, c->xz_cx64,
+                                             c->smem_xz64, n_dir, st);
+    default:
+      return launch_xz_t<double, XZ_BASE>(c, in6, out3, c->base64, tx, tz, c->xz_rp64, c->xz_cx64,
+                                          c->smem_xz64, n_dir, st);
+  }
+}
+
+static size_t solve_smem(const sp_ctx* c, int esize) {
+  const int TM = kTileSolve, NY = c->NY, NR = c->N - 1;
+  size_t vals = (size_t)3 * NY * TM * 2 * esize;
+  vals = (vals + 15) / 16 * 16;
+  size_t d = (size_t)16 * (3 * TM * NY + 3 * TM * NR + TM * 2 * c->cv + 2 * TM * NR + 2 * TM * NY);
+  return vals + d + 16;
+}
+
+cudaError_t launch_solve(const sp_ctx* c, bool fp32, const void* in3, const double* du, double* out,
+                         int n_dir, cudaStream_t st) {
+  SolveArgs a;
+  a.ops = c->ops;
+  a.Cfh_d = c->Cfh;
+  a.Cfh_f = c->Cfh_f;
+  a.n_unique = c->n_unique; a.Mm = c->Mm; a.MX = c->MX; a.MZ = c->MZ; a.Kx = c->Kx;
+  a.NY = c->NY; a.N = c->N; a.NH = c->NH;
+  a.cv = c->cv; a.rb0 = c->rb0; a.rb1 = c->rb1;
+  a.off_v0 = c->off_v0; a.off_v1 = c->off_v1; a.off_h0 = c->off_h0; a.off_h1 = c->off_h1;
+  a.op_stride = c->op_stride;
+  a.alpha = c->alpha; a.beta = c->beta; a.inv_dt = 1.0 / c->dt;
+  dim3 grid((c->n_unique + kTileSolve - 1) / kTileSolve, n_dir);
+  if (fp32) {
+    size_t sm = solve_smem(c, 4);
+    cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_solve<float><<<grid, kThreadsSolve, sm, st>>>(reinterpret_cast<const C2<float>*>(in3),
+                                                    reinterpret_cast<const double2*>(du),
+                                                    reinterpret_cast<double2*>(out), a);
+  } else {
+    size_t sm = solve_smem(c, 8);
+    cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_solve<double><<<grid, kThreadsSolve, sm, st>>>(reinterpret_cast<const C2<double>*>(in3),
+                                                     reinterpret_cast<const double2*>(du),
+                                                     reinterpret_cast<double2*>(out), a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_base_to_f32(const sp_ctx* c, cudaStream_t st) {
+  size_t n = (size_t)6 * c->NY * c->nx * c->nz;
+  k_f64_to_f32<<<grid_for(n, 256, c->sm_count), 256, 0, st>>>(c->base64, c->base32, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed(const sp_ctx* c, const double* ra, const double* rb, const double* rc, double* U,
+                        cudaStream_t st) {
+  SeedArgs a;
+  a.Mm = c->Mm; a.MX = c->MX; a.MZ = c->MZ; a.Kx = c->Kx; a.NY = c->NY;
+  a.alpha = c->alpha; a.beta = c->beta;
+  k_seed<<<c->Mm, 32, (size_t)3 * c->NY * sizeof(double2), st>>>(reinterpret_cast<const double2*>(ra),
+                                           reinterpret_cast<const double2*>(rb),
+                                           reinterpret_cast<const double2*>(rc),
+                                           reinterpret_cast<double2*>(U), a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(double* x, double s, size_t n, cudaStream_t st) {
+  k_scale<<<grid_for(n, 256, 152), 256, 0, st>>>(x, s, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(double* out, double a, const double* x, double b, const double* y, size_t n,
+                         cudaStream_t st) {
+  k_axpby<<<grid_for(n, 256, 152), 256, 0, st>>>(out, a, x, b, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_inner(const sp_ctx* c, const double* V, int k, const double* w, double* partials,
+                               int nblocks, cudaStream_t st) {
+  dim3 grid(nblocks, k);
+  k_multi_inner<<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(V), k, c->cplx_per_state,
+                                      reinterpret_cast<const double2*>(w), c->NY, c->MZ, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inner_partials(const sp_ctx* c, const double* a, const double* b, double* partials,
+                                  int nblocks, cudaStream_t st) {
+  return launch_multi_inner(c, a, 1, b, partials, nblocks, st);
+}
+
+cudaError_t launch_multi_axpy(const sp_ctx* c, const double* V, int k, const double* h, double* w,
+                              cudaStream_t st) {
+  k_multi_axpy<<<grid_for(c->state_len, 256, c->sm_count), 256, 0, st>>>(V, k, c->state_len, h, w);
+  return cudaGetLastError();
+}

@@ -1,0 +1,317 @@
+// Plan building: transform tables and the per-mode Stokes solution operators.
+//
+// Everything here runs once per context on the host and is uploaded to the
+// device; no step of the BEFE map itself runs on the host.
+//
+// The per-mode operators restate the Chebyshev-tau Stokes problem that one
+// BEFE step solves for every Fourier mode (Sec. 2, Eq. befe; Sec. 3.2: exact
+// direct inversions per mode, pressure through incompressibility satisfied to
+// machine accuracy). Rotating the wall-parallel velocity into the component
+// along the wavevector (a = (kx u + kz w)/k) and across it
+// (b = (-kz u + kx w)/k), the pressure only acts on a and v:
+//   (lam - nu D^2) a + i k p = f_a   (Chebyshev rows 0..N-2)
+//   (lam - nu D^2) v + D p   = f_v   (rows 0..N-2)
+//   i k a + D v = 0                  (every coefficient 0..N)
+//   a(+-1) = v(+-1) = 0
+//   (lam - nu D^2) b = f_b (rows 0..N-2),  b(+-1) = 0
+// with lam = 1/dt + nu k^2. Writing a = i a~ makes the coupled block real.
+// Even and odd Chebyshev degrees decouple: v of parity P couples with a~ and
+// p of parity 1-P. For each parity the real system is factored once and its
+// inverse, restricted to the momentum right-hand sides and to the v unknowns,
+// is stored (the matrix V_P); a follows from continuity, a = (i/k) D v.
+// b uses the restricted inverse H_Q of the Dirichlet Helmholtz tau problem.
+// The mean mode (0,0) uses H_Q with k = 0 for u and w.
+#include <cmath>
+#include <cstring>
+#include <thread>
+
+#include "sp_internal.h"
+
+namespace {
+
+// exact-where-possible cos(pi * k / N) for integer k
+double cospi_frac(long k, long N) {
+  long m = k % (2 * N);
+  if (m < 0) m += 2 * N;
+  if (m == 0) return 1.0;
+  if (m == N) return -1.0;
+  if (2 * m == N || 2 * m == 3 * N) return 0.0;
+  return std::cos(M_PI * (double)m / (double)N);
+}
+
+bool make_fft_plan(int n, FftPlan* p) {
+  p->n = n;
+  p->nst = 0;
+  int m = n;
+  while (m % 4 == 0) { p->radix[p->nst++] = 4; m /= 4; }
+  while (m % 3 == 0) { p->radix[p->nst++] = 3; m /= 3; }
+  while (m % 2 == 0) { p->radix[p->nst++] = 2; m /= 2; }
+  return m == 1 && p->nst <= 12;
+}
+
+// LU with partial pivoting, in place, row-major n x n. Returns false if singular.
+bool lu_factor(std::vector<double>& A, int n, std::vector<int>& piv) {
+  piv.resize(n);
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = std::fabs(A[(size_t)k * n + k]);
+    for (int i = k + 1; i < n; ++i) {
+      double v = std::fabs(A[(size_t)i * n + k]);
+      if (v > best) { best = v; p = i; }
+    }
+    if (best == 0.0) return false;
+    piv[k] = p;
+    if (p != k)
+      for (int j = 0; j < n; ++j) std::swap(A[(size_t)k * n + j], A[(size_t)p * n + j]);
+    double inv = 1.0 / A[(size_t)k * n + k];
+    for (int i = k + 1; i < n; ++i) {
+      double l = A[(size_t)i * n + k] * inv;
+      A[(size_t)i * n + k] = l;
+      if (l != 0.0)
+        for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
+    }
+  }
+  return true;
+}
+
+void lu_solve(const std::vector<double>& LU, int n, const std::vector<int>& piv, double* b) {
+  for (int k = 0; k < n; ++k) {
+    int p = piv[k];
+    if (p != k) std::swap(b[k], b[p]);
+  }
+  for (int i = 0; i < n; ++i) {
+    double s = b[i];
+    for (int j = 0; j < i; ++j) s -= LU[(size_t)i * n + j] * b[j];
+    b[i] = s;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int j = i + 1; j < n; ++j) s -= LU[(size_t)i * n + j] * b[j];
+    b[i] = s / LU[(size_t)i * n + i];
+  }
+}
+
+struct ChebOps {
+  int N;
+  std::vector<double> D, D2;  // (N+1)^2 row-major: (Du)_n = sum_m D[n][m] u_m
+  explicit ChebOps(int N_) : N(N_) {
+    int n1 = N + 1;
+    D.assign((size_t)n1 * n1, 0.0);
+    for (int n = 0; n < n1; ++n)
+      for (int p = n + 1; p < n1; ++p)
+        if ((p + n) & 1) D[(size_t)n * n1 + p] = 2.0 * p / (n == 0 ? 2.0 : 1.0);
+    D2.assign((size_t)n1 * n1, 0.0);
+    for (int i = 0; i < n1; ++i)
+      for (int k = 0; k < n1; ++k) {
+        double d = D[(size_t)i * n1 + k];
+        if (d == 0.0) continue;
+        for (int j = 0; j < n1; ++j) D2[(size_t)i * n1 + j] += d * D[(size_t)k * n1 + j];
+      }
+  }
+};
+
+// V_P: rows = v unknowns of parity P (increasing n), columns = [f_v rows of
+// parity P (n <= N-2), f~_a rows of parity 1-P (n <= N-2)].
+bool build_vop(const ChebOps& C, int P, double k, double lam, double nu, double* out) {
+  const int N = C.N, n1 = N + 1;
+  std::vector<int> vi, ai;
+  for (int n = 0; n <= N; ++n) ((n % 2 == P) ? vi : ai).push_back(n);
+  const int nv = (int)vi.size(), na = (int)ai.size();
+  const int nt = nv + 2 * na;  // v, a~, p (p has the parity of a~)
+  std::vector<int> iv(n1, -1), ia(n1, -1);
+  for (int i = 0; i < nv; ++i) iv[vi[i]] = i;
+  for (int i = 0; i < na; ++i) ia[ai[i]] = i;
+  auto col_v = [&](int n) { return iv[n]; };
+  auto col_a = [&](int n) { return nv + ia[n]; };
+  auto col_p = [&](int n) { return nv + na + ia[n]; };
+  std::vector<double> A((size_t)nt * nt, 0.0);
+  std::vector<int> rhs_rows;  // row index of each RHS column, in V_P column order
+  int r = 0;
+  std::vector<int> vrows, arows;
+  for (int n = 0; n <= N - 2; ++n) {
+    if (n % 2 == P) {  // v-momentum
+      for (int m : vi) A[(size_t)r * nt + col_v(m)] = (n == m ? lam : 0.0) - nu * C.D2[(size_t)n * n1 + m];
+      for (int m : ai) A[(size_t)r * nt + col_p(m)] = C.D[(size_t)n * n1 + m];
+      vrows.push_back(r++);
+    }
+  }
+  for (int n = 0; n <= N - 2; ++n) {
+    if (n % 2 != P) {  // a~-momentum: (lam - nu D^2) a~ + k p = f~_a
+      for (int m : ai) A[(size_t)r * nt + col_a(m)] = (n == m ? lam : 0.0) - nu * C.D2[(size_t)n * n1 + m];
+      A[(size_t)r * nt + col_p(n)] += k;
+      arows.push_back(r++);
+    }
+  }
+  for (int n = 0; n <= N; ++n) {
+    if (n % 2 != P) {  // continuity: -k a~_n + (D v)_n = 0
+      A[(size_t)r * nt + col_a(n)] = -k;
+      for (int m : vi) A[(size_t)r * nt + col_v(m)] = C.D[(size_t)n * n1 + m];
+      ++r;
+    }
+  }
+  for (int m : vi) A[(size_t)r * nt + col_v(m)] = 1.0;  // v(+1) = 0 (= v(-1) up to sign)
+  ++r;
+  for (int m : ai) A[(size_t)r * nt + col_a(m)] = 1.0;  // a(+1) = 0
+  ++r;
+  if (r != nt) return false;
+  std::vector<int> piv;
+  if (!lu_factor(A, nt, piv)) return false;
+  rhs_rows = vrows;
+  rhs_rows.insert(rhs_rows.end(), arows.begin(), arows.end());
+  const int ncol = (int)rhs_rows.size();
+  std::vector<double> b(nt);
+  for (int cidx = 0; cidx < ncol; ++cidx) {
+    std::fill(b.begin(), b.end(), 0.0);
+    b[rhs_rows[cidx]] = 1.0;
+    lu_solve(A, nt, piv, b.data());
+    for (int i = 0; i < nv; ++i) out[(size_t)i * ncol + cidx] = b[i];
+  }
+  return true;
+}
+
+// H_Q: rows = unknowns of parity Q, columns = momentum rows of parity Q (n <= N-2).
+bool build_hop(const ChebOps& C, int Q, double lam, double nu, double* out) {
+  const int N = C.N, n1 = N + 1;
+  std::vector<int> bi;
+  for (int n = Q; n <= N; n += 2) bi.push_back(n);
+  const int nb = (int)bi.size();
+  std::vector<double> A((size_t)nb * nb, 0.0);
+  std::vector<int> rows;
+  int r = 0;
+  for (int n = Q; n <= N - 2; n += 2) {
+    for (int i = 0; i < nb; ++i) {
+      int m = bi[i];
+      A[(size_t)r * nb + i] = (n == m ? lam : 0.0) - nu * C.D2[(size_t)n * n1 + m];
+    }
+    rows.push_back(r++);
+  }
+  for (int i = 0; i < nb; ++i) A[(size_t)r * nb + i] = 1.0;
+  ++r;
+  if (r != nb) return false;
+  std::vector<int> piv;
+  if (!lu_factor(A, nb, piv)) return false;
+  const int ncol = (int)rows.size();
+  std::vector<double> b(nb);
+  for (int cidx = 0; cidx < ncol; ++cidx) {
+    std::fill(b.begin(), b.end(), 0.0);
+    b[rows[cidx]] = 1.0;
+    lu_solve(A, nb, piv, b.data());
+    for (int i = 0; i < nb; ++i) out[(size_t)i * ncol + cidx] = b[i];
+  }
+  return true;
+}
+
+}  // namespace
+
+// unique mode u -> (pos, iz): positions 0..Kx keep every iz, negative ix skip iz = 0
+static inline void unique_mode(const sp_ctx* c, int u, int* pos, int* iz) {
+  int first = (c->Kx + 1) * c->MZ;
+  if (u < first) {
+    *pos = u / c->MZ;
+    *iz = u % c->MZ;
+  } else {
+    int v = u - first;
+    *pos = c->Kx + 1 + v / (c->MZ - 1);
+    *iz = 1 + v % (c->MZ - 1);
+  }
+}
+
+sp_status sp_build_plan(sp_ctx* c) {
+  const int N = c->N, n1 = N + 1, NH = c->NH;
+  // Chebyshev tables on the half grid j = 0..N/2
+  std::vector<double> Th((size_t)NH * n1), TDh((size_t)NH * n1), Cfh((size_t)n1 * NH);
+  for (int j = 0; j < NH; ++j) {
+    for (int n = 0; n < n1; ++n) {
+      Th[(size_t)j * n1 + n] = cospi_frac((long)j * n, N);
+      // T_n'(cos th) = n sin(n th) / sin(th); T_n'(1) = n^2
+      double d;
+      if (j == 0) d = (double)n * n;
+      else d = n * cospi_frac((long)N - 2L * j * n, 2L * N) / cospi_frac((long)N - 2L * j, 2L * N);
+      TDh[(size_t)j * n1 + n] = d;
+    }
+  }
+  for (int n = 0; n < n1; ++n) {
+    double cbn = (n == 0 || n == N) ? 2.0 : 1.0;
+    for (int j = 0; j < NH; ++j) {
+      double cbj = (j == 0) ? 2.0 : 1.0;  // j = N is not on the half grid
+      Cfh[(size_t)n * NH + j] = 2.0 / (N * cbn) * cospi_frac((long)j * n, N) / cbj;
+    }
+  }
+  // twiddles exp(-2 pi i k / n)
+  // twiddles exp(-2 pi i k / n); sin(pi m / N) = cos(pi (N - 2m) / (2N))
+  auto tw = [](int n) {
+    std::vector<double2> t(n);
+    for (int k = 0; k < n; ++k) {
+      t[k].x = cospi_frac(2L * k, n);
+      t[k].y = -cospi_frac((long)n - 4L * k, 2L * n);
+    }
+    return t;
+  };
+  std::vector<double2> twx = tw(c->nx), twz = tw(c->nz);
+  std::vector<double> yv(n1);
+  for (int j = 0; j < n1; ++j) yv[j] = cospi_frac(j, N);
+  if (!make_fft_plan(c->nx, &c->px) || !make_fft_plan(c->nz, &c->pz))
+    return sp_fail(c, SP_EINVAL, "Nx and Nz must be products of 2 and 3");
+
+  // per-mode operators
+  c->nv0 = N / 2 + 1;
+  c->nv1 = N / 2;
+  c->cv = N - 1;
+  c->rb0 = N / 2;
+  c->rb1 = N / 2 - 1;
+  c->off_v0 = 0;
+  c->off_v1 = c->off_v0 + c->nv0 * c->cv;
+  c->off_h0 = c->off_v1 + c->nv1 * c->cv;
+  c->off_h1 = c->off_h0 + c->nv0 * c->rb0;
+  c->op_stride = c->off_h1 + c->nv1 * c->rb1;
+  std::vector<double> ops((size_t)c->n_unique * c->op_stride, 0.0);
+  ChebOps C(N);
+  int nthreads = (int)std::thread::hardware_concurrency();
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 32) nthreads = 32;
+  std::vector<int> bad(nthreads, 0);
+  auto work = [&](int tid) {
+    for (int u = tid; u < c->n_unique; u += nthreads) {
+      int pos, iz;
+      unique_mode(c, u, &pos, &iz);
+      int ix = pos <= c->Kx ? pos : pos - c->MX;
+      double kx = c->alpha * ix, kz = c->beta * iz;
+      double k2 = kx * kx + kz * kz, k = std::sqrt(k2);
+      double lam = 1.0 / c->dt + c->nu * k2;
+      double* o = ops.data() + (size_t)u * c->op_stride;
+      bool ok = true;
+      if (u != 0) {
+        ok = ok && build_vop(C, 0, k, lam, c->nu, o + c->off_v0);
+        ok = ok && build_vop(C, 1, k, lam, c->nu, o + c->off_v1);
+      }
+      ok = ok && build_hop(C, 0, lam, c->nu, o + c->off_h0);
+      ok = ok && build_hop(C, 1, lam, c->nu, o + c->off_h1);
+      if (!ok) bad[tid] = 1;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 0; t < nthreads; ++t) th.emplace_back(work, t);
+  for (auto& t : th) t.join();
+  for (int b : bad)
+    if (b) return sp_fail(c, SP_EINVAL, "singular per-mode Stokes system");
+
+  // float copies
+  std::vector<float> Thf(Th.begin(), Th.end()), TDhf(TDh.begin(), TDh.end()),
+      Cfhf(Cfh.begin(), Cfh.end());
+  std::vector<float2> twxf(c->nx), twzf(c->nz);
+  for (int k = 0; k < c->nx; ++k) twxf[k] = make_float2((float)twx[k].x, (float)twx[k].y);
+  for (int k = 0; k < c->nz; ++k) twzf[k] = make_float2((float)twz[k].x, (float)twz[k].y);
+
+  auto up = [&](void** dst, const void* src, size_t bytes) -> bool {
+    if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
+    return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  bool ok = up((void**)&c->Th, Th.data(), Th.size() * 8) && up((void**)&c->TDh, TDh.data(), TDh.size() * 8) &&
+            up((void**)&c->Cfh, Cfh.data(), Cfh.size() * 8) && up((void**)&c->Th_f, Thf.data(), Thf.size() * 4) &&
+            up((void**)&c->TDh_f, TDhf.data(), TDhf.size() * 4) && up((void**)&c->Cfh_f, Cfhf.data(), Cfhf.size() * 4) &&
+            up((void**)&c->twx, twx.data(), twx.size() * 16) && up((void**)&c->twz, twz.data(), twz.size() * 16) &&
+            up((void**)&c->twx_f, twxf.data(), twxf.size() * 8) && up((void**)&c->twz_f, twzf.data(), twzf.size() * 8) &&
+            up((void**)&c->ops, ops.data(), ops.size() * 8) && up((void**)&c->yv, yv.data(), yv.size() * 8);
+  if (!ok) return sp_fail(c, SP_ENOMEM, "device allocation of plan tables failed");
+  return SP_OK;
+}

@@ -1,0 +1,139 @@
+// Internal declarations of the stokesprec library: the context, the complex
+// helper type and the kernel launchers shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "stokesprec.h"
+
+// ------------------------------------------------------------------ complex
+template <typename T>
+struct C2 {
+  T x, y;
+};
+
+template <typename T>
+__host__ __device__ inline C2<T> mk(T a, T b) {
+  C2<T> r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+template <typename T>
+__host__ __device__ inline C2<T> operator+(C2<T> a, C2<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T>
+__host__ __device__ inline C2<T> operator-(C2<T> a, C2<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T>
+__host__ __device__ inline C2<T> operator*(C2<T> a, C2<T> b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__host__ __device__ inline C2<T> scl(C2<T> a, T s) { return mk(a.x * s, a.y * s); }
+template <typename T>
+__host__ __device__ inline C2<T> conj2(C2<T> a) { return mk(a.x, -a.y); }
+// multiply by i*s (s = +1 or -1)
+template <typename T>
+__host__ __device__ inline C2<T> mul_is(C2<T> a, T s) { return mk(-s * a.y, s * a.x); }
+
+// ----------------------------------------------------------------- FFT plan
+// Mixed-radix (2, 3, 4) Stockham plan for one transform length.
+struct FftPlan {
+  int n;
+  int nst;
+  int radix[12];
+};
+
+// ------------------------------------------------------------------ context
+struct sp_ctx {
+  sp_config cfg;
+  int dev = 0;
+  int sm_count = 0;
+  int nx = 0, ny = 0, nz = 0;
+  int N = 0, NH = 0;             // Chebyshev degree, N/2 + 1
+  int Kx = 0, Kz = 0, MX = 0, MZ = 0, NY = 0, Mm = 0;
+  int n_unique = 0;              // modes solved: (Kx+1) MZ + Kx (MZ-1)
+  double alpha = 0, beta = 0, nu = 0, dt = 0;
+  size_t state_len = 0;          // doubles per state
+  size_t cplx_per_state = 0;
+  FftPlan px{}, pz{};
+  // per-mode solve operators: V0, V1, H0, H1 (row-major), FP64
+  int nv0 = 0, nv1 = 0, cv = 0;  // rows of V0 / V1, columns of both (N-1)
+  int rb0 = 0, rb1 = 0;          // columns of H0 / H1 (rows: nv0 / nv1)
+  int off_v0 = 0, off_v1 = 0, off_h0 = 0, off_h1 = 0, op_stride = 0;
+
+  // device tables
+  double *Th = nullptr, *TDh = nullptr, *Cfh = nullptr;
+  double* yv = nullptr;          // [NY] Gauss-Lobatto points cos(pi j / N)
+  float *Th_f = nullptr, *TDh_f = nullptr, *Cfh_f = nullptr;
+  double2 *twx = nullptr, *twz = nullptr;
+  float2 *twx_f = nullptr, *twz_f = nullptr;
+  double* ops = nullptr;
+  // device workspaces
+  void* ws6 = nullptr;           // [batch][6][NY][Mm] complex (double-sized)
+  void* ws3 = nullptr;           // [batch][3][NY][Mm] complex (double-sized)
+  double* base64 = nullptr;      // [6][NY][nx][nz]
+  float* base32 = nullptr;
+  double* U0 = nullptr;          // linearisation point
+  double* G0 = nullptr;          // G(U0)
+  double* tmp = nullptr;         // [batch] states
+  double* red = nullptr;         // reduction partials
+  double* red_host = nullptr;    // pinned
+  int red_blocks = 0;
+  int has_base = 0;
+  // sizes of shared memory per kernel (bytes)
+  size_t smem_xz64 = 0, smem_xz32 = 0;
+  int xz_rp64 = 1, xz_rp32 = 1;
+  int xz_cx64 = 1, xz_cx32 = 1;
+  std::string err;
+  // tracing: event pairs per stage, recorded while `trace` is on
+  bool trace = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> trace_ev[SP_NSTAGE];
+  std::vector<cudaEvent_t> ev_pool;
+  // Newton scratch
+  double* kry = nullptr;         // Krylov basis [max_krylov+1] states
+  int kry_cap = 0;
+};
+
+// run `launch` (returning cudaError_t) bracketed by trace events when tracing
+cudaError_t sp_traced(sp_ctx* c, int stage, cudaStream_t st, cudaError_t (*fn)(void*), void* arg);
+template <class F>
+cudaError_t traced(sp_ctx* c, int stage, cudaStream_t st, F&& f) {
+  return sp_traced(c, stage, st, [](void* p) -> cudaError_t { return (*static_cast<F*>(p))(); }, &f);
+}
+
+// status helpers
+sp_status sp_fail(sp_ctx* c, sp_status s, const std::string& msg);
+sp_status sp_cuda(sp_ctx* c, cudaError_t e, const char* what);
+
+// plan building (plan.cpp)
+sp_status sp_build_plan(sp_ctx* c);
+
+// shared-memory sizing of k_xz; false if even the FP32 variant cannot fit
+bool sp_xz_fits(sp_ctx* c);
+
+// kernel launchers (kernels.cu); all asynchronous on `st`
+enum XzMode { XZ_STEP = 0, XZ_TANGENT = 1, XZ_BASE = 2 };
+cudaError_t launch_yinv(const sp_ctx* c, bool fp32, const double* in, void* out6, int n_dir,
+                        cudaStream_t st);
+cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, void* out3,
+                      int n_dir, cudaStream_t st);
+cudaError_t launch_solve(const sp_ctx* c, bool fp32, const void* in3, const double* du,
+                         double* out, int n_dir, cudaStream_t st);
+cudaError_t launch_base_to_f32(const sp_ctx* c, cudaStream_t st);
+cudaError_t launch_seed(const sp_ctx* c, const double* ra, const double* rb, const double* rc,
+                        double* U, cudaStream_t st);
+cudaError_t launch_scale(double* x, double s, size_t n, cudaStream_t st);
+cudaError_t launch_axpby(double* out, double a, const double* x, double b, const double* y,
+                         size_t n, cudaStream_t st);
+cudaError_t launch_inner_partials(const sp_ctx* c, const double* a, const double* b,
+                                  double* partials, int nblocks, cudaStream_t st);
+// many inner products <V_i, w> for i < k in one pass: partials [k][nblocks]
+cudaError_t launch_multi_inner(const sp_ctx* c, const double* V, int k, const double* w,
+                               double* partials, int nblocks, cudaStream_t st);
+// w -= sum_i h_i V_i (h on device)
+cudaError_t launch_multi_axpy(const sp_ctx* c, const double* V, int k, const double* h,
+                              double* w, cudaStream_t st);
