@@ -130,6 +130,27 @@ sp_status sp_vjp(sp_ctx* ctx, const double* r, double* JTr, int n_dir, void* str
  * Needs sp_set_base. Synchronous (reads the norms on the host). */
 sp_status sp_jvp_fd(sp_ctx* ctx, const double* du, double* Jdu, int n_dir, void* stream);
 
+/* ---- tangent step without allocation ------------------------------------ */
+
+/* Jdu = G_U du for ONE direction, exactly as sp_jvp computes it, but with the
+ * intermediate fields kept in a fixed 8 MiB array that the library holds on
+ * every device it runs on, so this call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine). The paper has no counterpart: it
+ * is an interface for callers that cannot allocate device memory when they
+ * need a Jacobian action, for instance a process whose GPU memory is already
+ * committed to its own pool allocator, or a latency-critical loop where
+ * cudaMalloc/cudaFree would synchronise the device.
+ * Limit: 9 Ny MX MZ complex values of the transform type (16 bytes in FP64,
+ * 8 in mixed) must fit in 8 MiB (48 x 65 x 48 FP64 needs 4.6 MB; larger grids
+ * return SP_EINVAL). The context, its plan and the base (sp_set_base) are set
+ * up as for sp_jvp.
+ * The first call on each device looks up the array's device address; make
+ * that first call before any stream capture. All calls share the one array:
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it and must be serialised by the caller. Every intermediate value
+ * is written before it is read, so nothing has to be cleared between calls. */
+sp_status sp_jvp_static(sp_ctx* ctx, const double* du, double* Jdu, void* stream);
+
 /* ---- vector operations in the inner product above ---------------------- */
 
 /* out[i] = <a_i, b_i> for i < n (states back to back), FP64. Synchronous. */

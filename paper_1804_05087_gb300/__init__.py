@@ -68,6 +68,7 @@ def _load():
         "sp_jvp_fd": ([P, P, P, I, V], I),
         "sp_inner": ([P, P, P, I, ctypes.POINTER(D), V], I),
         "sp_newton_gmres": ([P, P, ctypes.POINTER(_NewtonOpts), ctypes.POINTER(_NewtonReport), V], I),
+        "sp_jvp_static": ([P, P, P, V], I),
         "sp_trace_enable": ([P, I], I),
         "sp_trace_read": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), I], I),
     }
@@ -83,7 +84,7 @@ _lib = _load()
 #: names every build must export (the declarations of include/stokesprec.h)
 EXPORTS = ("sp_create", "sp_destroy", "sp_last_error", "sp_state_len", "sp_dims", "sp_seed_state",
            "sp_step", "sp_set_base", "sp_jvp", "sp_vjp", "sp_jvp_fd", "sp_inner", "sp_newton_gmres",
-           "sp_trace_enable", "sp_trace_read")
+           "sp_trace_enable", "sp_trace_read", "sp_jvp_static")
 STAGES = ("k_yinv", "k_xz", "k_solve", "step", "vector")
 
 
@@ -182,6 +183,13 @@ class Context:
         pd, n = self._ptr(du)
         po, _ = self._ptr(out, n)
         self._check(_lib.sp_jvp(self._h, pd, po, n, _stream(stream)))
+        return out
+
+    def sp_jvp_static(self, du, out, stream=None):
+        """One tangent action that allocates nothing (see include/stokesprec.h)."""
+        pd, _ = self._ptr(du, 1)
+        po, _ = self._ptr(out, 1)
+        self._check(_lib.sp_jvp_static(self._h, pd, po, _stream(stream)))
         return out
 
     def sp_vjp(self, r, out, stream=None):
