@@ -125,6 +125,12 @@ sp_status sp_jvp(sp_ctx* ctx, const double* du, double* Jdu, int n_dir, void* st
  * above (the transpose of every stage, in reverse). Precision: cfg.prec. */
 sp_status sp_vjp(sp_ctx* ctx, const double* r, double* JTr, int n_dir, void* stream);
 
+/* The same adjoint in the plain Euclidean inner product of the stored real
+ * and imaginary parts (sum Re(conj(a) b), no w(iz) weights): JTg = G_U^T g.
+ * This is the vector-Jacobian product that reverse-mode automatic
+ * differentiation of complex tensors expects (torch.autograd). */
+sp_status sp_vjp_euclid(sp_ctx* ctx, const double* g, double* JTg, int n_dir, void* stream);
+
 /* Finite-difference action [G(U + eps du) - G(U)]/eps (Eq. finitediff) for
  * n_dir directions, FP64, with eps = 1e-7 (1 + |U|)/|du| per direction.
  * Needs sp_set_base. Synchronous (reads the norms on the host). */

@@ -69,6 +69,7 @@ def _load():
         "sp_inner": ([P, P, P, I, ctypes.POINTER(D), V], I),
         "sp_newton_gmres": ([P, P, ctypes.POINTER(_NewtonOpts), ctypes.POINTER(_NewtonReport), V], I),
         "sp_jvp_static": ([P, P, P, V], I),
+        "sp_vjp_euclid": ([P, P, P, I, V], I),
         "sp_trace_enable": ([P, I], I),
         "sp_trace_read": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), I], I),
     }
@@ -84,7 +85,7 @@ _lib = _load()
 #: names every build must export (the declarations of include/stokesprec.h)
 EXPORTS = ("sp_create", "sp_destroy", "sp_last_error", "sp_state_len", "sp_dims", "sp_seed_state",
            "sp_step", "sp_set_base", "sp_jvp", "sp_vjp", "sp_jvp_fd", "sp_inner", "sp_newton_gmres",
-           "sp_trace_enable", "sp_trace_read", "sp_jvp_static")
+           "sp_trace_enable", "sp_trace_read", "sp_jvp_static", "sp_vjp_euclid")
 STAGES = ("k_yinv", "k_xz", "k_solve", "step", "vector")
 
 
@@ -147,6 +148,8 @@ class Context:
             raise TypeError("expected a CUDA tensor")
         if t.dtype != torch.complex128 or not t.is_contiguous():
             raise TypeError("expected a contiguous complex128 tensor")
+        if t.is_conj() or t.is_neg():
+            raise TypeError("tensor carries a lazy conjugate/negative bit; call resolve_conj()/resolve_neg()")
         n = t.numel() * 2
         if n % self.state_len:
             raise ValueError(f"tensor size {t.numel()} is not a whole number of states")
@@ -198,6 +201,12 @@ class Context:
         self._check(_lib.sp_vjp(self._h, pr, po, n, _stream(stream)))
         return out
 
+    def sp_vjp_euclid(self, g, out, stream=None):
+        pg, n = self._ptr(g)
+        po, _ = self._ptr(out, n)
+        self._check(_lib.sp_vjp_euclid(self._h, pg, po, n, _stream(stream)))
+        return out
+
     def sp_jvp_fd(self, du, out, stream=None):
         pd, n = self._ptr(du)
         po, _ = self._ptr(out, n)
@@ -233,3 +242,41 @@ class Context:
         if st not in (0, 4):
             self._check(st)
         return rep
+
+
+class StokesStep(torch.autograd.Function):
+    """G = B_dt(U) - U as a differentiable function of the spectral state.
+
+    forward  -> sp_step (FP64); the linearisation point is set with sp_set_base.
+    backward -> sp_vjp_euclid: G_U^T applied to the incoming gradient (the
+                hand-written adjoint step, in the Euclidean inner product of
+                the stored real and imaginary parts that torch uses).
+    jvp      -> sp_jvp: the hand-written tangent step (forward-mode AD).
+    Usage: G = StokesStep.apply(U, ctx) with U a complex128 CUDA tensor.
+    """
+
+    @staticmethod
+    def forward(fctx, U, ctx):
+        G = ctx.zeros()
+        ctx.sp_step(U.detach().resolve_conj().resolve_neg().contiguous(), G)
+        fctx.sp = ctx
+        fctx.save_for_backward(U.detach().clone())
+        fctx.U_fw = U.detach().clone()
+        return G
+
+    @staticmethod
+    def backward(fctx, grad):
+        ctx = fctx.sp
+        (U,) = fctx.saved_tensors
+        ctx.sp_set_base(U)
+        out = ctx.zeros()
+        ctx.sp_vjp_euclid(grad.resolve_conj().resolve_neg().contiguous(), out)
+        return out, None
+
+    @staticmethod
+    def jvp(fctx, dU, _):
+        ctx = fctx.sp
+        ctx.sp_set_base(fctx.U_fw)
+        out = ctx.zeros()
+        ctx.sp_jvp(dU.resolve_conj().resolve_neg().contiguous(), out)
+        return out

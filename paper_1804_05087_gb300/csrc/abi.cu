@@ -249,9 +249,39 @@ extern "C" sp_status sp_jvp(sp_ctx* c, const double* du, double* Jdu, int n_dir,
   return SP_OK;
 }
 
+static sp_status vjp_impl(sp_ctx* c, const double* r, double* JTr, int n_dir, bool weighted, cudaStream_t st,
+                          const char* who) {
+  if (!c || !r || !JTr || n_dir < 0 || r == JTr) return sp_fail(c, SP_EINVAL, std::string(who) + ": bad arguments");
+  if (!c->has_base) return sp_fail(c, SP_EINVAL, std::string(who) + ": call sp_set_base first");
+  const bool f32 = c->cfg.prec == SP_MIXED;
+  for (int d0 = 0; d0 < n_dir; d0 += c->cfg.max_batch) {
+    const int nb = std::min(c->cfg.max_batch, n_dir - d0);
+    const double* rr = r + (size_t)d0 * c->state_len;
+    double* g = JTr + (size_t)d0 * c->state_len;
+    sp_status s;
+    if ((s = sp_cuda(c, traced(c, SP_STAGE_SOLVE, st,
+                               [&] { return launch_solve_adj(c, f32, rr, g, c->ws3, nb, weighted, st); }),
+                     "solve adjoint")) != SP_OK)
+      return s;
+    if ((s = sp_cuda(c, traced(c, SP_STAGE_XZ, st, [&] { return launch_xz(c, f32, XZ_ADJOINT, c->ws3, c->ws6, nb, st); }),
+                     "xz adjoint")) != SP_OK)
+      return s;
+    if ((s = sp_cuda(c, traced(c, SP_STAGE_YINV, st, [&] { return launch_yinv_adj(c, f32, c->ws6, g, nb, st); }),
+                     "yinv adjoint")) != SP_OK)
+      return s;
+    if ((s = sp_cuda(c, traced(c, SP_STAGE_VEC, st, [&] { return launch_finish_adj(c, rr, g, nb, weighted, st); }),
+                     "finish adjoint")) != SP_OK)
+      return s;
+  }
+  return SP_OK;
+}
+
 extern "C" sp_status sp_vjp(sp_ctx* c, const double* r, double* JTr, int n_dir, void* stream) {
-  (void)r; (void)JTr; (void)n_dir; (void)stream;
-  return sp_fail(c, SP_EINVAL, "sp_vjp: not built yet");
+  return vjp_impl(c, r, JTr, n_dir, true, (cudaStream_t)stream, "sp_vjp");
+}
+
+extern "C" sp_status sp_vjp_euclid(sp_ctx* c, const double* g, double* JTg, int n_dir, void* stream) {
+  return vjp_impl(c, g, JTg, n_dir, false, (cudaStream_t)stream, "sp_vjp_euclid");
 }
 
 extern "C" sp_status sp_inner(sp_ctx* c, const double* a, const double* b, int n, double* out_host, void* stream) {

@@ -210,8 +210,8 @@ __global__ void __launch_bounds__(kThreadsYinv) k_yinv(const double2* __restrict
 // -------------------------------------------------------------- k_xz
 template <typename T>
 struct XzArgs {
-  const C2<T>* in6;   // [dir][6][NY][Mm]
-  C2<T>* out3;        // [dir][3][NY][Mm]
+  const C2<T>* in6;   // [dir][NIN][NY][Mm]  (NIN = 6, or 3 for the adjoint)
+  C2<T>* out3;        // [dir][NOUT][NY][Mm] (NOUT = 3, or 6 for the adjoint)
   T* base;            // [6][NY][nx][nz] (read for the tangent, written for BASE)
   const C2<T>* twx;   // [nx] exp(-2 pi i k/nx)
   const C2<T>* twz;
@@ -222,8 +222,15 @@ struct XzArgs {
   int FS, RS;         // field and row strides of the plane buffer G
 };
 
+// MODE XZ_ADJOINT runs the transpose of the tangent's plane stage: the
+// transpose of the truncated forward FFT (an inverse FFT with the iz > 0 terms
+// halved and the 1/(Nx Nz) factor), the transposed product
+// (u* = Omega_tot x a, omega* = a x U_tot) and the transpose of the inverse
+// FFT (a forward FFT weighted by 1 for iz = 0 and 2 for iz > 0).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
+  constexpr int NIN = MODE == XZ_ADJOINT ? 3 : 6;
+  constexpr int NOUT = MODE == XZ_ADJOINT ? 6 : 3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* stwx = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* stwz = stwx + a.nx;
@@ -238,11 +245,12 @@ __global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
   __syncthreads();
   const C2<T> zero = mk((T)0, (T)0);
   const size_t planeMm = (size_t)a.NY * a.Mm;
-  const C2<T>* in6 = a.in6 + (size_t)dir * 6 * planeMm + (size_t)j * a.Mm;
+  const C2<T>* in6 = a.in6 + (size_t)dir * NIN * planeMm + (size_t)j * a.Mm;
+  const T inv_nxnz = (T)(1.0 / ((double)nx * (double)nz));
 
   // ---- phase 1: inverse FFT along x of every (field, iz) column
   {
-    const int ncol = 6 * MZ;
+    const int ncol = NIN * MZ;
     for (int c0 = 0; c0 < ncol; c0 += a.cx) {
       const int nb = min(a.cx, ncol - c0);
       auto load = [&](int b, int e) -> C2<T> {
@@ -252,7 +260,9 @@ __global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
         if (e <= Kx) pos = e;
         else if (e >= nx - Kx) pos = e - nx + a.MX;
         else return zero;
-        return ld_c2(in6 + (size_t)f * planeMm + pos * MZ + iz);
+        const C2<T> v = ld_c2(in6 + (size_t)f * planeMm + pos * MZ + iz);
+        if (MODE == XZ_ADJOINT) return scl(v, iz == 0 ? inv_nxnz : (T)0.5 * inv_nxnz);
+        return v;
       };
       auto store = [&](int b, int e, C2<T> v) {
         const int col = c0 + b;
@@ -269,14 +279,14 @@ __global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
   C2<T>* P0 = S;
   C2<T>* P1 = S + (size_t)6 * rp * nz;
   C2<T>* Q = S + (size_t)12 * rp * nz;
-  C2<T>* R = S + (size_t)18 * rp * nz;
+  C2<T>* R = S + (size_t)18 * rp * nz;  // 6 rp nz (the adjoint writes six fields)
   const size_t nxz = (size_t)nx * nz;
   for (int q0 = 0; q0 < nx / 2; q0 += rp) {
     const int nq = min(rp, nx / 2 - q0);
     {
-      const int nb = 6 * nq;
+      const int nb = NIN * nq;
       auto load = [&](int b, int e) -> C2<T> {
-        const int qq = b / 6, f = b - qq * 6;
+        const int qq = b / NIN, f = b - qq * NIN;
         const int x0 = 2 * (q0 + qq);
         const C2<T>* g0 = G + x0 * RS + f * FS;
         const C2<T>* g1 = g0 + RS;
@@ -296,32 +306,32 @@ __global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
     }
     // pointwise products on the two rows of each pair
     {
-      const int nb6 = 6 * nq, nb3 = 3 * nq;
+      const int nbi = NIN * nq, nbo = NOUT * nq;
       for (int it = threadIdx.x; it < nq * nz; it += blockDim.x) {
         const int qq = it / nz, k = it - qq * nz;
         const int x0 = 2 * (q0 + qq);
-        C2<T> fv[6];
+        C2<T> fv[NIN];
 #pragma unroll
-        for (int f = 0; f < 6; ++f) fv[f] = Q[k * nb6 + qq * 6 + f];
-        T res[2][3];
+        for (int f = 0; f < NIN; ++f) fv[f] = Q[k * nbi + qq * NIN + f];
+        T res[2][NOUT];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           T F[6];
 #pragma unroll
-          for (int f = 0; f < 6; ++f) F[f] = r ? fv[f].y : fv[f].x;
+          for (int f = 0; f < NIN; ++f) F[f] = r ? fv[f].y : fv[f].x;
           const size_t gidx = (size_t)j * nxz + (size_t)(x0 + r) * nz + k;
-          if (MODE == XZ_BASE) {
+          if constexpr (MODE == XZ_BASE) {
             F[0] += yj;
             F[5] -= (T)1;
 #pragma unroll
             for (int f = 0; f < 6; ++f) a.base[(size_t)f * a.NY * nxz + gidx] = F[f];
-          } else if (MODE == XZ_STEP) {
+          } else if constexpr (MODE == XZ_STEP) {
             const T U0 = F[0] + yj, U1 = F[1], U2 = F[2];
             const T O0 = F[3], O1 = F[4], O2 = F[5] - (T)1;
             res[r][0] = U1 * O2 - U2 * O1;
             res[r][1] = U2 * O0 - U0 * O2;
             res[r][2] = U0 * O1 - U1 * O0;
-          } else {
+          } else if constexpr (MODE == XZ_TANGENT) {
             T B[6];
 #pragma unroll
             for (int f = 0; f < 6; ++f) B[f] = a.base[(size_t)f * a.NY * nxz + gidx];
@@ -329,24 +339,35 @@ __global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
             res[r][0] = (B[1] * F[5] - B[2] * F[4]) + (F[1] * B[5] - F[2] * B[4]);
             res[r][1] = (B[2] * F[3] - B[0] * F[5]) + (F[2] * B[3] - F[0] * B[5]);
             res[r][2] = (B[0] * F[4] - B[1] * F[3]) + (F[0] * B[4] - F[1] * B[3]);
+          } else {
+            T B[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) B[f] = a.base[(size_t)f * a.NY * nxz + gidx];
+            // transposed product: u* = Omega_tot x a, omega* = a x U_tot
+            res[r][0] = B[4] * F[2] - B[5] * F[1];
+            res[r][1] = B[5] * F[0] - B[3] * F[2];
+            res[r][2] = B[3] * F[1] - B[4] * F[0];
+            res[r][3] = F[1] * B[2] - F[2] * B[1];
+            res[r][4] = F[2] * B[0] - F[0] * B[2];
+            res[r][5] = F[0] * B[1] - F[1] * B[0];
           }
         }
-        if (MODE != XZ_BASE) {
+        if constexpr (MODE != XZ_BASE) {
 #pragma unroll
-          for (int cc = 0; cc < 3; ++cc) R[k * nb3 + qq * 3 + cc] = mk(res[0][cc], res[1][cc]);
+          for (int cc = 0; cc < NOUT; ++cc) R[k * nbo + qq * NOUT + cc] = mk(res[0][cc], res[1][cc]);
         }
       }
       __syncthreads();
     }
     if (MODE != XZ_BASE) {
-      const int nb = 3 * nq;
+      const int nb = NOUT * nq;
       auto load = [&](int b, int e) -> C2<T> { return R[e * nb + b]; };
       auto store = [&](int b, int e, C2<T> v) { Q[e * nb + b] = v; };
       fft_batch<T>(a.pz, nb, stwz, (T)-1, P0, P1, load, store);
       // separate the two real rows: A(k) = (X(k) + conj X(-k))/2, B(k) = (X(k) - conj X(-k))/(2i)
       for (int it = threadIdx.x; it < nb * MZ; it += blockDim.x) {
         const int iz = it / nb, b = it - iz * nb;
-        const int qq = b / 3, cc = b - qq * 3;
+        const int qq = b / NOUT, cc = b - qq * NOUT;
         const int x0 = 2 * (q0 + qq);
         const C2<T> X = Q[iz * nb + b];
         const C2<T> Xm = Q[((nz - iz) % nz) * nb + b];
@@ -362,9 +383,8 @@ __global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
 
   // ---- phase 3: forward FFT along x, keep the 2/3-rule modes
   {
-    const T inv = (T)(1.0 / ((double)nx * (double)nz));
-    C2<T>* out = a.out3 + (size_t)dir * 3 * planeMm + (size_t)j * a.Mm;
-    const int ncol = 3 * MZ;
+    C2<T>* out = a.out3 + (size_t)dir * NOUT * planeMm + (size_t)j * a.Mm;
+    const int ncol = NOUT * MZ;
     for (int c0 = 0; c0 < ncol; c0 += a.cx) {
       const int nb = min(a.cx, ncol - c0);
       auto load = [&](int b, int e) -> C2<T> {
@@ -379,7 +399,8 @@ __global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
         else return;
         const int col = c0 + b;
         const int cc = col / MZ, iz = col - cc * MZ;
-        out[(size_t)cc * planeMm + pos * MZ + iz] = scl(v, inv);
+        const T sc = MODE == XZ_ADJOINT ? (iz == 0 ? (T)1 : (T)2) : inv_nxnz;
+        out[(size_t)cc * planeMm + pos * MZ + iz] = scl(v, sc);
       };
       fft_batch<T>(a.px, nb, stwx, (T)-1, S, S + (size_t)a.cx * nx, load, store);
     }
@@ -614,6 +635,327 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict
   }
 }
 
+
+// ------------------------------------------------------------ adjoint
+// The adjoint of the tangent in the weighted inner product <a,b> =
+// sum w(iz) Re(conj a b) is J* = W^-1 J^T W with J^T the plain transpose.
+// The tangent is J = P S (1/dt + M) P - P (P: Hermitian projection, S: the
+// per-mode solve, M: curl, values, plane stage, Chebyshev coefficients), so
+// J^T r' = P (1/dt + M^T) S^T P r' - P r' with r' = W r. The chain below
+// evaluates it stage by stage in reverse order.
+
+// k_solve_adj: r' = P W r, f* = S^T r' (transposed per-mode operators),
+// out = f*/dt (boundary layout) and vals = Cf^T f* (values at the
+// Gauss-Lobatto points, plane-major) for every stored mode.
+template <typename T>
+__global__ void __launch_bounds__(kThreadsSolve) k_solve_adj(const double2* __restrict__ r,
+                                                             double2* __restrict__ out,
+                                                             C2<T>* __restrict__ vals, SolveArgs a,
+                                                             int weighted) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int TM = kTileSolve;
+  const int NY = a.NY, N = a.N, NH = a.NH, Mm = a.Mm, MZ = a.MZ;
+  const int NR = N - 1;
+  double2* sg = reinterpret_cast<double2*>(smem_raw);  // [3][TM][NY] r' (u, v, w)
+  double2* sga = sg + 3 * TM * NY;                     // [TM][NY] along-k part
+  double2* sgb = sga + TM * NY;                        // [TM][NY] across-k part
+  double2* sva = sgb + TM * NY;                        // [TM][NY] v* = gv + D^T(-i ga/k)
+  double2* srv = sva + TM * NY;                        // [TM][2][cv] V_P^T v*
+  double2* sfb = srv + TM * 2 * a.cv;                  // [TM][NR] H^T gb (or H^T gu)
+  double2* sfw = sfb + TM * NR;                        // [TM][NR] H^T gw (mean mode)
+  double2* sf = sfw + TM * NR;                         // [3][TM][NR] f*
+  __shared__ int s_pos[kTileSolve], s_iz[kTileSolve], s_u[kTileSolve];
+  __shared__ double s_kx[kTileSolve], s_kz[kTileSolve], s_ik[kTileSolve];
+  const int u0 = blockIdx.x * TM;
+  const int dir = blockIdx.y;
+  if (threadIdx.x < TM) {
+    const int u = u0 + threadIdx.x;
+    int pos = 0, iz = 0;
+    if (u < a.n_unique) unique_to_mode(u, a.Kx, MZ, &pos, &iz);
+    s_pos[threadIdx.x] = pos;
+    s_iz[threadIdx.x] = iz;
+    s_u[threadIdx.x] = u;
+    const int ix = pos <= a.Kx ? pos : pos - a.MX;
+    const double kx = a.alpha * ix, kz = a.beta * iz;
+    const double k = sqrt(kx * kx + kz * kz);
+    s_kx[threadIdx.x] = kx;
+    s_kz[threadIdx.x] = kz;
+    s_ik[threadIdx.x] = k > 0 ? 1.0 / k : 0.0;
+  }
+  __syncthreads();
+  const double2* rsrc = r + (size_t)dir * 3 * Mm * NY;
+  // r' = P W r
+  for (int idx = threadIdx.x; idx < 3 * TM * NY; idx += blockDim.x) {
+    const int n = idx % NY;
+    const int t = (idx / NY) % TM;
+    const int c = idx / (NY * TM);
+    double2 v = make_double2(0.0, 0.0);
+    if (s_u[t] < a.n_unique) {
+      const int pos = s_pos[t], iz = s_iz[t];
+      v = __ldg(rsrc + ((size_t)c * Mm + pos * MZ + iz) * NY + n);
+      if (iz == 0) {
+        const int mpos = pos == 0 ? 0 : a.MX - pos;
+        const double2 w = __ldg(rsrc + ((size_t)c * Mm + mpos * MZ) * NY + n);
+        v = make_double2(0.5 * (v.x + w.x), 0.5 * (v.y - w.y));
+      } else if (weighted) {
+        v = make_double2(2.0 * v.x, 2.0 * v.y);
+      }
+    }
+    sg[(c * TM + t) * NY + n] = v;
+  }
+  __syncthreads();
+  // rotation^T: ga = (kx gu + kz gw)/k, gb = (-kz gu + kx gw)/k
+  for (int idx = threadIdx.x; idx < TM * NY; idx += blockDim.x) {
+    const int t = idx / NY, n = idx - t * NY;
+    const double2 gu = sg[(0 * TM + t) * NY + n], gw = sg[(2 * TM + t) * NY + n];
+    if (s_pos[t] == 0 && s_iz[t] == 0) {
+      sga[idx] = gu;
+      sgb[idx] = gw;
+      continue;
+    }
+    const double kx = s_kx[t], kz = s_kz[t], ik = s_ik[t];
+    sga[idx] = make_double2((kx * gu.x + kz * gw.x) * ik, (kx * gu.y + kz * gw.y) * ik);
+    sgb[idx] = make_double2((-kz * gu.x + kx * gw.x) * ik, (-kz * gu.y + kx * gw.y) * ik);
+  }
+  __syncthreads();
+  // a = (i/k) D v  =>  v* = gv + D^T (-i ga / k); (D^T x)_n = sum_{m<n, m+n odd} (2n/c_m) x_m
+  for (int idx = threadIdx.x; idx < TM * NY; idx += blockDim.x) {
+    const int t = idx / NY, n = idx - t * NY;
+    const double2 gv = sg[(1 * TM + t) * NY + n];
+    if (s_pos[t] == 0 && s_iz[t] == 0) {
+      sva[idx] = make_double2(0.0, 0.0);
+      continue;
+    }
+    double2 acc = make_double2(0.0, 0.0);
+    for (int m = (n & 1) ? 0 : 1; m < n; m += 2) {
+      const double2 x = sga[t * NY + m];
+      const double cm = m == 0 ? 0.5 : 1.0;
+      acc.x += cm * x.x;
+      acc.y += cm * x.y;
+    }
+    const double s = 2.0 * n * s_ik[t];
+    // -i ga / k: (x + i y) * (-i) = y - i x
+    sva[idx] = make_double2(gv.x + s * acc.y, gv.y - s * acc.x);
+  }
+  __syncthreads();
+  // V_P^T v* (columns of V_P) and H_Q^T gb
+  for (int idx = threadIdx.x; idx < TM * 2 * a.cv; idx += blockDim.x) {
+    const int t = idx / (2 * a.cv), rem = idx - t * 2 * a.cv;
+    const int P = rem / a.cv, col = rem - P * a.cv;
+    if (s_u[t] >= a.n_unique || (s_pos[t] == 0 && s_iz[t] == 0)) {
+      srv[idx] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const double* V = a.ops + (size_t)s_u[t] * a.op_stride + (P == 0 ? a.off_v0 : a.off_v1);
+    const int nv = P == 0 ? N / 2 + 1 : N / 2;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int row = 0; row < nv; ++row) {
+      const double vv = __ldg(V + (size_t)row * a.cv + col);
+      const double2 x = sva[t * NY + P + 2 * row];
+      acc.x += vv * x.x;
+      acc.y += vv * x.y;
+    }
+    srv[idx] = acc;
+  }
+  for (int idx = threadIdx.x; idx < TM * NR; idx += blockDim.x) {
+    const int t = idx / NR, n = idx - t * NR;  // momentum row n
+    if (s_u[t] >= a.n_unique) continue;
+    const int Q = n & 1, col = n >> 1;
+    const int rb = Q == 0 ? a.rb0 : a.rb1;
+    const int nrow = Q == 0 ? N / 2 + 1 : N / 2;
+    const double* H = a.ops + (size_t)s_u[t] * a.op_stride + (Q == 0 ? a.off_h0 : a.off_h1);
+    const bool mean = s_pos[t] == 0 && s_iz[t] == 0;
+    double2 accb = make_double2(0.0, 0.0), accw = accb;
+    for (int row = 0; row < nrow; ++row) {
+      const double h = __ldg(H + (size_t)row * rb + col);
+      const double2 gb = sgb[t * NY + Q + 2 * row];
+      accb.x += h * gb.x;
+      accb.y += h * gb.y;
+      if (mean) {
+        // sga holds gu and sgb holds gw for the mean mode
+        const double2 gu = sga[t * NY + Q + 2 * row];
+        accw.x += h * gu.x;
+        accw.y += h * gu.y;
+      }
+    }
+    sfb[idx] = accb;
+    sfw[idx] = accw;
+  }
+  __syncthreads();
+  // f* per component, rows 0..N-2
+  const int rv0 = N / 2, rv1 = N / 2 - 1;
+  for (int idx = threadIdx.x; idx < TM * NR; idx += blockDim.x) {
+    const int t = idx / NR, n = idx - t * NR;
+    double2 fx, fy, fz;
+    if (s_pos[t] == 0 && s_iz[t] == 0) {
+      fx = make_double2(sfw[idx].x, 0.0);  // H^T gu
+      fz = make_double2(sfb[idx].x, 0.0);  // H^T gw
+      fy = make_double2(0.0, 0.0);
+    } else {
+      const int P = n & 1, Pa = 1 - P;
+      fy = srv[(t * 2 + P) * a.cv + (n >> 1)];
+      const double2 fta = srv[(t * 2 + Pa) * a.cv + (Pa == 0 ? rv0 : rv1) + (n >> 1)];
+      const double2 fa = make_double2(-fta.y, fta.x);  // f_a* = i f~_a*
+      const double2 fb = sfb[idx];
+      const double kx = s_kx[t], kz = s_kz[t], ik = s_ik[t];
+      fx = make_double2((kx * fa.x - kz * fb.x) * ik, (kx * fa.y - kz * fb.y) * ik);
+      fz = make_double2((kz * fa.x + kx * fb.x) * ik, (kz * fa.y + kx * fb.y) * ik);
+    }
+    sf[(0 * TM + t) * NR + n] = fx;
+    sf[(1 * TM + t) * NR + n] = fy;
+    sf[(2 * TM + t) * NR + n] = fz;
+  }
+  __syncthreads();
+  // out = f*/dt (boundary layout, rows N-1, N zero), mirrored for iz = 0
+  double2* dst = out + (size_t)dir * 3 * Mm * NY;
+  for (int idx = threadIdx.x; idx < 3 * TM * NY; idx += blockDim.x) {
+    const int n = idx % NY;
+    const int t = (idx / NY) % TM;
+    const int c = idx / (NY * TM);
+    if (s_u[t] >= a.n_unique) continue;
+    const int pos = s_pos[t], iz = s_iz[t];
+    double2 v = make_double2(0.0, 0.0);
+    if (n < NR) {
+      const double2 f = sf[(c * TM + t) * NR + n];
+      v = make_double2(f.x * a.inv_dt, f.y * a.inv_dt);
+    }
+    dst[((size_t)c * Mm + pos * MZ + iz) * NY + n] = v;
+    if (iz == 0 && pos != 0) dst[((size_t)c * Mm + (a.MX - pos) * MZ) * NY + n] = make_double2(v.x, -v.y);
+  }
+  // vals = Cf^T f*: sum_n Cf[n][j] f*_n with Cf[n][N-j] = (-1)^n Cf[n][j]
+  C2<T>* vdst = vals + (size_t)dir * 3 * NY * Mm;
+  for (int idx = threadIdx.x; idx < 3 * TM * NH; idx += blockDim.x) {
+    const int t = idx % TM;
+    const int jh = (idx / TM) % NH;
+    const int c = idx / (TM * NH);
+    if (s_u[t] >= a.n_unique) continue;
+    C2<T> E = mk((T)0, (T)0), O = E;
+    const double2* f = sf + (c * TM + t) * NR;
+    for (int n = 0; n < NR; ++n) {
+      const T cf = sizeof(T) == 8 ? (T)a.Cfh_d[(size_t)n * NH + jh] : (T)a.Cfh_f[(size_t)n * NH + jh];
+      const C2<T> fv = mk((T)f[n].x, (T)f[n].y);
+      if (n & 1) O = O + scl(fv, cf);
+      else E = E + scl(fv, cf);
+    }
+    const int pos = s_pos[t], iz = s_iz[t];
+    const int m = pos * MZ + iz, mm = (a.MX - pos) * MZ;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int j = side == 0 ? jh : N - jh;
+      if (side == 1 && j == jh) break;
+      const C2<T> v = side == 0 ? E + O : E - O;
+      vdst[((size_t)c * NY + j) * Mm + m] = v;
+      if (iz == 0 && pos != 0) vdst[((size_t)c * NY + j) * Mm + mm] = conj2(v);
+    }
+  }
+}
+
+// k_yinv_adj: the transpose of k_yinv. In value space the curl gives
+//   u* += gu - i kz gy, v* += gv + i kz gx - i kx gz, w* += gw + i kx gy,
+//   (Du)* = -gz, (Dw)* = gx;
+// then coefficients: x*_n = sum_j T_n(y_j) x*_j + sum_j T_n'(y_j) (Dx)*_j,
+// added to `out` (which already holds f*/dt).
+template <typename T>
+__global__ void __launch_bounds__(kThreadsYinv) k_yinv_adj(const C2<T>* __restrict__ in,
+                                                          double2* __restrict__ out,
+                                                          const T* __restrict__ Th,
+                                                          const T* __restrict__ TDh, YinvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int TM = kTileYinv;
+  const int NY = a.NY, Mm = a.Mm, N = a.N, NH = a.NH;
+  C2<T>* s5 = reinterpret_cast<C2<T>*>(smem_raw);  // [5][NY][TM]: u*, v*, w*, Du*, Dw* values
+  const int m0 = blockIdx.x * TM;
+  const int dir = blockIdx.z;
+  const C2<T>* src = in + (size_t)dir * 6 * NY * Mm;
+  for (int idx = threadIdx.x; idx < TM * NY; idx += blockDim.x) {
+    const int t = idx % TM, j = idx / TM;
+    const int m = m0 + t;
+    C2<T> g[6];
+    if (m < Mm) {
+#pragma unroll
+      for (int f = 0; f < 6; ++f) g[f] = ld_c2(src + ((size_t)f * NY + j) * Mm + m);
+    } else {
+#pragma unroll
+      for (int f = 0; f < 6; ++f) g[f] = mk((T)0, (T)0);
+    }
+    const int pos = m / a.MZ, iz = m - pos * a.MZ;
+    const int ix = pos <= a.Kx ? pos : pos - a.MX;
+    const T kx = (T)(a.alpha * ix), kz = (T)(a.beta * iz);
+    s5[(0 * NY + j) * TM + t] = g[0] - mul_is(g[4], kz);
+    s5[(1 * NY + j) * TM + t] = g[1] + mul_is(g[3], kz) - mul_is(g[5], kx);
+    s5[(2 * NY + j) * TM + t] = g[2] + mul_is(g[4], kx);
+    s5[(3 * NY + j) * TM + t] = mk(-g[5].x, -g[5].y);
+    s5[(4 * NY + j) * TM + t] = g[3];
+  }
+  __syncthreads();
+  double2* dst = out + (size_t)dir * 3 * Mm * NY;
+  for (int idx = threadIdx.x; idx < TM * NY; idx += blockDim.x) {
+    const int t = idx % TM, n = idx / TM;
+    const int m = m0 + t;
+    if (m >= Mm) continue;
+    const T sgT = (n & 1) ? (T)-1 : (T)1;  // T_n(y_{N-j}) = (-1)^n T_n(y_j)
+    const T sgD = -sgT;                    // T_n'(y_{N-j}) = (-1)^(n+1) T_n'(y_j)
+    C2<T> au = mk((T)0, (T)0), av = au, aw = au;
+    for (int jh = 0; jh < NH; ++jh) {
+      const T tv = Th[(size_t)jh * NY + n], dv = TDh[(size_t)jh * NY + n];
+      const int j2 = N - jh;
+      const bool mid = (j2 == jh);
+      C2<T> xu = s5[(0 * NY + jh) * TM + t], xv = s5[(1 * NY + jh) * TM + t], xw = s5[(2 * NY + jh) * TM + t];
+      C2<T> xdu = s5[(3 * NY + jh) * TM + t], xdw = s5[(4 * NY + jh) * TM + t];
+      if (!mid) {
+        xu = xu + scl(s5[(0 * NY + j2) * TM + t], sgT);
+        xv = xv + scl(s5[(1 * NY + j2) * TM + t], sgT);
+        xw = xw + scl(s5[(2 * NY + j2) * TM + t], sgT);
+        xdu = xdu + scl(s5[(3 * NY + j2) * TM + t], sgD);
+        xdw = xdw + scl(s5[(4 * NY + j2) * TM + t], sgD);
+      }
+      au = au + scl(xu, tv) + scl(xdu, dv);
+      av = av + scl(xv, tv);
+      aw = aw + scl(xw, tv) + scl(xdw, dv);
+    }
+    const C2<T> res[3] = {au, av, aw};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double2* p = dst + ((size_t)c * Mm + m) * NY + n;
+      const double2 o = *p;
+      *p = make_double2(o.x + (double)res[c].x, o.y + (double)res[c].y);
+    }
+  }
+}
+
+// weighted: out = W^-1 (P out - P W r), i.e. iz > 0: out/2 - r; iz = 0: P out - P r.
+// plain (Euclidean transpose): out = P out - P r.
+__global__ void k_finish_adj(const double2* __restrict__ r, double2* __restrict__ out, int Mm, int MX, int MZ,
+                             int Kx, int NY, int n_dir, int weighted) {
+  const size_t per = (size_t)3 * Mm * NY;
+  const size_t total = per * n_dir;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t rem = e % per;
+    const int n = (int)(rem % NY);
+    const int m = (int)((rem / NY) % Mm);
+    const size_t cbase = e - rem + (rem / ((size_t)Mm * NY)) * Mm * NY;  // start of this component
+    const int pos = m / MZ, iz = m - pos * MZ;
+    if (iz > 0) {
+      const double2 o = out[e], rr = r[e];
+      const double h = weighted ? 0.5 : 1.0;
+      out[e] = make_double2(h * o.x - rr.x, h * o.y - rr.y);
+      continue;
+    }
+    if (pos > Kx) continue;  // handled with its mirror
+    const int mpos = pos == 0 ? 0 : MX - pos;
+    const size_t em = cbase + (size_t)(mpos * MZ) * NY + n;
+    const double2 o = out[e], om = out[em], rr = r[e], rm = r[em];
+    const double2 res = make_double2(0.5 * (o.x + om.x) - 0.5 * (rr.x + rm.x),
+                                     0.5 * (o.y - om.y) - 0.5 * (rr.y - rm.y));
+    if (pos == 0) {
+      out[e] = make_double2(res.x, 0.0);
+    } else {
+      out[e] = res;
+      out[em] = make_double2(res.x, -res.y);
+    }
+  }
+}
+
 // ------------------------------------------------------------ seeding
 struct SeedArgs {
   int Mm, MX, MZ, Kx, NY;
@@ -752,7 +1094,7 @@ int grid_for(size_t n, int threads, int sms) {
 static size_t xz_smem_bytes(const sp_ctx* c, int esize, int rp, int cx) {
   const int FS = c->MZ + 1, RS = 6 * FS;
   size_t scr = (size_t)2 * cx * c->nx;
-  size_t zs = (size_t)21 * rp * c->nz;
+  size_t zs = (size_t)24 * rp * c->nz;
   if (zs > scr) scr = zs;
   return (size_t)esize * 2 * ((size_t)c->nx + c->nz + (size_t)c->nx * RS + scr);
 }
@@ -762,7 +1104,7 @@ static bool xz_config(const sp_ctx* c, int esize, int* rp, int* cx, size_t* byte
   // prefer two resident blocks per SM (about 113 KB each), else one (up to 220 KB)
   for (size_t budget : {(size_t)113 * 1024, (size_t)220 * 1024}) {
   for (int r = 4; r >= 1; --r) {
-    int scr_c = 21 * r * c->nz;
+    int scr_c = 24 * r * c->nz;
     int x = scr_c / (2 * c->nx);
     if (x < 1) x = 1;
     if (x > 6 * c->MZ) x = 6 * c->MZ;
@@ -840,6 +1182,9 @@ cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, voi
     if (mode == XZ_TANGENT)
       return launch_xz_t<float, XZ_TANGENT>(c, in6, out3, c->base32, tx, tz, c->xz_rp32, c->xz_cx32,
                                             c->smem_xz32, n_dir, st);
+    if (mode == XZ_ADJOINT)
+      return launch_xz_t<float, XZ_ADJOINT>(c, in6, out3, c->base32, tx, tz, c->xz_rp32, c->xz_cx32,
+                                            c->smem_xz32, n_dir, st);
     return cudaErrorInvalidValue;  // the step and the base are always FP64
   }
   if (c->smem_xz64 == 0) return cudaErrorInvalidConfiguration;
@@ -851,6 +1196,9 @@ cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, voi
                                           c->smem_xz64, n_dir, st);
     case XZ_TANGENT:
       return launch_xz_t<double, XZ_TANGENT>(c, in6, out3, c->base64, tx, tz, c->xz_rp64, c->xz_cx64,
+                                             c->smem_xz64, n_dir, st);
+    case XZ_ADJOINT:
+      return launch_xz_t<double, XZ_ADJOINT>(c, in6, out3, c->base64, tx, tz, c->xz_rp64, c->xz_cx64,
                                              c->smem_xz64, n_dir, st);
     default:
       return launch_xz_t<double, XZ_BASE>(c, in6, out3, c->base64, tx, tz, c->xz_rp64, c->xz_cx64,
@@ -892,6 +1240,76 @@ cudaError_t launch_solve(const sp_ctx* c, bool fp32, const void* in3, const doub
                                                      reinterpret_cast<const double2*>(du),
                                                      reinterpret_cast<double2*>(out), a);
   }
+  return cudaGetLastError();
+}
+
+
+static size_t solve_adj_smem(const sp_ctx* c) {
+  const int TM = kTileSolve, NY = c->NY, NR = c->N - 1;
+  return (size_t)16 * (3 * TM * NY + 3 * TM * NY + TM * 2 * c->cv + 2 * TM * NR + 3 * TM * NR) + 16;
+}
+
+static SolveArgs solve_args(const sp_ctx* c) {
+  SolveArgs a;
+  a.ops = c->ops;
+  a.Cfh_d = c->Cfh;
+  a.Cfh_f = c->Cfh_f;
+  a.n_unique = c->n_unique; a.Mm = c->Mm; a.MX = c->MX; a.MZ = c->MZ; a.Kx = c->Kx;
+  a.NY = c->NY; a.N = c->N; a.NH = c->NH;
+  a.cv = c->cv; a.rb0 = c->rb0; a.rb1 = c->rb1;
+  a.off_v0 = c->off_v0; a.off_v1 = c->off_v1; a.off_h0 = c->off_h0; a.off_h1 = c->off_h1;
+  a.op_stride = c->op_stride;
+  a.alpha = c->alpha; a.beta = c->beta; a.inv_dt = 1.0 / c->dt;
+  return a;
+}
+
+cudaError_t launch_solve_adj(const sp_ctx* c, bool fp32, const double* r, double* out, void* vals3, int n_dir,
+                             bool weighted, cudaStream_t st) {
+  SolveArgs a = solve_args(c);
+  dim3 grid((c->n_unique + kTileSolve - 1) / kTileSolve, n_dir);
+  size_t sm = solve_adj_smem(c);
+  if (fp32) {
+    cudaFuncSetAttribute(k_solve_adj<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_solve_adj<float><<<grid, kThreadsSolve, sm, st>>>(reinterpret_cast<const double2*>(r),
+                                                        reinterpret_cast<double2*>(out),
+                                                        reinterpret_cast<C2<float>*>(vals3), a, weighted ? 1 : 0);
+  } else {
+    cudaFuncSetAttribute(k_solve_adj<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_solve_adj<double><<<grid, kThreadsSolve, sm, st>>>(reinterpret_cast<const double2*>(r),
+                                                         reinterpret_cast<double2*>(out),
+                                                         reinterpret_cast<C2<double>*>(vals3), a, weighted ? 1 : 0);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_yinv_adj(const sp_ctx* c, bool fp32, const void* in6, double* out, int n_dir,
+                            cudaStream_t st) {
+  YinvArgs a;
+  a.Mm = c->Mm; a.MZ = c->MZ; a.MX = c->MX; a.Kx = c->Kx; a.NY = c->NY; a.N = c->N; a.NH = c->NH;
+  a.alpha = c->alpha; a.beta = c->beta;
+  a.jchunk = c->NH;
+  const int tiles = (c->Mm + kTileYinv - 1) / kTileYinv;
+  dim3 grid(tiles, 1, n_dir);
+  if (fp32) {
+    size_t sm = (size_t)5 * c->NY * kTileYinv * sizeof(C2<float>);
+    cudaFuncSetAttribute(k_yinv_adj<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_yinv_adj<float><<<grid, kThreadsYinv, sm, st>>>(reinterpret_cast<const C2<float>*>(in6),
+                                                      reinterpret_cast<double2*>(out), c->Th_f, c->TDh_f, a);
+  } else {
+    size_t sm = (size_t)5 * c->NY * kTileYinv * sizeof(C2<double>);
+    cudaFuncSetAttribute(k_yinv_adj<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_yinv_adj<double><<<grid, kThreadsYinv, sm, st>>>(reinterpret_cast<const C2<double>*>(in6),
+                                                       reinterpret_cast<double2*>(out), c->Th, c->TDh, a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_adj(const sp_ctx* c, const double* r, double* out, int n_dir, bool weighted,
+                              cudaStream_t st) {
+  size_t n = (size_t)3 * c->Mm * c->NY * n_dir;
+  k_finish_adj<<<grid_for(n, 256, c->sm_count), 256, 0, st>>>(reinterpret_cast<const double2*>(r),
+                                                             reinterpret_cast<double2*>(out), c->Mm, c->MX,
+                                                             c->MZ, c->Kx, c->NY, n_dir, weighted ? 1 : 0);
   return cudaGetLastError();
 }
 

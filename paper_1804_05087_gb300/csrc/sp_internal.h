@@ -116,7 +116,7 @@ sp_status sp_build_plan(sp_ctx* c);
 bool sp_xz_fits(sp_ctx* c);
 
 // kernel launchers (kernels.cu); all asynchronous on `st`
-enum XzMode { XZ_STEP = 0, XZ_TANGENT = 1, XZ_BASE = 2 };
+enum XzMode { XZ_STEP = 0, XZ_TANGENT = 1, XZ_BASE = 2, XZ_ADJOINT = 3 };
 cudaError_t launch_yinv(const sp_ctx* c, bool fp32, const double* in, void* out6, int n_dir,
                         cudaStream_t st);
 cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, void* out3,
@@ -124,6 +124,14 @@ cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, voi
 cudaError_t launch_solve(const sp_ctx* c, bool fp32, const void* in3, const double* du,
                          double* out, int n_dir, cudaStream_t st);
 cudaError_t launch_base_to_f32(const sp_ctx* c, cudaStream_t st);
+// adjoint chain (sp_vjp): solve^T + Chebyshev^T, plane stage^T (launch_xz with
+// XZ_ADJOINT), values^T + curl^T, then weights and the Hermitian projection
+cudaError_t launch_solve_adj(const sp_ctx* c, bool fp32, const double* r, double* out, void* vals3,
+                             int n_dir, bool weighted, cudaStream_t st);
+cudaError_t launch_yinv_adj(const sp_ctx* c, bool fp32, const void* in6, double* out, int n_dir,
+                            cudaStream_t st);
+cudaError_t launch_finish_adj(const sp_ctx* c, const double* r, double* out, int n_dir, bool weighted,
+                              cudaStream_t st);
 cudaError_t launch_seed(const sp_ctx* c, const double* ra, const double* rb, const double* rc,
                         double* U, cudaStream_t st);
 cudaError_t launch_scale(double* x, double s, size_t n, cudaStream_t st);
