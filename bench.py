@@ -93,9 +93,11 @@ def kernel_flops(stage, n_dir):
         per_plane = (6 + 3) * mz * fx + (6 + 3) * (NX // 2) * fz + NX * NZ * 30
         return n_dir * ny * per_plane
     if stage == "k_solve":
+        # FP64 work only: the per-mode operators (complex input, real matrices) and the
+        # continuity/rotation epilogue; the Chebyshev transform (float in mixed mode) is excluded
         n = ny - 1
         op = (n // 2 + 1) * (n - 1) + (n // 2) * (n - 1) + (n // 2 + 1) * (n // 2) + (n // 2) * (n // 2 - 1)
-        return n_dir * n_unique() * (3 * (n - 1) * nh * 4 + op * 4 + ny * nh * 4)
+        return n_dir * n_unique() * (op * 4 + ny * 16)
     return 0
 
 

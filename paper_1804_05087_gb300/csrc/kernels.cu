@@ -448,6 +448,7 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict
   double2* sv = sfw + TM * NR;                // [TM][NY]
   double2* sb = sv + TM * NY;                 // [TM][NY]
   __shared__ int s_pos[kTileSolve], s_iz[kTileSolve], s_u[kTileSolve];
+  __shared__ double s_kx[kTileSolve], s_kz[kTileSolve], s_ik[kTileSolve];
   const int u0 = blockIdx.x * TM;
   const int dir = blockIdx.y;
   if (threadIdx.x < TM) {
@@ -457,6 +458,13 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict
     s_pos[threadIdx.x] = pos;
     s_iz[threadIdx.x] = iz;
     s_u[threadIdx.x] = u;
+    // wavenumbers once per mode: no division or square root in the loops below
+    const int ix = pos <= a.Kx ? pos : pos - a.MX;
+    const double kx = a.alpha * ix, kz = a.beta * iz;
+    const double kk = sqrt(kx * kx + kz * kz);
+    s_kx[threadIdx.x] = kx;
+    s_kz[threadIdx.x] = kz;
+    s_ik[threadIdx.x] = kk > 0 ? 1.0 / kk : 0.0;
   }
   __syncthreads();
   const C2<T>* vin = in3 + (size_t)dir * 3 * NY * Mm;
@@ -534,8 +542,7 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict
   for (int idx = threadIdx.x; idx < TM * NR; idx += blockDim.x) {
     const int t = idx / NR, n = idx - t * NR;
     const int pos = s_pos[t], iz = s_iz[t];
-    const int ix = pos <= a.Kx ? pos : pos - a.MX;
-    const double kx = a.alpha * ix, kz = a.beta * iz;
+    const double kx = s_kx[t], kz = s_kz[t], ik = s_ik[t];
     const double2 fx = sf[(0 * TM + t) * NR + n];
     const double2 fy = sf[(1 * TM + t) * NR + n];
     const double2 fz = sf[(2 * TM + t) * NR + n];
@@ -544,7 +551,6 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict
       sfw[t * NR + n] = fz;
       continue;
     }
-    const double k = sqrt(kx * kx + kz * kz), ik = 1.0 / k;
     const double2 fa = make_double2((kx * fx.x + kz * fz.x) * ik, (kx * fx.y + kz * fz.y) * ik);
     const double2 fb = make_double2((-kz * fx.x + kx * fz.x) * ik, (-kz * fx.y + kx * fz.y) * ik);
     const double2 fta = make_double2(fa.y, -fa.x);  // -i f_a
@@ -593,6 +599,21 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict
     sv[t * NY + n] = accv;
   }
   __syncthreads();
+  // (D v)_n = (2/c_n) sum_{p > n, p + n odd} p v_p: one suffix sum per (mode, parity),
+  // kept in sfb (free after phase D) as S_n = sum_{p >= n, p = n mod 2} p v_p
+  double2* ssum = sfb;
+  if (threadIdx.x < 2 * TM) {
+    const int t = threadIdx.x >> 1, par = threadIdx.x & 1;
+    double2 acc = make_double2(0.0, 0.0);
+    const int top = ((NY - 1 - par) & 1) ? NY - 2 : NY - 1;  // largest index of this parity
+    for (int p = top; p >= 0; p -= 2) {
+      const double2 vp = sv[t * NY + p];
+      acc.x += p * vp.x;
+      acc.y += p * vp.y;
+      ssum[t * NY + p] = acc;
+    }
+  }
+  __syncthreads();
   // phase E: a = (i/k) D v, back-rotation, G = u_new - u, Hermitian output
   double2* dst = out + (size_t)dir * 3 * Mm * NY;
   for (int idx = threadIdx.x; idx < TM * NY; idx += blockDim.x) {
@@ -605,16 +626,13 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict
       wn = make_double2(sv[t * NY + n].x, 0.0);
       vn = make_double2(0.0, 0.0);
     } else {
-      const int ix = pos <= a.Kx ? pos : pos - a.MX;
-      const double kx = a.alpha * ix, kz = a.beta * iz;
-      const double k = sqrt(kx * kx + kz * kz), ik = 1.0 / k;
+      const double kx = s_kx[t], kz = s_kz[t], ik = s_ik[t];
       double2 dv = make_double2(0.0, 0.0);
-      for (int p = n + 1; p < NY; p += 2) {
-        const double2 vp = sv[t * NY + p];
-        dv.x += 2.0 * p * vp.x;
-        dv.y += 2.0 * p * vp.y;
+      if (n + 1 < NY) {
+        const double2 sp = ssum[t * NY + n + 1];
+        const double f = n == 0 ? 1.0 : 2.0;
+        dv = make_double2(f * sp.x, f * sp.y);
       }
-      if (n == 0) { dv.x *= 0.5; dv.y *= 0.5; }
       const double2 an = make_double2(-dv.y * ik, dv.x * ik);  // (i/k) Dv
       const double2 bn = sb[t * NY + n];
       un = make_double2((kx * an.x - kz * bn.x) * ik, (kx * an.y - kz * bn.y) * ik);
@@ -1176,6 +1194,8 @@ static cudaError_t launch_xz_t(const sp_ctx* c, const void* in6, void* out3, T* 
 
 cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, void* out3, int n_dir,
                       cudaStream_t st) {
+  if (fp32 && c->use_xz_reg && sp_xz_reg_supported(c) && (mode == XZ_TANGENT || mode == XZ_ADJOINT))
+    return launch_xz_reg(c, mode, in6, out3, n_dir, st);
   if (fp32) {
     const C2<float>* tx = reinterpret_cast<const C2<float>*>(c->twx_f);
     const C2<float>* tz = reinterpret_cast<const C2<float>*>(c->twz_f);

@@ -84,6 +84,7 @@ struct sp_ctx {
   double* red_host = nullptr;    // pinned
   int red_blocks = 0;
   int has_base = 0;
+  int use_xz_reg = 1;            // float plane stage: register FFT kernel when the size allows
   // sizes of shared memory per kernel (bytes)
   size_t smem_xz64 = 0, smem_xz32 = 0;
   int xz_rp64 = 1, xz_rp32 = 1;
@@ -121,6 +122,9 @@ cudaError_t launch_yinv(const sp_ctx* c, bool fp32, const double* in, void* out6
                         cudaStream_t st);
 cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, void* out3,
                       int n_dir, cudaStream_t st);
+// float plane stage with register-resident FFTs (xz_reg.cu), square grids 16..64
+bool sp_xz_reg_supported(const sp_ctx* c);
+cudaError_t launch_xz_reg(const sp_ctx* c, int mode, const void* in, void* out, int n_dir, cudaStream_t st);
 cudaError_t launch_solve(const sp_ctx* c, bool fp32, const void* in3, const double* du,
                          double* out, int n_dir, cudaStream_t st);
 cudaError_t launch_base_to_f32(const sp_ctx* c, cudaStream_t st);

@@ -1,0 +1,349 @@
+// Plane stage of the tangent and the adjoint in float, with register-resident
+// FFTs: one thread owns a whole transform (length <= 64), so each phase of
+// the plane needs a single barrier instead of one per FFT stage.
+//
+// Same mathematics as k_xz (kernels.cu): per y-plane, inverse FFT along x of
+// every (field, kz) column, packed c2r along z of pairs of x-rows, the
+// pointwise product, packed r2c along z, forward FFT along x truncated to the
+// 2/3-rule modes (pseudospectral products, Sec. 3.2).
+//
+// The FFT is a decimation-in-frequency Cooley-Tukey recursion with radices
+// 4, 3 and 2 fully unrolled at compile time: inputs in natural order, outputs
+// in digit-reversed positions resolved by a compile-time index map, twiddles
+// as compile-time constants (sine and cosine evaluated by Taylor series at
+// compile time).
+#include <utility>
+
+#include "sp_internal.h"
+
+namespace {
+
+// ------------------------------------------------- compile-time trigonometry
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// Taylor series about 0; |x| <= pi/4 after the reduction below (30 terms is
+// far below double rounding there)
+__host__ __device__ constexpr double taylor_sin(double x) {
+  double term = x, sum = x;
+  for (int k = 1; k < 30; ++k) {
+    term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+__host__ __device__ constexpr double taylor_cos(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 30; ++k) {
+    term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+    sum += term;
+  }
+  return sum;
+}
+// cos and sin of 2 pi k / n for integers, reduced exactly by octant symmetry
+__host__ __device__ constexpr double cos2pi(long k, long n) {
+  long m = ((k % n) + n) % n;            // angle 2 pi m / n in [0, 2 pi)
+  if (8 * m <= n) return taylor_cos(2.0 * kPi * (double)m / (double)n);
+  if (8 * m <= 3 * n) return taylor_sin(2.0 * kPi * (double)(n - 4 * m) / (4.0 * n));   // cos(pi/2 - t)
+  if (8 * m <= 5 * n) return -taylor_cos(2.0 * kPi * (double)(2 * m - n) / (2.0 * n));  // -cos(t - pi)
+  if (8 * m <= 7 * n) return -taylor_sin(2.0 * kPi * (double)(3 * n - 4 * m) / (4.0 * n));
+  return taylor_cos(2.0 * kPi * (double)(n - m) / (double)n);
+}
+__host__ __device__ constexpr double sin2pi(long k, long n) { return cos2pi(n - 4 * k, 4 * n); }  // sin t = cos(pi/2 - t)
+
+// -------------------------------------------------------------- radix plans
+template <int N> struct Plan;
+template <> struct Plan<2> { using type = std::integer_sequence<int, 2>; };
+template <> struct Plan<3> { using type = std::integer_sequence<int, 3>; };
+template <> struct Plan<4> { using type = std::integer_sequence<int, 4>; };
+template <> struct Plan<16> { using type = std::integer_sequence<int, 4, 4>; };
+template <> struct Plan<24> { using type = std::integer_sequence<int, 4, 3, 2>; };
+template <> struct Plan<32> { using type = std::integer_sequence<int, 4, 4, 2>; };
+template <> struct Plan<48> { using type = std::integer_sequence<int, 4, 4, 3>; };
+template <> struct Plan<64> { using type = std::integer_sequence<int, 4, 4, 4>; };
+
+// position of output frequency f after the DIF recursion with radices P0, Pr...
+template <int N, int P0, int... Pr>
+__host__ __device__ constexpr int dif_pos(int f) {
+  constexpr int M = N / P0;
+  if constexpr (sizeof...(Pr) == 0) {
+    return (f % P0) * M;
+  } else {
+    return (f % P0) * M + dif_pos<M, Pr...>(f / P0);
+  }
+}
+template <int N, int... P>
+__host__ __device__ constexpr int out_pos_impl(int f, std::integer_sequence<int, P...>) { return dif_pos<N, P...>(f); }
+template <int N>
+__host__ __device__ constexpr int out_pos(int f) { return out_pos_impl<N>(f, typename Plan<N>::type{}); }
+
+// y_d = sum_r x_r w_P^{r d}, w_P = exp(SGN 2 pi i / P)
+template <int P, int SGN>
+__device__ __forceinline__ void bfly(C2<float>* v) {
+  if constexpr (P == 2) {
+    const C2<float> a = v[0], b = v[1];
+    v[0] = a + b;
+    v[1] = a - b;
+  } else if constexpr (P == 3) {
+    constexpr float h3 = (float)(0.86602540378443864676 * SGN);
+    const C2<float> t1 = v[1] + v[2];
+    const C2<float> t2 = mul_is(v[1] - v[2], h3);
+    const C2<float> m = v[0] - scl(t1, 0.5f);
+    v[0] = v[0] + t1;
+    v[1] = m + t2;
+    v[2] = m - t2;
+  } else {
+    const C2<float> a = v[0] + v[2], b = v[0] - v[2];
+    const C2<float> c = v[1] + v[3], d = mul_is(v[1] - v[3], (float)SGN);
+    v[0] = a + c;
+    v[2] = a - c;
+    v[1] = b + d;
+    v[3] = b - d;
+  }
+}
+
+template <int NT, int N, int OFF, int SGN, int P0, int... Pr>
+__device__ __forceinline__ void dif(C2<float> (&x)[NT]);
+
+template <int NT, int M, int OFF, int SGN, int... Pr, int... D>
+__device__ __forceinline__ void dif_blocks(C2<float> (&x)[NT], std::integer_sequence<int, D...>) {
+  (dif<NT, M, OFF + D * M, SGN, Pr...>(x), ...);
+}
+
+// twiddle by w_N^{m d} (a compile-time constant) and store at position OFF + m + d M
+template <int NT, int N, int OFF, int SGN, int M, int m, int d>
+__device__ __forceinline__ void tw_store(C2<float> (&x)[NT], C2<float> y) {
+  if constexpr (m * d != 0) {
+    constexpr float wc = (float)cos2pi((long)m * d, N);
+    constexpr float ws = (float)(SGN * sin2pi((long)m * d, N));
+    y = mk(y.x * wc - y.y * ws, y.x * ws + y.y * wc);
+  }
+  x[OFF + m + d * M] = y;
+}
+
+template <int NT, int N, int OFF, int SGN, int P0, int M, int m, int... D>
+__device__ __forceinline__ void dif_col(C2<float> (&x)[NT], std::integer_sequence<int, D...>) {
+  C2<float> v[P0] = {x[OFF + m + D * M]...};
+  bfly<P0, SGN>(v);
+  (tw_store<NT, N, OFF, SGN, M, m, D>(x, v[D]), ...);
+}
+
+template <int NT, int N, int OFF, int SGN, int P0, int M, int... Ms>
+__device__ __forceinline__ void dif_cols(C2<float> (&x)[NT], std::integer_sequence<int, Ms...>) {
+  (dif_col<NT, N, OFF, SGN, P0, M, Ms>(x, std::make_integer_sequence<int, P0>{}), ...);
+}
+
+// one decimation-in-frequency level on positions [OFF, OFF + N), then recurse
+// on the P0 blocks of length M = N / P0
+template <int NT, int N, int OFF, int SGN, int P0, int... Pr>
+__device__ __forceinline__ void dif(C2<float> (&x)[NT]) {
+  constexpr int M = N / P0;
+  dif_cols<NT, N, OFF, SGN, P0, M>(x, std::make_integer_sequence<int, M>{});
+  if constexpr (sizeof...(Pr) > 0) dif_blocks<NT, M, OFF, SGN, Pr...>(x, std::make_integer_sequence<int, P0>{});
+}
+
+template <int N, int SGN, int... P>
+__device__ __forceinline__ void fft_impl(C2<float> (&x)[N], std::integer_sequence<int, P...>) {
+  dif<N, N, 0, SGN, P...>(x);
+}
+// in-register FFT: natural-order input, output frequency f at x[out_pos<N>(f)]
+template <int N, int SGN>
+__device__ __forceinline__ void fft_reg(C2<float> (&x)[N]) {
+  fft_impl<N, SGN>(x, typename Plan<N>::type{});
+}
+
+struct XzRegArgs {
+  const C2<float>* in;  // [dir][NIN][NY][Mm]
+  C2<float>* out;       // [dir][NOUT][NY][Mm]
+  const float* base;    // [6][NY][NX][NZ]
+  const double* yv;
+  int NY, Mm;
+};
+
+constexpr int kThreadsReg = 256;
+
+template <int NX, int NZ, int MODE>
+__global__ void __launch_bounds__(kThreadsReg) k_xz_reg(XzRegArgs a) {
+  constexpr int NIN = MODE == XZ_ADJOINT ? 3 : 6;
+  constexpr int NOUT = MODE == XZ_ADJOINT ? 6 : 3;
+  constexpr int KX = (NX - 1) / 3, KZ = (NZ - 1) / 3;
+  constexpr int MX = 2 * KX + 1, MZ = KZ + 1;
+  constexpr int FS = MZ + 1, RS = 6 * FS;
+  constexpr int NQ = NX / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<float>* G = reinterpret_cast<C2<float>*>(smem_raw);  // [NX][6][FS]
+  C2<float>* Ph = G + NX * RS;                              // [6][NQ][NZ] packed row pairs
+  const int j = blockIdx.x, dir = blockIdx.y;
+  const size_t planeMm = (size_t)a.NY * a.Mm;
+  const C2<float>* in = a.in + (size_t)dir * NIN * planeMm + (size_t)j * a.Mm;
+  const float inv = (float)(1.0 / ((double)NX * (double)NZ));
+
+  // phase 1: inverse FFT along x, one thread per (field, kz) column
+  for (int col = threadIdx.x; col < NIN * MZ; col += blockDim.x) {
+    const int f = col / MZ, iz = col - f * MZ;
+    const C2<float>* src = in + (size_t)f * planeMm + iz;
+    float sc = 1.0f;
+    if constexpr (MODE == XZ_ADJOINT) sc = iz == 0 ? inv : 0.5f * inv;
+    C2<float> x[NX];
+#pragma unroll
+    for (int e = 0; e < NX; ++e) {
+      if (e <= KX) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(src + e * MZ));
+        x[e] = mk(v.x * sc, v.y * sc);
+      } else if (e >= NX - KX) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(src + (e - NX + MX) * MZ));
+        x[e] = mk(v.x * sc, v.y * sc);
+      } else {
+        x[e] = mk(0.f, 0.f);
+      }
+    }
+    fft_reg<NX, 1>(x);
+#pragma unroll
+    for (int p = 0; p < NX; ++p) G[p * RS + f * FS + iz] = x[out_pos<NX>(p)];
+  }
+  __syncthreads();
+
+  // phase 2a: c2r along z of row pairs (2q, 2q+1) packed as real + i imag
+  for (int it = threadIdx.x; it < NIN * NQ; it += blockDim.x) {
+    const int f = it / NQ, q = it - f * NQ;
+    const C2<float>* g0 = G + (2 * q) * RS + f * FS;
+    const C2<float>* g1 = g0 + RS;
+    C2<float> z[NZ];
+#pragma unroll
+    for (int e = 0; e < NZ; ++e) {
+      if (e == 0) {
+        z[e] = mk(g0[0].x, g1[0].x);
+      } else if (e <= KZ) {
+        const C2<float> A = g0[e], B = g1[e];
+        z[e] = mk(A.x - B.y, A.y + B.x);
+      } else if (e >= NZ - KZ) {
+        const C2<float> A = g0[NZ - e], B = g1[NZ - e];
+        z[e] = mk(A.x + B.y, B.x - A.y);
+      } else {
+        z[e] = mk(0.f, 0.f);
+      }
+    }
+    fft_reg<NZ, 1>(z);
+    C2<float>* dst = Ph + (f * NQ + q) * NZ;
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) dst[k] = z[out_pos<NZ>(k)];
+  }
+  __syncthreads();
+
+  // phase 2b: pointwise products (in place: each point reads its NIN fields first)
+  const size_t nxz = (size_t)NX * NZ;
+  for (int it = threadIdx.x; it < NQ * NZ; it += blockDim.x) {
+    const int q = it / NZ, k = it - q * NZ;
+    C2<float> fv[NIN];
+#pragma unroll
+    for (int f = 0; f < NIN; ++f) fv[f] = Ph[(f * NQ + q) * NZ + k];
+    float res[2][NOUT];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      float F[NIN], B[6];
+#pragma unroll
+      for (int f = 0; f < NIN; ++f) F[f] = r ? fv[f].y : fv[f].x;
+      const size_t gidx = (size_t)j * nxz + (size_t)(2 * q + r) * NZ + k;
+#pragma unroll
+      for (int f = 0; f < 6; ++f) B[f] = __ldg(a.base + (size_t)f * a.NY * nxz + gidx);
+      if constexpr (MODE == XZ_TANGENT) {
+        res[r][0] = (B[1] * F[5] - B[2] * F[4]) + (F[1] * B[5] - F[2] * B[4]);
+        res[r][1] = (B[2] * F[3] - B[0] * F[5]) + (F[2] * B[3] - F[0] * B[5]);
+        res[r][2] = (B[0] * F[4] - B[1] * F[3]) + (F[0] * B[4] - F[1] * B[3]);
+      } else {
+        res[r][0] = B[4] * F[2] - B[5] * F[1];
+        res[r][1] = B[5] * F[0] - B[3] * F[2];
+        res[r][2] = B[3] * F[1] - B[4] * F[0];
+        res[r][3] = F[1] * B[2] - F[2] * B[1];
+        res[r][4] = F[2] * B[0] - F[0] * B[2];
+        res[r][5] = F[0] * B[1] - F[1] * B[0];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NOUT; ++c) Ph[(c * NQ + q) * NZ + k] = mk(res[0][c], res[1][c]);
+  }
+  __syncthreads();
+
+  // phase 2c: r2c along z and separation of the two rows; result into G rows
+  for (int it = threadIdx.x; it < NOUT * NQ; it += blockDim.x) {
+    const int c = it / NQ, q = it - c * NQ;
+    C2<float> z[NZ];
+    const C2<float>* src = Ph + (c * NQ + q) * NZ;
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) z[k] = src[k];
+    fft_reg<NZ, -1>(z);
+    C2<float>* g0 = G + (2 * q) * RS + c * FS;
+    C2<float>* g1 = g0 + RS;
+#pragma unroll
+    for (int iz = 0; iz <= KZ; ++iz) {
+      const C2<float> X = z[out_pos<NZ>(iz)];
+      const C2<float> Xm = z[out_pos<NZ>((NZ - iz) % NZ)];
+      const C2<float> Aa = scl(X + conj2(Xm), 0.5f);
+      const C2<float> D = X - conj2(Xm);
+      g0[iz] = Aa;
+      g1[iz] = mk(D.y * 0.5f, -D.x * 0.5f);
+    }
+  }
+  __syncthreads();
+
+  // phase 3: forward FFT along x, keep the 2/3-rule modes
+  C2<float>* out = a.out + (size_t)dir * NOUT * planeMm + (size_t)j * a.Mm;
+  for (int col = threadIdx.x; col < NOUT * MZ; col += blockDim.x) {
+    const int c = col / MZ, iz = col - c * MZ;
+    C2<float> x[NX];
+#pragma unroll
+    for (int p = 0; p < NX; ++p) x[p] = G[p * RS + c * FS + iz];
+    fft_reg<NX, -1>(x);
+    float sc = inv;
+    if constexpr (MODE == XZ_ADJOINT) sc = iz == 0 ? 1.0f : 2.0f;
+    C2<float>* dst = out + (size_t)c * planeMm + iz;
+#pragma unroll
+    for (int e = 0; e < NX; ++e) {
+      if (e <= KX) dst[e * MZ] = scl(x[out_pos<NX>(e)], sc);
+      else if (e >= NX - KX) dst[(e - NX + MX) * MZ] = scl(x[out_pos<NX>(e)], sc);
+    }
+  }
+}
+
+template <int NX, int NZ, int MODE>
+cudaError_t launch_reg(const sp_ctx* c, const void* in, void* out, int n_dir, cudaStream_t st) {
+  constexpr int KZ = (NZ - 1) / 3, MZ = KZ + 1, FS = MZ + 1, RS = 6 * FS;
+  const size_t smem = sizeof(C2<float>) * ((size_t)NX * RS + (size_t)6 * (NX / 2) * NZ);
+  if (smem > 227 * 1024) return cudaErrorNotSupported;
+  XzRegArgs a;
+  a.in = reinterpret_cast<const C2<float>*>(in);
+  a.out = reinterpret_cast<C2<float>*>(out);
+  a.base = c->base32;
+  a.yv = c->yv;
+  a.NY = c->NY;
+  a.Mm = c->Mm;
+  cudaFuncSetAttribute(k_xz_reg<NX, NZ, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(c->NY, n_dir);
+  k_xz_reg<NX, NZ, MODE><<<grid, kThreadsReg, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t dispatch_reg(const sp_ctx* c, const void* in, void* out, int n_dir, cudaStream_t st) {
+  if (c->nx != c->nz) return cudaErrorNotSupported;
+  switch (c->nx) {
+    case 16: return launch_reg<16, 16, MODE>(c, in, out, n_dir, st);
+    case 24: return launch_reg<24, 24, MODE>(c, in, out, n_dir, st);
+    case 32: return launch_reg<32, 32, MODE>(c, in, out, n_dir, st);
+    case 48: return launch_reg<48, 48, MODE>(c, in, out, n_dir, st);
+    case 64: return launch_reg<64, 64, MODE>(c, in, out, n_dir, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace
+
+bool sp_xz_reg_supported(const sp_ctx* c) {
+  if (c->nx != c->nz) return false;
+  return c->nx == 16 || c->nx == 24 || c->nx == 32 || c->nx == 48 || c->nx == 64;
+}
+
+cudaError_t launch_xz_reg(const sp_ctx* c, int mode, const void* in, void* out, int n_dir, cudaStream_t st) {
+  if (mode == XZ_TANGENT) return dispatch_reg<XZ_TANGENT>(c, in, out, n_dir, st);
+  if (mode == XZ_ADJOINT) return dispatch_reg<XZ_ADJOINT>(c, in, out, n_dir, st);
+  return cudaErrorNotSupported;
+}

@@ -60,7 +60,7 @@ def test_vjp_dense_transpose_4x9x4():
     assert np.max(np.abs(Jg - Jstar)) < 1e-12 * np.max(np.abs(Jstar))
 
 
-@pytest.mark.parametrize("grid", [(16, 33, 16), (48, 65, 48)])
+@pytest.mark.parametrize("grid", [(16, 33, 16), (48, 65, 48), (64, 65, 64), (18, 17, 24)])
 def test_vjp_mixed(grid):
     ctx, orc = make(*grid, prec=1)
     u = seeded(orc, 1000, 0.1)

@@ -78,7 +78,9 @@ def test_jvp_parity_fp64(grid):
         assert rel(got[i], orc.jvp(base, ds[i])) < 1e-12
 
 
-@pytest.mark.parametrize("grid", [(16, 33, 16), (48, 65, 48)])
+# square grids up to 64 take the register-FFT plane kernel, others the Stockham one
+@pytest.mark.parametrize("grid", [(16, 33, 16), (24, 33, 24), (32, 33, 32), (48, 65, 48), (64, 65, 64),
+                                  (18, 17, 24)])
 def test_jvp_parity_mixed(grid):
     ctx, orc = make(*grid, prec=1, max_batch=2)
     u = seeded(orc, 1000, 0.1)
