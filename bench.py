@@ -45,6 +45,12 @@ def parse():
     p.add_argument("--ndir", type=int, default=256)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--newton", action="store_true",
+                   help="time-to-converge comparison (Newton-GMRES-hookstep) instead of the JVP throughput")
+    p.add_argument("--grid", default="16x33x16", help="grid of the --newton run")
+    p.add_argument("--krylov", type=int, default=300)
+    p.add_argument("--config4", action="store_true",
+                   help="96x97x96, Re 1000, doubled box: adjoint gradient check and Newton-hookstep with J^T F")
     return p.parse_args()
 
 
@@ -185,10 +191,99 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- our arm
+def run_newton(args):
+    """Time to |G(U)| < 1e-10 from a seeded perturbed-laminar state (Newton-GMRES-hookstep):
+    mixed tangent JVPs versus the plain FP64 finite-difference JVPs, same kernels."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1804_05087_gb300 as sp
+    import seeded_inputs as si
+    nx, ny, nz = (int(t) for t in args.grid.split("x"))
+    res = {}
+    for name, prec, fd in (("mixed_tangent", sp.SP_MIXED, False), ("fp64_tangent", sp.SP_FP64, False),
+                           ("fp64_fd", sp.SP_FP64, True)):
+        ctx = sp.Context(sp.Config(nx, ny, nz, lx=LX, lz=LZ, re=RE, dt=DT, prec=prec))
+        a, b, c = si.couette_random_coeffs(1000, nx, ny, nz)
+        U = ctx.zeros()
+        ctx.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], 0.1, U)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = ctx.sp_newton_gmres(U, max_newton=30, max_krylov=args.krylov, tol=1e-10, eta=1e-3, use_fd=fd)
+        torch.cuda.synchronize()
+        rep["wall_s"] = time.perf_counter() - t0
+        res[name] = rep
+    out = {"metric": "time to |F|<1e-10 (Newton-GMRES-hookstep)", "unit": "s", "higher_is_better": False,
+           "config": {"workload": f"plane Couette {args.grid}, Re=400, dt=100, seed 1000, amplitude 0.1",
+                      "max_krylov": args.krylov, "eta": 1e-3},
+           "runs": res,
+           "speedup_mixed_vs_fp64_fd": res["fp64_fd"]["wall_s"] / res["mixed_tangent"]["wall_s"]}
+    print(json.dumps(out))
+
+
+def run_config4(args):
+    """96x97x96 plane Couette, Re 1000, box 4pi/1.14 x 2 x 4pi/2.5, mixed precision:
+    (1) J^T F from the adjoint step against central differences of |F|^2/2 (h = 1e-7) on
+    32 seeded directions (FP64 steps); (2) 8 Newton-hookstep iterations whose trust-region
+    space includes J^* F."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1804_05087_gb300 as sp
+    import seeded_inputs as si
+    nx, ny, nz = 96, 97, 96
+    lx, lz = 4 * math.pi / 1.14, 4 * math.pi / 2.5
+    ctx = sp.Context(sp.Config(nx, ny, nz, lx=lx, lz=lz, re=1000.0, dt=DT, prec=sp.SP_MIXED))
+    ctx64 = sp.Context(sp.Config(nx, ny, nz, lx=lx, lz=lz, re=1000.0, dt=DT, prec=sp.SP_FP64))
+
+    def seeded(c, seed, amp):
+        a, b, cc = si.couette_random_coeffs(seed, nx, ny, nz)
+        U = c.zeros()
+        return c.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, cc)], amp, U)
+
+    def wdot(c, a, b):
+        return c.sp_inner(a, b)[0]
+
+    U = seeded(ctx64, 6000, 0.1)
+    F = ctx64.zeros()
+    ctx64.sp_step(U, F)
+    ctx64.sp_set_base(U)
+    g = ctx64.zeros()
+    t0 = time.perf_counter()
+    ctx64.sp_vjp(F, g)
+    torch.cuda.synchronize()
+    t_vjp = time.perf_counter() - t0
+    errs = []
+    h = 1e-7
+    for s in range(32):
+        d = seeded(ctx64, 5000 + s, 1.0)
+        Fp, Fm = ctx64.zeros(), ctx64.zeros()
+        ctx64.sp_step(U + h * d, Fp)
+        ctx64.sp_step(U - h * d, Fm)
+        fd = (0.5 * wdot(ctx64, Fp, Fp) - 0.5 * wdot(ctx64, Fm, Fm)) / (2 * h)
+        an = wdot(ctx64, g, d)
+        errs.append(abs(fd - an) / max(abs(an), 1e-30))
+    # Newton-hookstep with the gradient direction, mixed tangents, FP64 residual
+    U2 = seeded(ctx, 6000, 0.1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep = ctx.sp_newton_gmres(U2, max_newton=8, max_krylov=40, tol=1e-10, eta=1e-3, use_gradient=True)
+    torch.cuda.synchronize()
+    rep["wall_s"] = time.perf_counter() - t0
+    out = {"metric": "config 4: adjoint gradient check and Newton-hookstep with J^T F",
+           "config": {"workload": "plane Couette 96x97x96, Re=1000, dt=100, box 4pi/1.14 x 2 x 4pi/2.5"},
+           "gradient_check": {"directions": 32, "h": h, "max_rel_err": max(errs), "median_rel_err": statistics.median(errs),
+                              "vjp_ms": 1e3 * t_vjp},
+           "newton": rep}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.newton:
+        return run_newton(args)
+    if args.config4:
+        return run_config4(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:

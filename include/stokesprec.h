@@ -188,6 +188,10 @@ typedef struct {
   double eta;         /* GMRES stops at residual <= eta |G(U)| (Sec. 3.6)    */
   double delta0;      /* initial trust radius (<= 0: 0.1 max(|U|, 1))        */
   int use_fd;         /* 1: Jacobian actions by Eq. finitediff, 0: tangent   */
+  int use_gradient;   /* 1: add the steepest-descent direction J^* G(U) (one
+                         sp_vjp and one more action) to the Krylov space of the
+                         hookstep, so the trust-region step also spans the
+                         Cauchy (dogleg) direction                             */
 } sp_newton_opts;
 
 typedef struct {

@@ -40,7 +40,8 @@ class _Config(ctypes.Structure):
 
 class _NewtonOpts(ctypes.Structure):
     _fields_ = [("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int), ("tol", ctypes.c_double),
-                ("eta", ctypes.c_double), ("delta0", ctypes.c_double), ("use_fd", ctypes.c_int)]
+                ("eta", ctypes.c_double), ("delta0", ctypes.c_double), ("use_fd", ctypes.c_int),
+                ("use_gradient", ctypes.c_int)]
 
 
 class _NewtonReport(ctypes.Structure):
@@ -232,9 +233,9 @@ class Context:
         return {STAGES[i]: (ms[i], cnt[i]) for i in range(n)}
 
     def sp_newton_gmres(self, U, max_newton=20, max_krylov=30, tol=1e-10, eta=1e-3, delta0=0.0,
-                        use_fd=False, stream=None):
+                        use_fd=False, use_gradient=False, stream=None):
         pu, _ = self._ptr(U, 1)
-        o = _NewtonOpts(max_newton, max_krylov, tol, eta, delta0, 1 if use_fd else 0)
+        o = _NewtonOpts(max_newton, max_krylov, tol, eta, delta0, 1 if use_fd else 0, 1 if use_gradient else 0)
         r = _NewtonReport()
         st = _lib.sp_newton_gmres(self._h, pu, ctypes.byref(o), ctypes.byref(r), _stream(stream))
         rep = {k: getattr(r, k) for k, _ in _NewtonReport._fields_}

@@ -86,7 +86,7 @@ static bool good_fft_len(int n) {
 static void free_ctx(sp_ctx* c) {
   void* ptrs[] = {c->Th, c->TDh, c->Cfh, c->yv, c->Th_f, c->TDh_f, c->Cfh_f, c->twx, c->twz,
                   c->twx_f, c->twz_f, c->ops, c->ws6, c->ws3, c->base64, c->base32, c->U0,
-                  c->G0, c->tmp, c->red, c->kry};
+                  c->G0, c->tmp, c->red, c->kry, c->wsG};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -134,7 +134,6 @@ extern "C" sp_status sp_create(const sp_config* cfg, sp_ctx** out) {
   if (c->sm_count <= 0) c->sm_count = 1;
   if (sp_build_plan(c) != SP_OK) return bail(SP_EINVAL, c->err);
   if (!sp_xz_fits(c)) return bail(SP_EINVAL, "grid too large for the plane kernel");
-  if (c->smem_xz64 == 0) return bail(SP_EINVAL, "grid too large for the FP64 plane kernel");
   const size_t B = (size_t)cfg->max_batch;
   const size_t plane6 = (size_t)6 * c->NY * c->Mm * 16, plane3 = (size_t)3 * c->NY * c->Mm * 16;
   const size_t grid = (size_t)c->NY * c->nx * c->nz;
@@ -147,6 +146,8 @@ extern "C" sp_status sp_create(const sp_config* cfg, sp_ctx** out) {
             cudaMalloc((void**)&c->tmp, B * c->state_len * 8) == cudaSuccess &&
             cudaMalloc((void**)&c->red, (size_t)64 * c->red_blocks * 8 + 4096) == cudaSuccess &&
             cudaMallocHost((void**)&c->red_host, (size_t)64 * c->red_blocks * 8 + 4096) == cudaSuccess;
+  const size_t gplane = sp_xz_global_plane_bytes(c);
+  if (ok && gplane) ok = cudaMalloc(&c->wsG, B * gplane) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     return bail(SP_ENOMEM, "workspace allocation");
@@ -338,79 +339,138 @@ extern "C" sp_status sp_seed_state(sp_ctx* c, const double* ra, const double* rb
 // ================================================================= Newton
 namespace {
 
-// one-sided Jacobi SVD of the m x n matrix A (column-major, m >= n):
-// A = U diag(s) V^T; A is overwritten by U diag(s)
-void jacobi_svd(std::vector<double>& A, int m, int n, std::vector<double>& s, std::vector<double>& V) {
-  V.assign((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        double alpha = 0, beta = 0, gamma = 0;
-        for (int i = 0; i < m; ++i) {
-          const double ap = A[(size_t)p * m + i], aq = A[(size_t)q * m + i];
-          alpha += ap * ap;
-          beta += aq * aq;
-          gamma += ap * aq;
-        }
-        if (gamma == 0.0) continue;
-        const double rel = std::fabs(gamma) / std::sqrt(alpha * beta);
-        if (rel > off) off = rel;
-        if (rel < 1e-15) continue;
-        const double zeta = (beta - alpha) / (2.0 * gamma);
-        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = cs * t;
-        for (int i = 0; i < m; ++i) {
-          const double ap = A[(size_t)p * m + i], aq = A[(size_t)q * m + i];
-          A[(size_t)p * m + i] = cs * ap - sn * aq;
-          A[(size_t)q * m + i] = sn * ap + cs * aq;
-        }
-        for (int i = 0; i < n; ++i) {
-          const double vp = V[(size_t)p * n + i], vq = V[(size_t)q * n + i];
-          V[(size_t)p * n + i] = cs * vp - sn * vq;
-          V[(size_t)q * n + i] = sn * vp + cs * vq;
-        }
-      }
-    if (off < 1e-15) break;
-  }
-  s.assign(n, 0.0);
-  for (int j = 0; j < n; ++j) {
-    double acc = 0;
-    for (int i = 0; i < m; ++i) acc += A[(size_t)j * m + i] * A[(size_t)j * m + i];
-    s[j] = std::sqrt(acc);
-  }
-}
+// Trust-region subproblem min |g - R y| s.t. |y| <= delta in the Krylov space (the hookstep,
+// Sec. 3.2): R^T R = Q T Q^T by Householder tridiagonalisation (once per Newton step), then
+// for each radius a safeguarded Newton iteration on 1/|z(mu)| - 1/delta with
+// z(mu) = (T + mu I)^-1 Q^T R^T g (two tridiagonal solves per iteration), y = Q z.
+struct TrustRegion {
+  int k = 0;
+  std::vector<double> d, e, c, V;  // diagonal, off-diagonal, Q^T b, Householder vectors (k x k)
+  std::vector<double> beta;        // reflector scalars
 
-// z minimising |p - diag(s) z| with |z| <= delta (hookstep, Sec. 3.2)
-std::vector<double> hook(const std::vector<double>& s, const std::vector<double>& p, double delta) {
-  const int n = (int)s.size();
-  std::vector<double> z(n);
-  double nz = 0;
-  for (int i = 0; i < n; ++i) {
-    z[i] = s[i] > 0 ? p[i] / s[i] : 0.0;
-    nz += z[i] * z[i];
-  }
-  if (std::sqrt(nz) <= delta) return z;
-  double smax = 0, spmax = 0;
-  for (int i = 0; i < n; ++i) {
-    smax = std::max(smax, s[i]);
-    spmax = std::max(spmax, s[i] * std::fabs(p[i]));
-  }
-  double lo = 0, hi = spmax / delta + smax * smax;
-  for (int it = 0; it < 200; ++it) {
-    const double mu = 0.5 * (lo + hi);
-    double acc = 0;
-    for (int i = 0; i < n; ++i) {
-      const double zi = s[i] * p[i] / (s[i] * s[i] + mu);
-      acc += zi * zi;
+  void setup(const double* R, int ld, int k_, const double* g) {
+    k = k_;
+    std::vector<double> M((size_t)k * k, 0.0), b(k, 0.0);
+    for (int i = 0; i < k; ++i)
+      for (int j = i; j < k; ++j) {
+        double acc = 0;
+        for (int l = 0; l <= i; ++l) acc += R[(size_t)i * ld + l] * R[(size_t)j * ld + l];
+        M[(size_t)i * k + j] = M[(size_t)j * k + i] = acc;
+      }
+    for (int j = 0; j < k; ++j) {
+      double acc = 0;
+      for (int l = 0; l <= j; ++l) acc += R[(size_t)j * ld + l] * g[l];
+      b[j] = acc;
     }
-    if (std::sqrt(acc) > delta) lo = mu;
-    else hi = mu;
+    V.assign((size_t)k * k, 0.0);
+    beta.assign(k, 0.0);
+    std::vector<double> p(k), wv(k);
+    for (int col = 0; col + 2 < k; ++col) {
+      // reflector zeroing M[col+2.., col]
+      double alpha = 0;
+      for (int i = col + 1; i < k; ++i) alpha += M[(size_t)i * k + col] * M[(size_t)i * k + col];
+      alpha = std::sqrt(alpha);
+      if (alpha == 0.0) continue;
+      const double x0 = M[(size_t)(col + 1) * k + col];
+      const double s = x0 >= 0 ? -alpha : alpha;
+      double* v = V.data() + (size_t)col * k;
+      for (int i = 0; i < k; ++i) v[i] = 0.0;
+      v[col + 1] = x0 - s;
+      for (int i = col + 2; i < k; ++i) v[i] = M[(size_t)i * k + col];
+      double vv = 0;
+      for (int i = col + 1; i < k; ++i) vv += v[i] * v[i];
+      if (vv == 0.0) continue;
+      const double bt = 2.0 / vv;
+      beta[col] = bt;
+      // M <- H M H with H = I - bt v v^T (symmetric rank-2 update)
+      for (int i = col; i < k; ++i) {
+        double acc = 0;
+        for (int j = col + 1; j < k; ++j) acc += M[(size_t)i * k + j] * v[j];
+        p[i] = bt * acc;
+      }
+      double vp = 0;
+      for (int i = col + 1; i < k; ++i) vp += v[i] * p[i];
+      const double kk = 0.5 * bt * vp;
+      for (int i = col; i < k; ++i) wv[i] = p[i] - kk * (i > col ? v[i] : 0.0);
+      for (int i = col; i < k; ++i)
+        for (int j = col; j < k; ++j) {
+          const double vi = i > col ? v[i] : 0.0, vj = j > col ? v[j] : 0.0;
+          M[(size_t)i * k + j] -= vi * wv[j] + wv[i] * vj;
+        }
+    }
+    d.assign(k, 0.0);
+    e.assign(k, 0.0);
+    for (int i = 0; i < k; ++i) d[i] = M[(size_t)i * k + i];
+    for (int i = 0; i + 1 < k; ++i) e[i] = M[(size_t)(i + 1) * k + i];
+    // c = Q^T b, Q = H_0 H_1 ... (apply H_0 first)
+    c = b;
+    for (int col = 0; col + 2 < k; ++col) apply(col, c);
   }
-  for (int i = 0; i < n; ++i) z[i] = s[i] * p[i] / (s[i] * s[i] + hi);
-  return z;
-}
+
+  void apply(int col, std::vector<double>& x) const {
+    if (beta[col] == 0.0) return;
+    const double* v = V.data() + (size_t)col * k;
+    double acc = 0;
+    for (int i = col + 1; i < k; ++i) acc += v[i] * x[i];
+    acc *= beta[col];
+    for (int i = col + 1; i < k; ++i) x[i] -= acc * v[i];
+  }
+
+  // (T + mu I) z = rhs by the Thomas algorithm (T + mu I is positive definite for mu > 0)
+  void tri_solve(double mu, const std::vector<double>& rhs, std::vector<double>& z) const {
+    std::vector<double> cp(k), dp(k);
+    double den = d[0] + mu;
+    cp[0] = k > 1 ? e[0] / den : 0.0;
+    dp[0] = rhs[0] / den;
+    for (int i = 1; i < k; ++i) {
+      den = d[i] + mu - e[i - 1] * cp[i - 1];
+      cp[i] = i + 1 < k ? e[i] / den : 0.0;
+      dp[i] = (rhs[i] - e[i - 1] * dp[i - 1]) / den;
+    }
+    z.assign(k, 0.0);
+    z[k - 1] = dp[k - 1];
+    for (int i = k - 2; i >= 0; --i) z[i] = dp[i] - cp[i] * z[i + 1];
+  }
+
+  std::vector<double> solve(double delta) const {
+    double tmax = 0;
+    for (int i = 0; i < k; ++i)
+      tmax = std::max(tmax, std::fabs(d[i]) + (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(e[i]) : 0.0));
+    double cn = 0;
+    for (double v : c) cn += v * v;
+    cn = std::sqrt(cn);
+    double lo = 0.0, hi = cn / delta + tmax;   // |z(hi)| <= delta
+    double mu = std::max(1e-12 * tmax, 1e-300);
+    std::vector<double> z, z2;
+    for (int it = 0; it < 100; ++it) {
+      tri_solve(mu, c, z);
+      double nz = 0;
+      for (double v : z) nz += v * v;
+      nz = std::sqrt(nz);
+      if (!std::isfinite(nz)) {  // mu too close to the spectrum's bottom
+        lo = mu;
+        mu = 0.5 * (lo + hi);
+        continue;
+      }
+      if (std::fabs(nz - delta) <= 1e-10 * delta) break;
+      if (nz > delta) lo = mu;
+      else hi = mu;
+      tri_solve(mu, z, z2);
+      double zz2 = 0;
+      for (int i = 0; i < k; ++i) zz2 += z[i] * z2[i];
+      // Newton step on phi(mu) = 1/|z| - 1/delta, phi' = (z . z2)/|z|^3
+      double step = (1.0 / nz - 1.0 / delta) * nz * nz * nz / std::max(zz2, 1e-300);
+      double next = mu - step;
+      if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
+      if (hi - lo <= 1e-15 * hi) { mu = hi; tri_solve(mu, c, z); break; }
+      mu = next;
+    }
+    // y = Q z: apply the reflectors in reverse order
+    std::vector<double> y = z;
+    for (int col = k - 3; col >= 0; --col) apply(col, y);
+    return y;
+  }
+};
 
 double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -425,20 +485,31 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   if (K < 1 || K > 4096 || o->max_newton < 0) return sp_fail(c, SP_EINVAL, "sp_newton_gmres: bad options");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t L = c->state_len;
-  if (c->kry_cap < K + 3) {
+  // one partial sum per ~1024 complex values, at most red_blocks
+  const int nb = (int)std::max<size_t>(1, std::min<size_t>(c->red_blocks, (c->cplx_per_state + 1023) / 1024));
+  // device scratch after the basis: partials, hA, hB, hn/inv
+  const size_t extra = (size_t)(K + 2) * nb + 3 * (size_t)(K + 3) + 8;
+  if (c->kry_cap < K + 5) {
     if (c->kry) cudaFree(c->kry);
     c->kry = nullptr;
     c->kry_cap = 0;
-    if (cudaMalloc((void**)&c->kry, ((size_t)(K + 3) * L + K + 8) * 8) != cudaSuccess) {
+    if (cudaMalloc((void**)&c->kry, ((size_t)(K + 5) * L + extra) * 8) != cudaSuccess) {
       cudaGetLastError();
       return sp_fail(c, SP_ENOMEM, "Krylov basis allocation");
     }
-    c->kry_cap = K + 3;
+    c->kry_cap = K + 5;
   }
-  double* V = c->kry;                       // K+1 basis vectors
-  double* F = c->kry + (size_t)(K + 1) * L; // residual
-  double* Ut = c->kry + (size_t)(K + 2) * L;// trial state
-  double* dh = c->kry + (size_t)(K + 3) * L;  // device copy of h or y (K + 1 doubles)
+  double* V = c->kry;                           // K+2 basis vectors
+  double* F = c->kry + (size_t)(K + 2) * L;     // residual
+  double* Ut = c->kry + (size_t)(K + 3) * L;    // trial state
+  double* Zg = c->kry + (size_t)(K + 4) * L;    // gradient direction (use_gradient)
+  double* dpart = c->kry + (size_t)(K + 5) * L; // partial sums
+  double* dhA = dpart + (size_t)(K + 2) * nb;   // first Gram-Schmidt pass
+  double* dhB = dhA + (K + 3);                  // second pass
+  double* dhn = dhB + (K + 3);                  // [0] = |w|, [1] = 1/|w|, then y
+  double* hbuf = c->red_host;                   // pinned: hA | hB | hn
+  if ((size_t)2 * (K + 3) + 2 > (size_t)64 * c->red_blocks + 512)
+    return sp_fail(c, SP_EINVAL, "sp_newton_gmres: Krylov dimension too large for the pinned buffer");
   sp_newton_report r{};
   const double t0 = now_ms();
   sp_status s;
@@ -452,7 +523,9 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   double nU;
   if ((s = norm(U, &nU)) != SP_OK) return s;
   double delta = o->delta0 > 0 ? o->delta0 : 0.1 * std::max(std::sqrt(nU), 1.0);
-  std::vector<double> H((size_t)(K + 1) * K), h(K + 1), h2(K + 1);
+  // H: unrotated Hessenberg (column-major, ld K+1); R: the same after the Givens rotations
+  const int LD = K + 2;  // leading dimension of H and R (one extra row and column for the gradient)
+  std::vector<double> H((size_t)LD * (K + 1)), R((size_t)LD * (K + 1)), g(K + 2), cs(K + 1), sn(K + 1);
   sp_status result = SP_ENOTCONV;
   for (int it = 0; it <= o->max_newton; ++it) {
     if (!std::isfinite(nF)) { result = SP_ENAN; break; }
@@ -460,10 +533,50 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     if (it == o->max_newton) break;
     if ((s = sp_set_base(c, U, st)) != SP_OK) return s;
     r.total_steps++;
-    // GMRES, classical Gram-Schmidt applied twice, basis in V
-    std::fill(H.begin(), H.end(), 0.0);
+    // GMRES without restarts; classical Gram-Schmidt applied twice, all reductions on the device
     if ((s = sp_cuda(c, launch_axpby(V, 1.0 / nF, F, 0.0, nullptr, L, st), "v0")) != SP_OK) return s;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = nF;
     int k = 0;
+    // orthogonalise w = (action on column j) against V[0..j] (CGS2 on the device), normalise it
+    // into V[j+1], and update column j of H, its Givens-rotated copy R and the residual g
+    auto orth_column = [&](int j, double* w, double* hn_out) -> sp_status {
+      sp_status q;
+      if ((q = sp_cuda(c, launch_dev_dots(c, V, j + 1, w, dpart, nb, dhA, nullptr, st), "dots")) != SP_OK) return q;
+      if ((q = sp_cuda(c, launch_multi_axpy(c, V, j + 1, dhA, w, st), "axpy")) != SP_OK) return q;
+      if ((q = sp_cuda(c, launch_dev_dots(c, V, j + 1, w, dpart, nb, dhB, nullptr, st), "dots")) != SP_OK) return q;
+      if ((q = sp_cuda(c, launch_multi_axpy(c, V, j + 1, dhB, w, st), "axpy")) != SP_OK) return q;
+      if ((q = sp_cuda(c, launch_dev_norm(c, w, dpart, nb, dhn, dhn + 1, st), "norm")) != SP_OK) return q;
+      if ((q = sp_cuda(c, launch_scale_dev(c, w, dhn + 1, st), "scale")) != SP_OK) return q;
+      if ((q = sp_cuda(c, cudaMemcpyAsync(hbuf, dhA, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, st), "h")) != SP_OK)
+        return q;
+      if ((q = sp_cuda(c, cudaMemcpyAsync(hbuf + K + 3, dhB, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, st), "h")) !=
+          SP_OK)
+        return q;
+      if ((q = sp_cuda(c, cudaMemcpyAsync(hbuf + 2 * (K + 3), dhn, 8, cudaMemcpyDeviceToHost, st), "h")) != SP_OK)
+        return q;
+      if ((q = sp_cuda(c, cudaStreamSynchronize(st), "orth sync")) != SP_OK) return q;
+      const double hn = hbuf[2 * (K + 3)];
+      double* Hc = H.data() + (size_t)j * LD;
+      double* Rc = R.data() + (size_t)j * LD;
+      for (int i = 0; i <= j; ++i) Hc[i] = hbuf[i] + hbuf[K + 3 + i];
+      Hc[j + 1] = hn;
+      for (int i = 0; i <= j + 1; ++i) Rc[i] = Hc[i];
+      for (int i = 0; i < j; ++i) {  // earlier rotations, then a new one for (j, j+1)
+        const double x = Rc[i], y = Rc[i + 1];
+        Rc[i] = cs[i] * x + sn[i] * y;
+        Rc[i + 1] = -sn[i] * x + cs[i] * y;
+      }
+      const double rr = std::hypot(Rc[j], Rc[j + 1]);
+      cs[j] = rr > 0 ? Rc[j] / rr : 1.0;
+      sn[j] = rr > 0 ? Rc[j + 1] / rr : 0.0;
+      Rc[j] = rr;
+      Rc[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      *hn_out = hn;
+      return SP_OK;
+    };
     for (int j = 0; j < K; ++j) {
       double* vj = V + (size_t)j * L;
       double* w = V + (size_t)(j + 1) * L;
@@ -471,81 +584,92 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
       if (o->use_fd) s = sp_jvp_fd(c, vj, w, 1, st);
       else s = sp_jvp(c, vj, w, 1, st);
       if (s != SP_OK) return s;
-      if ((s = sp_cuda(c, cudaStreamSynchronize(st), "jvp sync")) != SP_OK) return s;
+      if (r.t_action_ms >= 0) {
+        if ((s = sp_cuda(c, cudaStreamSynchronize(st), "jvp sync")) != SP_OK) return s;
+      }
       double tb = now_ms();
       r.t_action_ms += tb - ta;
       r.total_jvps++;
-      for (int pass = 0; pass < 2; ++pass) {
-        std::vector<double>& hh = pass == 0 ? h : h2;
-        if ((s = inner_many(c, V, j + 1, w, hh.data(), st)) != SP_OK) return s;
-        if ((s = sp_cuda(c, cudaMemcpyAsync(dh, hh.data(), (size_t)(j + 1) * 8, cudaMemcpyHostToDevice, st),
-                         "h copy")) != SP_OK)
-          return s;
-        if ((s = sp_cuda(c, launch_multi_axpy(c, V, j + 1, dh, w, st), "axpy")) != SP_OK) return s;
-        if ((s = sp_cuda(c, cudaStreamSynchronize(st), "orth sync")) != SP_OK) return s;
-      }
-      for (int i = 0; i <= j; ++i) H[(size_t)j * (K + 1) + i] = h[i] + h2[i];
-      double hn;
-      if ((s = norm(w, &hn)) != SP_OK) return s;
-      hn = std::sqrt(hn);
-      H[(size_t)j * (K + 1) + j + 1] = hn;
-      k = j + 1;
-      if (hn > 0)
-        if ((s = sp_cuda(c, launch_scale(w, 1.0 / hn, L, st), "scale")) != SP_OK) return s;
+      double hn = 0;
+      if ((s = orth_column(j, w, &hn)) != SP_OK) return s;
       r.t_orth_ms += now_ms() - tb;
-      // least-squares residual of beta e1 - H_k y via Givens on a copy
-      std::vector<double> Hc((size_t)(k + 1) * k), g(k + 1, 0.0);
-      for (int cc = 0; cc < k; ++cc)
-        for (int i = 0; i <= k; ++i) Hc[(size_t)cc * (k + 1) + i] = H[(size_t)cc * (K + 1) + i];
-      g[0] = nF;
-      for (int cc = 0; cc < k; ++cc) {
-        const double a = Hc[(size_t)cc * (k + 1) + cc], b = Hc[(size_t)cc * (k + 1) + cc + 1];
-        const double rr = std::hypot(a, b);
-        if (rr == 0) continue;
-        const double cs = a / rr, sn = b / rr;
-        for (int c2 = cc; c2 < k; ++c2) {
-          const double x = Hc[(size_t)c2 * (k + 1) + cc], y = Hc[(size_t)c2 * (k + 1) + cc + 1];
-          Hc[(size_t)c2 * (k + 1) + cc] = cs * x + sn * y;
-          Hc[(size_t)c2 * (k + 1) + cc + 1] = -sn * x + cs * y;
-        }
-        const double x = g[cc], y = g[cc + 1];
-        g[cc] = cs * x + sn * y;
-        g[cc + 1] = -sn * x + cs * y;
-      }
+      k = j + 1;
+      if (!std::isfinite(hn)) return sp_fail(c, SP_ENAN, "non-finite Arnoldi vector");
       if (std::fabs(g[k]) <= o->eta * nF || hn == 0.0) break;
     }
-    // hookstep on the (k+1) x k Hessenberg matrix
-    std::vector<double> A((size_t)(k + 1) * k), sv, Vs;
-    for (int cc = 0; cc < k; ++cc)
-      for (int i = 0; i <= k; ++i) A[(size_t)cc * (k + 1) + i] = H[(size_t)cc * (K + 1) + i];
-    std::vector<double> Acopy = A;
-    jacobi_svd(A, k + 1, k, sv, Vs);
-    std::vector<double> p(k);
-    for (int i = 0; i < k; ++i) p[i] = sv[i] > 0 ? nF * A[(size_t)i * (k + 1) + 0] / sv[i] : 0.0;
+    // optional extra direction: the steepest-descent direction J^* F of |F|^2 / 2,
+    // made orthogonal to the Krylov basis; one more (flexible) Arnoldi column
+    bool grad_col = false;
+    if (o->use_gradient && k >= 1) {
+      if ((s = sp_vjp(c, F, Zg, 1, st)) != SP_OK) return s;
+      double* w = V + (size_t)(k + 1) * L;
+      for (int pass = 0; pass < 2; ++pass) {
+        if ((s = sp_cuda(c, launch_dev_dots(c, V, k + 1, Zg, dpart, nb, dhA, nullptr, st), "dots")) != SP_OK) return s;
+        if ((s = sp_cuda(c, launch_multi_axpy(c, V, k + 1, dhA, Zg, st), "axpy")) != SP_OK) return s;
+      }
+      // z must also be orthogonal to v_k (the last Krylov vector) for the update formula below
+      if ((s = sp_cuda(c, launch_dev_norm(c, Zg, dpart, nb, dhn, dhn + 1, st), "norm")) != SP_OK) return s;
+      if ((s = sp_cuda(c, cudaMemcpyAsync(hbuf, dhn, 16, cudaMemcpyDeviceToHost, st), "zn")) != SP_OK) return s;
+      if ((s = sp_cuda(c, cudaStreamSynchronize(st), "zn sync")) != SP_OK) return s;
+      if (hbuf[0] > 1e-12 * nF && std::isfinite(hbuf[0])) {
+        if ((s = sp_cuda(c, launch_scale_dev(c, Zg, dhn + 1, st), "scale")) != SP_OK) return s;
+        if ((s = sp_jvp(c, Zg, w, 1, st)) != SP_OK) return s;
+        r.total_jvps++;
+        double hn = 0;
+        if ((s = orth_column(k, w, &hn)) != SP_OK) return s;
+        if (std::isfinite(hn)) {
+          grad_col = true;
+          k = k + 1;
+        }
+      }
+    }
+    // hookstep: minimise |g - R y| (R = rotated k x k Hessenberg) subject to |y| <= delta.
+    // The constrained minimiser is y(mu) = (R^T R + mu I)^-1 R^T g with mu >= 0 chosen so that
+    // |y(mu)| = delta; R^T R = Q T Q^T (tridiagonal T) makes every |y(mu)| an O(k) solve.
+    std::vector<double> y0(k, 0.0);
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int jj = i + 1; jj < k; ++jj) acc -= R[(size_t)jj * LD + i] * y0[jj];
+      y0[i] = R[(size_t)i * LD + i] != 0.0 ? acc / R[(size_t)i * LD + i] : 0.0;
+    }
+    double ny0 = 0;
+    for (double v : y0) ny0 += v * v;
+    ny0 = std::sqrt(ny0);
+    TrustRegion tr;
+    bool have_tr = false;
     bool accepted = false;
     double nT = nF;
     for (int trial = 0; trial < 12; ++trial) {
-      std::vector<double> z = hook(sv, p, delta), y(k, 0.0);
-      for (int i = 0; i < k; ++i)
-        for (int jj = 0; jj < k; ++jj) y[i] += Vs[(size_t)jj * k + i] * z[jj];
+      std::vector<double> y;
+      if (ny0 <= delta) {
+        y = y0;
+      } else {
+        if (!have_tr) {
+          tr.setup(R.data(), LD, k, g.data());
+          have_tr = true;
+        }
+        y = tr.solve(delta);
+      }
+      // predicted residual |g - R y|^2 + g_k^2
+      double pred2 = g[k] * g[k];
+      for (int i = 0; i < k; ++i) {
+        double acc = g[i];
+        for (int jj = i; jj < k; ++jj) acc -= R[(size_t)jj * LD + i] * y[jj];
+        pred2 += acc * acc;
+      }
       double ylen = 0;
       for (double v : y) ylen += v * v;
       ylen = std::sqrt(ylen);
-      // predicted residual |beta e1 - H y|
-      double pred = 0;
-      for (int i = 0; i <= k; ++i) {
-        double acc = i == 0 ? nF : 0.0;
-        for (int cc = 0; cc < k; ++cc) acc -= Acopy[(size_t)cc * (k + 1) + i] * y[cc];
-        pred += acc * acc;
-      }
-      pred = std::sqrt(pred);
-      // U_trial = U - V y
-      std::vector<double> ny(k);
-      for (int i = 0; i < k; ++i) ny[i] = y[i];
+      const double pred = std::sqrt(pred2);
       if ((s = sp_cuda(c, cudaMemcpyAsync(Ut, U, L * 8, cudaMemcpyDeviceToDevice, st), "copy")) != SP_OK) return s;
-      if ((s = sp_cuda(c, cudaMemcpyAsync(dh, ny.data(), (size_t)k * 8, cudaMemcpyHostToDevice, st), "y copy")) != SP_OK)
+      if ((s = sp_cuda(c, cudaMemcpyAsync(dhn + 2, y.data(), (size_t)k * 8, cudaMemcpyHostToDevice, st), "y copy")) !=
+          SP_OK)
         return s;
-      if ((s = sp_cuda(c, launch_multi_axpy(c, V, k, dh, Ut, st), "update")) != SP_OK) return s;
+      // U_trial = U - sum y_i z_i with z_i = v_i (Krylov) and, last, the gradient direction
+      const int kv = grad_col ? k - 1 : k;
+      if ((s = sp_cuda(c, launch_multi_axpy(c, V, kv, dhn + 2, Ut, st), "update")) != SP_OK) return s;
+      if (grad_col)
+        if ((s = sp_cuda(c, launch_multi_axpy(c, Zg, 1, dhn + 2 + kv, Ut, st), "update")) != SP_OK) return s;
       if ((s = step_batch(c, Ut, F, 1, st)) != SP_OK) return s;
       r.total_steps++;
       if ((s = norm(F, &nT)) != SP_OK) return s;
@@ -562,7 +686,6 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
       break;
     }
     if (!accepted) {
-      // restore F for the report and stop: the trust region collapsed
       if ((s = step_batch(c, U, F, 1, st)) != SP_OK) return s;
       break;
     }

@@ -220,6 +220,7 @@ struct XzArgs {
   int nx, nz, NY, Mm, MX, MZ, Kx, Kz;
   int rp, cx;         // row pairs per z chunk, columns per x chunk
   int FS, RS;         // field and row strides of the plane buffer G
+  C2<T>* Gg;          // if non-null, the plane buffers live here, [dir][NY][nx * RS] (large grids)
 };
 
 // MODE XZ_ADJOINT runs the transpose of the tangent's plane stage: the
@@ -234,8 +235,10 @@ __global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* stwx = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* stwz = stwx + a.nx;
-  C2<T>* G = stwz + a.nz;                       // [nx][6][FS] (row stride RS)
-  C2<T>* S = G + (size_t)a.nx * a.RS;           // scratch
+  // plane buffer G [nx][6][FS] (row stride RS): in shared memory, or in global
+  // memory (L2-resident) for grids whose plane does not fit on chip
+  C2<T>* G = a.Gg ? a.Gg + ((size_t)blockIdx.y * a.NY + blockIdx.x) * a.nx * a.RS : stwz + a.nz;
+  C2<T>* S = a.Gg ? stwz + a.nz : G + (size_t)a.nx * a.RS;  // scratch
   const int j = blockIdx.x;
   const int dir = blockIdx.y;
   const int nx = a.nx, nz = a.nz, MZ = a.MZ, Kx = a.Kx, Kz = a.Kz;
@@ -561,40 +564,45 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict
     srv[(t * 2 + Pa) * a.cv + (Pa == 0 ? rv0 : rv1) + n / 2] = fta;
   }
   __syncthreads();
-  // phase D: apply the per-mode operators (FP64)
+  // phase D: apply the per-mode operators (FP64). The mean-mode test is hoisted
+  // out of the loops so that no predicated-off double FMA occupies the FP64 pipe.
   for (int idx = threadIdx.x; idx < TM * NY; idx += blockDim.x) {
     const int t = idx / NY, n = idx - t * NY;
     if (s_u[t] >= a.n_unique) continue;
     const double* op = a.ops + (size_t)s_u[t] * a.op_stride;
     const int Q = n & 1, row = n >> 1;
-    const bool mean = (s_pos[t] == 0 && s_iz[t] == 0);
-    // Helmholtz (b, or the mean u and w)
     const int rb = Q == 0 ? a.rb0 : a.rb1;
     const double* H = op + (Q == 0 ? a.off_h0 : a.off_h1) + (size_t)row * rb;
-    double2 accb = make_double2(0.0, 0.0), accw = accb;
-    for (int cidx = 0; cidx < rb; ++cidx) {
-      const double h = __ldg(H + cidx);
-      const double2 fb = sfb[t * NR + Q + 2 * cidx];
-      accb.x += h * fb.x;
-      accb.y += h * fb.y;
-      if (mean) {
-        const double2 fw = sfw[t * NR + Q + 2 * cidx];
-        accw.x += h * fw.x;
-        accw.y += h * fw.y;
+    const double2* fbq = sfb + t * NR + Q;
+    if (s_pos[t] == 0 && s_iz[t] == 0) {
+      // mean flow: u and w from the Helmholtz operator, v = 0
+      const double2* fwq = sfw + t * NR + Q;
+      double2 accb = make_double2(0.0, 0.0), accw = accb;
+      for (int cidx = 0; cidx < rb; ++cidx) {
+        const double h = __ldg(H + cidx);
+        accb.x = fma(h, fbq[2 * cidx].x, accb.x);
+        accb.y = fma(h, fbq[2 * cidx].y, accb.y);
+        accw.x = fma(h, fwq[2 * cidx].x, accw.x);
+        accw.y = fma(h, fwq[2 * cidx].y, accw.y);
       }
-    }
-    sb[t * NY + n] = accb;
-    if (mean) {
+      sb[t * NY + n] = accb;
       sv[t * NY + n] = accw;
       continue;
     }
+    double2 accb = make_double2(0.0, 0.0);
+    for (int cidx = 0; cidx < rb; ++cidx) {
+      const double h = __ldg(H + cidx);
+      accb.x = fma(h, fbq[2 * cidx].x, accb.x);
+      accb.y = fma(h, fbq[2 * cidx].y, accb.y);
+    }
+    sb[t * NY + n] = accb;
     const double* V = op + (Q == 0 ? a.off_v0 : a.off_v1) + (size_t)row * a.cv;
     const double2* r = srv + (t * 2 + Q) * a.cv;
     double2 accv = make_double2(0.0, 0.0);
     for (int cidx = 0; cidx < a.cv; ++cidx) {
       const double vv = __ldg(V + cidx);
-      accv.x += vv * r[cidx].x;
-      accv.y += vv * r[cidx].y;
+      accv.x = fma(vv, r[cidx].x, accv.x);
+      accv.y = fma(vv, r[cidx].y, accv.y);
     }
     sv[t * NY + n] = accv;
   }
@@ -1087,11 +1095,70 @@ __global__ void k_multi_inner(const double2* V, int k, size_t ncplx, const doubl
   if (threadIdx.x == 0) partials[(size_t)i * gridDim.x + blockIdx.x] = acc;
 }
 
+// partial weighted inner products of 8 rows of V with w per block row: grid (nb, ceil(k/8))
+__global__ void k_multi_inner8(const double2* V, int k, size_t ncplx, const double2* w, int NY, int MZ,
+                               double* partials) {
+  const int i0 = blockIdx.y * 8;
+  double acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ncplx; e += (size_t)gridDim.x * blockDim.x) {
+    const int iz = (int)((e / NY) % MZ);
+    const double wt = iz == 0 ? 1.0 : 2.0;
+    const double2 b = w[e];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (i0 + q < k) {
+        const double2 a = V[(size_t)(i0 + q) * ncplx + e];
+        acc[q] += wt * (a.x * b.x + a.y * b.y);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double s = block_sum(acc[q]);
+    if (threadIdx.x == 0 && i0 + q < k) partials[(size_t)(i0 + q) * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// out[i] = sum_b partials[i][b] (+ add[i] if add != null); one block per i
+__global__ void k_reduce_rows(const double* partials, int nb, double* out, const double* add) {
+  const int i = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partials[(size_t)i * nb + b];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[i] = acc + (add ? add[i] : 0.0);
+}
+
+// h = sqrt(sum of partials); inv = 1/h (0 if h == 0)
+__global__ void k_norm_finish(const double* partials, int nb, double* h, double* inv) {
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partials[b];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    const double s = sqrt(fmax(acc, 0.0));
+    *h = s;
+    *inv = s > 0.0 ? 1.0 / s : 0.0;
+  }
+}
+
+__global__ void k_scale_dev(double* x, size_t n, const double* s) {
+  const double f = *s;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] *= f;
+}
+
 __global__ void k_multi_axpy(const double* V, int k, size_t n, const double* h, double* w) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    double acc = w[e];
-    for (int i = 0; i < k; ++i) acc -= h[i] * V[(size_t)i * n + e];
-    w[e] = acc;
+    // eight independent partial sums keep eight loads in flight
+    double acc[8] = {w[e], 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int i = 0;
+    for (; i + 8 <= k; i += 8) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] -= h[i + q] * V[(size_t)(i + q) * n + e];
+    }
+    for (; i < k; ++i) acc[0] -= h[i] * V[(size_t)i * n + e];
+    w[e] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
   }
 }
 
@@ -1109,40 +1176,53 @@ int grid_for(size_t n, int threads, int sms) {
 }  // namespace
 
 // ================================================================ launchers
-static size_t xz_smem_bytes(const sp_ctx* c, int esize, int rp, int cx) {
+static size_t xz_smem_bytes(const sp_ctx* c, int esize, int rp, int cx, bool g_on_chip) {
   const int FS = c->MZ + 1, RS = 6 * FS;
   size_t scr = (size_t)2 * cx * c->nx;
   size_t zs = (size_t)24 * rp * c->nz;
   if (zs > scr) scr = zs;
-  return (size_t)esize * 2 * ((size_t)c->nx + c->nz + (size_t)c->nx * RS + scr);
+  return (size_t)esize * 2 * ((size_t)c->nx + c->nz + (g_on_chip ? (size_t)c->nx * RS : 0) + scr);
 }
 
-// pick the largest chunking that fits the shared-memory budget
-static bool xz_config(const sp_ctx* c, int esize, int* rp, int* cx, size_t* bytes) {
-  // prefer two resident blocks per SM (about 113 KB each), else one (up to 220 KB)
-  for (size_t budget : {(size_t)113 * 1024, (size_t)220 * 1024}) {
-  for (int r = 4; r >= 1; --r) {
-    int scr_c = 24 * r * c->nz;
-    int x = scr_c / (2 * c->nx);
-    if (x < 1) x = 1;
-    if (x > 6 * c->MZ) x = 6 * c->MZ;
-    size_t b = xz_smem_bytes(c, esize, r, x);
-    if (b <= budget) {
-      *rp = r;
-      *cx = x;
-      *bytes = b;
-      return true;
+// pick the largest chunking that fits the shared-memory budget; the plane buffer
+// moves to global memory only when it cannot fit on chip
+static bool xz_config(const sp_ctx* c, int esize, int* rp, int* cx, size_t* bytes, int* g_glob) {
+  for (int glob = 0; glob <= 1; ++glob) {
+    // prefer two resident blocks per SM (about 113 KB each), else one (up to 220 KB)
+    for (size_t budget : {(size_t)113 * 1024, (size_t)220 * 1024}) {
+      for (int r = 4; r >= 1; --r) {
+        int scr_c = 24 * r * c->nz;
+        int x = scr_c / (2 * c->nx);
+        if (x < 1) x = 1;
+        if (x > 6 * c->MZ) x = 6 * c->MZ;
+        size_t b = xz_smem_bytes(c, esize, r, x, glob == 0);
+        if (b <= budget) {
+          *rp = r;
+          *cx = x;
+          *bytes = b;
+          *g_glob = glob;
+          return true;
+        }
+      }
     }
-  }
   }
   return false;
 }
 
 bool sp_xz_fits(sp_ctx* c) {
-  bool ok64 = xz_config(c, 8, &c->xz_rp64, &c->xz_cx64, &c->smem_xz64);
-  bool ok32 = xz_config(c, 4, &c->xz_rp32, &c->xz_cx32, &c->smem_xz32);
+  bool ok64 = xz_config(c, 8, &c->xz_rp64, &c->xz_cx64, &c->smem_xz64, &c->xz_gglob64);
+  bool ok32 = xz_config(c, 4, &c->xz_rp32, &c->xz_cx32, &c->smem_xz32, &c->xz_gglob32);
   if (!ok64) c->smem_xz64 = 0;
-  return ok32;
+  return ok32 && ok64;
+}
+
+size_t sp_xz_global_plane_bytes(const sp_ctx* c) {
+  const size_t RS = 6 * (size_t)(c->MZ + 1);
+  const size_t per = (size_t)c->NY * c->nx * RS;  // complex values per direction
+  size_t b = 0;
+  if (c->xz_gglob64) b = per * 16;
+  if (c->xz_gglob32 && per * 8 > b) b = per * 8;
+  return b;
 }
 
 cudaError_t launch_yinv(const sp_ctx* c, bool fp32, const double* in, void* out6, int n_dir,
@@ -1186,6 +1266,9 @@ static cudaError_t launch_xz_t(const sp_ctx* c, const void* in6, void* out3, T* 
   a.rp = rp; a.cx = cx;
   a.FS = c->MZ + 1;
   a.RS = 6 * a.FS;
+  const bool glob = sizeof(T) == 8 ? c->xz_gglob64 : c->xz_gglob32;
+  a.Gg = glob ? reinterpret_cast<C2<T>*>(c->wsG) : nullptr;
+  if (glob && n_dir > c->cfg.max_batch) return cudaErrorInvalidValue;
   cudaFuncSetAttribute(k_xz<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid(c->NY, n_dir);
   k_xz<T, MODE><<<grid, kThreadsXZ, smem, st>>>(a);
@@ -1373,6 +1456,30 @@ cudaError_t launch_multi_inner(const sp_ctx* c, const double* V, int k, const do
 cudaError_t launch_inner_partials(const sp_ctx* c, const double* a, const double* b, double* partials,
                                   int nblocks, cudaStream_t st) {
   return launch_multi_inner(c, a, 1, b, partials, nblocks, st);
+}
+
+// device-resident Arnoldi helpers (no host round trip)
+cudaError_t launch_dev_dots(const sp_ctx* c, const double* V, int k, const double* w, double* partials,
+                            int nblocks, double* out, const double* add, cudaStream_t st) {
+  dim3 grid(nblocks, (k + 7) / 8);
+  k_multi_inner8<<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(V), k, c->cplx_per_state,
+                                       reinterpret_cast<const double2*>(w), c->NY, c->MZ, partials);
+  k_reduce_rows<<<k, 256, 0, st>>>(partials, nblocks, out, add);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dev_norm(const sp_ctx* c, const double* w, double* partials, int nblocks, double* h,
+                            double* inv, cudaStream_t st) {
+  dim3 grid(nblocks, 1);
+  k_multi_inner8<<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(w), 1, c->cplx_per_state,
+                                       reinterpret_cast<const double2*>(w), c->NY, c->MZ, partials);
+  k_norm_finish<<<1, 256, 0, st>>>(partials, nblocks, h, inv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_dev(const sp_ctx* c, double* x, const double* s, cudaStream_t st) {
+  k_scale_dev<<<grid_for(c->state_len, 256, c->sm_count), 256, 0, st>>>(x, c->state_len, s);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_multi_axpy(const sp_ctx* c, const double* V, int k, const double* h, double* w,

@@ -89,6 +89,8 @@ struct sp_ctx {
   size_t smem_xz64 = 0, smem_xz32 = 0;
   int xz_rp64 = 1, xz_rp32 = 1;
   int xz_cx64 = 1, xz_cx32 = 1;
+  int xz_gglob64 = 0, xz_gglob32 = 0;  // plane buffer in global memory (grid too large for chip)
+  void* wsG = nullptr;           // [batch][NY][nx * RS] complex, only when a plane does not fit
   std::string err;
   // tracing: event pairs per stage, recorded while `trace` is on
   bool trace = false;
@@ -115,6 +117,7 @@ sp_status sp_build_plan(sp_ctx* c);
 
 // shared-memory sizing of k_xz; false if even the FP32 variant cannot fit
 bool sp_xz_fits(sp_ctx* c);
+size_t sp_xz_global_plane_bytes(const sp_ctx* c);  // per direction, 0 if every plane fits on chip
 
 // kernel launchers (kernels.cu); all asynchronous on `st`
 enum XzMode { XZ_STEP = 0, XZ_TANGENT = 1, XZ_BASE = 2, XZ_ADJOINT = 3 };
@@ -146,6 +149,12 @@ cudaError_t launch_inner_partials(const sp_ctx* c, const double* a, const double
 // many inner products <V_i, w> for i < k in one pass: partials [k][nblocks]
 cudaError_t launch_multi_inner(const sp_ctx* c, const double* V, int k, const double* w,
                                double* partials, int nblocks, cudaStream_t st);
+// device-resident Arnoldi: out[i] = <V_i, w> (+ add[i]); h = |w|, inv = 1/|w|; x *= *s
+cudaError_t launch_dev_dots(const sp_ctx* c, const double* V, int k, const double* w, double* partials,
+                            int nblocks, double* out, const double* add, cudaStream_t st);
+cudaError_t launch_dev_norm(const sp_ctx* c, const double* w, double* partials, int nblocks, double* h,
+                            double* inv, cudaStream_t st);
+cudaError_t launch_scale_dev(const sp_ctx* c, double* x, const double* s, cudaStream_t st);
 // w -= sum_i h_i V_i (h on device)
 cudaError_t launch_multi_axpy(const sp_ctx* c, const double* V, int k, const double* h,
                               double* w, cudaStream_t st);

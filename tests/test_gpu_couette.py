@@ -12,7 +12,8 @@ from gpu_util import dev, host, make, rel, seeded
 
 pytestmark = pytest.mark.gpu
 
-GRIDS = [(4, 9, 4), (8, 17, 8), (16, 33, 16), (18, 17, 24), (24, 33, 12), (48, 65, 48)]
+# (96, 33, 96) keeps its FP64 plane buffers in global memory (too large for shared memory)
+GRIDS = [(4, 9, 4), (8, 17, 8), (16, 33, 16), (18, 17, 24), (24, 33, 12), (48, 65, 48), (96, 33, 96)]
 
 
 @pytest.mark.parametrize("grid", [(8, 17, 8), (16, 33, 16)])
@@ -80,7 +81,7 @@ def test_jvp_parity_fp64(grid):
 
 # square grids up to 64 take the register-FFT plane kernel, others the Stockham one
 @pytest.mark.parametrize("grid", [(16, 33, 16), (24, 33, 24), (32, 33, 32), (48, 65, 48), (64, 65, 64),
-                                  (18, 17, 24)])
+                                  (18, 17, 24), (96, 33, 96)])
 def test_jvp_parity_mixed(grid):
     ctx, orc = make(*grid, prec=1, max_batch=2)
     u = seeded(orc, 1000, 0.1)
@@ -157,3 +158,24 @@ def test_newton_converges_to_laminar():
     assert rep["converged"], rep
     assert rep["norm_F"] < 1e-10
     assert float(np.sqrt(orc.inner(host(U), host(U)))) < 1e-9
+
+
+def test_newton_with_gradient_direction_converges():
+    """Hookstep over the Krylov space augmented with J^* F (the dogleg direction)."""
+    ctx, orc = make(8, 17, 8, re=100.0)
+    u = seeded(orc, 1000, 0.05)
+    U = dev(u)
+    rep = ctx.sp_newton_gmres(U, max_newton=12, max_krylov=60, tol=1e-10, use_gradient=True)
+    assert rep["converged"], rep
+    assert float(np.sqrt(orc.inner(host(U), host(U)))) < 1e-9
+
+
+def test_newton_mixed_precision_reaches_fp64_tolerance():
+    """Inexact (float-transform) tangents inside GMRES, FP64 residual: |G| < 1e-10."""
+    ctx, orc = make(16, 33, 16, prec=1)
+    u = seeded(orc, 1000, 0.1)
+    U = dev(u)
+    rep = ctx.sp_newton_gmres(U, max_newton=20, max_krylov=300, tol=1e-10)
+    assert rep["converged"], rep
+    G = orc.step(host(U))
+    assert np.sqrt(orc.inner(G, G)) < 1e-10
