@@ -96,3 +96,31 @@ def couette_random_full(seed: int, nx: int, ny: int, nz: int):
     rng = np.random.default_rng(seed)
     r = rng.standard_normal((2, 3, mx, mz, nyy))
     return r[0] + 1j * r[1]
+
+
+def pipe_random_coeffs(seed, kz, mt, kmax=2, mmax=3, npoly=4):
+    """Random shapes for the seeded pipe state: (streak, pol).
+
+    streak[m'] for m' = 1..3: real standard normal amplitudes of the k = 0
+    axial streaks; pol[p, m', n]: complex standard-normal coefficients, damped by
+    2**-n, of the poloidal potentials of the modes 1 <= |kz| <= kmax,
+    m' <= mmax (zero elsewhere), Hermitian-consistent in the m' = 0 plane.
+    Layout: p in FFT order over 2 kz + 1 axial wavenumbers, m' in 0..mt.
+    """
+    rng = np.random.default_rng(seed)
+    mk = 2 * kz + 1
+    streak = np.zeros(mt + 1)
+    streak[1:min(4, mt + 1)] = rng.standard_normal(min(3, mt))
+    pol = np.zeros((mk, mt + 1, npoly), np.complex128)
+    decay = 2.0 ** -np.arange(npoly)
+    for q in range(0, min(mmax, mt) + 1):
+        for kk in range(-min(kmax, kz), min(kmax, kz) + 1):
+            if kk == 0 or (q == 0 and kk < 0):
+                continue
+            p = kk if kk >= 0 else kk + mk
+            rr = rng.standard_normal((2, npoly))
+            pol[p, q] = (rr[0] + 1j * rr[1]) * decay
+            if q == 0:
+                pm = (-kk) if -kk >= 0 else -kk + mk
+                pol[pm, 0] = np.conj(pol[p, 0])
+    return streak, pol
