@@ -90,6 +90,45 @@ size_t sp_state_len(const sp_ctx* ctx);
 /* Retained ranges: kx_max = Kx, kz_max = Kz, ny = N + 1. */
 sp_status sp_dims(const sp_ctx* ctx, int* kx_max, int* kz_max, int* ny);
 
+/* ---- pipe flow in a moving frame (Sec. 2 traveling waves, Sec. 3.1) --------
+ *
+ * Pipe of radius 1, deviation u = U - (1 - r^2) e_z from Hagen-Poiseuille flow
+ * (centreline-velocity scale: Re = U_c R / nu, the paper's bulk x diameter number,
+ * Sec. 3.1), frame moving with speed c along the axis: N_c(u) = U_tot x Omega_tot
+ * + c du/dz (Sec. 2: C dU/dx added to N for traveling waves).
+ * Fourier in theta (m = sym m', m' = 0..mt) and z (k = alpha kz, |kz| <= kz);
+ * radial points r_j = cos(pi j / (2 nr - 1)), j = 0..nr-1 (the wall j = 0, the
+ * axis excluded), 9-point finite differences with parity ghost points
+ * (Sec. 3.2: Openpipeflow discretises r by finite differences). Per mode the
+ * Stokes problem: momentum at interior points, no-slip, pressure Poisson at
+ * interior points, continuity at the wall.
+ * State layout: complex double [3][2kz+1][mt+1][nr] (u_r, u_theta, u_z; kz in
+ * FFT order; m' = 0..mt; radial index), then ONE more complex value (c, 0)
+ * holding the speed. sp_state_len() counts it. The inner product adds c_a c_b.
+ * sp_step returns (B(u;c) - u, 0); sp_jvp and sp_jvp_fd return
+ * (G_u du + G_c dc, <d/dz U, du>): the tangent plus the phase condition that
+ * fixes the axial position of the wave. sp_vjp and sp_jvp_static are not
+ * available for the pipe (SP_EINVAL). */
+typedef struct {
+  int nr;           /* radial points                                         */
+  int mt, kz;       /* stored modes: 0 <= m' <= mt, |kz| <= kz               */
+  int ntheta, nz;   /* physical grid over theta in [0, 2 pi/sym) and z      */
+  int sym;          /* rotational symmetry (m = sym m')                      */
+  double alpha;     /* axial wavenumber, box length 2 pi / alpha             */
+  double re, dt;
+  int prec, max_batch;
+} sp_pipe_config;
+
+sp_status sp_pipe_create(const sp_pipe_config* cfg, sp_ctx** out);
+
+/* Seeded pipe state: u_z streaks a_m (1 - r^2) r^m (k = 0, m' = 1..3) scaled to
+ * norm amp, plus a divergence-free k != 0 part from poloidal potentials
+ * phi = (1 - r^2)^3 r^m sum_n pol_n r^(2n) (u = curl curl (phi e_z)) scaled to
+ * norm frac * amp, and the speed c0. streak: host double [mt+1]; pol: host
+ * complex double [2kz+1][mt+1][npoly], npoly <= 32. Synchronous. */
+sp_status sp_pipe_seed_state(sp_ctx* ctx, const double* streak, const double* pol, int npoly,
+                             double amp, double frac, double c0, double* U, void* stream);
+
 /* ---- seeded initial states ---------------------------------------------- */
 
 /* Build a divergence-free, no-slip perturbation from random shape series.

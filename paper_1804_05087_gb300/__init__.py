@@ -38,6 +38,12 @@ class _Config(ctypes.Structure):
                 ("dt", ctypes.c_double), ("prec", ctypes.c_int), ("max_batch", ctypes.c_int)]
 
 
+class _PipeConfig(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int), ("mt", ctypes.c_int), ("kz", ctypes.c_int), ("ntheta", ctypes.c_int),
+                ("nz", ctypes.c_int), ("sym", ctypes.c_int), ("alpha", ctypes.c_double), ("re", ctypes.c_double),
+                ("dt", ctypes.c_double), ("prec", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
 class _NewtonOpts(ctypes.Structure):
     _fields_ = [("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int), ("tol", ctypes.c_double),
                 ("eta", ctypes.c_double), ("delta0", ctypes.c_double), ("use_fd", ctypes.c_int),
@@ -57,6 +63,8 @@ def _load():
     P, D, I, V = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p
     sig = {
         "sp_create": ([ctypes.POINTER(_Config), ctypes.POINTER(ctypes.c_void_p)], I),
+        "sp_pipe_create": ([ctypes.POINTER(_PipeConfig), ctypes.POINTER(ctypes.c_void_p)], I),
+        "sp_pipe_seed_state": ([P, P, P, I, D, D, D, P, V], I),
         "sp_destroy": ([P], I),
         "sp_last_error": ([P], ctypes.c_char_p),
         "sp_state_len": ([P], ctypes.c_size_t),
@@ -86,7 +94,8 @@ _lib = _load()
 #: names every build must export (the declarations of include/stokesprec.h)
 EXPORTS = ("sp_create", "sp_destroy", "sp_last_error", "sp_state_len", "sp_dims", "sp_seed_state",
            "sp_step", "sp_set_base", "sp_jvp", "sp_vjp", "sp_jvp_fd", "sp_inner", "sp_newton_gmres",
-           "sp_trace_enable", "sp_trace_read", "sp_jvp_static", "sp_vjp_euclid")
+           "sp_trace_enable", "sp_trace_read", "sp_jvp_static", "sp_vjp_euclid", "sp_pipe_create",
+           "sp_pipe_seed_state")
 STAGES = ("k_yinv", "k_xz", "k_solve", "step", "vector")
 
 
@@ -103,6 +112,22 @@ class Config:
     max_batch: int = 1
 
 
+@dataclass
+class PipeConfig:
+    """Pipe flow in a frame moving with the wave speed (sp_pipe_config)."""
+    nr: int = 64
+    mt: int = 12
+    kz: int = 24
+    ntheta: int = 48
+    nz: int = 96
+    sym: int = 2
+    alpha: float = 1.25
+    re: float = 2500.0
+    dt: float = 50.0
+    prec: int = SP_FP64
+    max_batch: int = 1
+
+
 def _stream(stream):
     if stream is None:
         return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -114,11 +139,17 @@ def _stream(stream):
 class Context:
     """One configuration: plans, operators and workspaces on the current GPU."""
 
-    def __init__(self, cfg: Config):
+    def __init__(self, cfg):
         self.cfg = cfg
-        c = _Config(cfg.nx, cfg.ny, cfg.nz, cfg.lx, cfg.lz, cfg.re, cfg.dt, cfg.prec, cfg.max_batch)
         h = ctypes.c_void_p()
-        st = _lib.sp_create(ctypes.byref(c), ctypes.byref(h))
+        self.pipe = isinstance(cfg, PipeConfig)
+        if self.pipe:
+            c = _PipeConfig(cfg.nr, cfg.mt, cfg.kz, cfg.ntheta, cfg.nz, cfg.sym, cfg.alpha, cfg.re, cfg.dt,
+                            cfg.prec, cfg.max_batch)
+            st = _lib.sp_pipe_create(ctypes.byref(c), ctypes.byref(h))
+        else:
+            c = _Config(cfg.nx, cfg.ny, cfg.nz, cfg.lx, cfg.lz, cfg.re, cfg.dt, cfg.prec, cfg.max_batch)
+            st = _lib.sp_create(ctypes.byref(c), ctypes.byref(h))
         if st != 0:
             raise SpError(st, _lib.sp_last_error(None).decode())
         self._h = h
@@ -127,7 +158,9 @@ class Context:
         self.Kx, self.Kz, self.NY = kx.value, kz.value, ny.value
         self.MX, self.MZ = 2 * self.Kx + 1, self.Kz + 1
         self.state_len = int(_lib.sp_state_len(h))
-        self.shape = (3, self.MX, self.MZ, self.NY)
+        self.field_shape = (3, self.MX, self.MZ, self.NY)
+        # pipe states are flat: the field followed by one complex slot (speed, 0)
+        self.shape = (self.state_len // 2,) if self.pipe else self.field_shape
 
     def close(self):
         if getattr(self, "_h", None):
@@ -161,6 +194,29 @@ class Context:
     def zeros(self, n=None, device="cuda"):
         shape = self.shape if n is None else (n,) + self.shape
         return torch.zeros(shape, dtype=torch.complex128, device=device)
+
+    # ------------------------------------------------------------ pipe states
+    def pipe_join(self, u, c):
+        """Flat pipe state from a field [3, 2kz+1, mt+1, nr] (complex) and a speed."""
+        flat = torch.zeros(self.shape, dtype=torch.complex128, device=u.device)
+        flat[:-1] = u.reshape(-1)
+        flat[-1] = complex(c, 0.0)
+        return flat
+
+    def pipe_split(self, s):
+        """(field view [3, 2kz+1, mt+1, nr], speed) of a flat pipe state."""
+        return s[:-1].reshape(self.field_shape), float(s[-1].real)
+
+    def sp_pipe_seed_state(self, streak, pol, amp, frac, c0, U, stream=None):
+        import numpy as np
+        streak = np.ascontiguousarray(streak, dtype=np.float64)
+        pol = np.ascontiguousarray(pol, dtype=np.complex128)
+        npoly = pol.shape[-1]
+        pu, _ = self._ptr(U, 1)
+        self._check(_lib.sp_pipe_seed_state(self._h, streak.ctypes.data_as(ctypes.c_void_p),
+                                            pol.ctypes.data_as(ctypes.c_void_p), npoly, float(amp), float(frac),
+                                            float(c0), pu, _stream(stream)))
+        return U
 
     # ------------------------------------------------------------ the ABI
     def sp_seed_state(self, ra, rb, rc, amp, U, stream=None):

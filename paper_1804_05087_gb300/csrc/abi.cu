@@ -84,9 +84,9 @@ static bool good_fft_len(int n) {
 }
 
 static void free_ctx(sp_ctx* c) {
-  void* ptrs[] = {c->Th, c->TDh, c->Cfh, c->yv, c->Th_f, c->TDh_f, c->Cfh_f, c->twx, c->twz,
+  void* ptrs[] = {c->Th, c->TDh, c->Cfh, c->yv, c->lam6, c->Th_f, c->TDh_f, c->Cfh_f, c->twx, c->twz, c->base32t,
                   c->twx_f, c->twz_f, c->ops, c->ws6, c->ws3, c->base64, c->base32, c->U0,
-                  c->G0, c->tmp, c->red, c->kry, c->wsG};
+                  c->G0, c->tmp, c->red, c->kry, c->wsG, c->pops, c->fd_w1, c->fd_c1, c->dzU};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -94,6 +94,8 @@ static void free_ctx(sp_ctx* c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
 }
+
+static bool alloc_workspaces(sp_ctx* c);
 
 extern "C" sp_status sp_create(const sp_config* cfg, sp_ctx** out) {
   if (!out) return SP_EINVAL;
@@ -134,13 +136,21 @@ extern "C" sp_status sp_create(const sp_config* cfg, sp_ctx** out) {
   if (c->sm_count <= 0) c->sm_count = 1;
   if (sp_build_plan(c) != SP_OK) return bail(SP_EINVAL, c->err);
   if (!sp_xz_fits(c)) return bail(SP_EINVAL, "grid too large for the plane kernel");
-  const size_t B = (size_t)cfg->max_batch;
+  c->field_cplx = c->cplx_per_state;
+  if (!alloc_workspaces(c)) return bail(SP_ENOMEM, "workspace allocation");
+  *out = c;
+  return SP_OK;
+}
+
+static bool alloc_workspaces(sp_ctx* c) {
+  const size_t B = (size_t)c->cfg.max_batch;
   const size_t plane6 = (size_t)6 * c->NY * c->Mm * 16, plane3 = (size_t)3 * c->NY * c->Mm * 16;
   const size_t grid = (size_t)c->NY * c->nx * c->nz;
   c->red_blocks = 2 * c->sm_count;
   bool ok = cudaMalloc(&c->ws6, B * plane6) == cudaSuccess && cudaMalloc(&c->ws3, B * plane3) == cudaSuccess &&
             cudaMalloc((void**)&c->base64, 6 * grid * 8) == cudaSuccess &&
             cudaMalloc((void**)&c->base32, 6 * grid * 4) == cudaSuccess &&
+            cudaMalloc((void**)&c->base32t, 6 * grid * 4) == cudaSuccess &&
             cudaMalloc((void**)&c->U0, c->state_len * 8) == cudaSuccess &&
             cudaMalloc((void**)&c->G0, c->state_len * 8) == cudaSuccess &&
             cudaMalloc((void**)&c->tmp, B * c->state_len * 8) == cudaSuccess &&
@@ -148,10 +158,63 @@ extern "C" sp_status sp_create(const sp_config* cfg, sp_ctx** out) {
             cudaMallocHost((void**)&c->red_host, (size_t)64 * c->red_blocks * 8 + 4096) == cudaSuccess;
   const size_t gplane = sp_xz_global_plane_bytes(c);
   if (ok && gplane) ok = cudaMalloc(&c->wsG, B * gplane) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    return bail(SP_ENOMEM, "workspace allocation");
-  }
+  if (ok && c->geom == 1) ok = cudaMalloc((void**)&c->dzU, c->state_len * 8) == cudaSuccess;
+  if (!ok) cudaGetLastError();
+  return ok;
+}
+
+extern "C" sp_status sp_pipe_create(const sp_pipe_config* cfg, sp_ctx** out) {
+  if (!out) return SP_EINVAL;
+  *out = nullptr;
+  if (!cfg) return SP_EINVAL;
+  sp_ctx* c = new (std::nothrow) sp_ctx();
+  if (!c) return SP_ENOMEM;
+  auto bail = [&](sp_status s, const std::string& m) {
+    g_create_error = "sp_pipe_create: " + m;
+    free_ctx(c);
+    delete c;
+    return s;
+  };
+  c->geom = 1;
+  c->pcfg = *cfg;
+  if (cfg->nr < 12 || cfg->nr > 512) return bail(SP_EINVAL, "nr");
+  if (cfg->mt < 1 || cfg->kz < 1 || cfg->sym < 1) return bail(SP_EINVAL, "mt, kz, sym");
+  if (!good_fft_len(cfg->nz) || !good_fft_len(cfg->ntheta)) return bail(SP_EINVAL, "nz, ntheta");
+  if (cfg->ntheta < 3 * cfg->mt + 1 || cfg->nz < 3 * cfg->kz + 1) return bail(SP_EINVAL, "grid below the 2/3 rule");
+  if (!(cfg->alpha > 0) || !(cfg->re > 0) || !(cfg->dt > 0)) return bail(SP_EINVAL, "params");
+  if (cfg->prec != SP_FP64 && cfg->prec != SP_MIXED) return bail(SP_EINVAL, "prec");
+  if (cfg->max_batch < 1) return bail(SP_EINVAL, "max_batch");
+  // the periodic directions map onto the Couette slots: "x" = z (full), "z" = theta (half)
+  c->cfg.nx = cfg->nz;
+  c->cfg.nz = cfg->ntheta;
+  c->cfg.ny = cfg->nr;
+  c->cfg.re = cfg->re;
+  c->cfg.dt = cfg->dt;
+  c->cfg.prec = cfg->prec;
+  c->cfg.max_batch = cfg->max_batch;
+  c->cfg.lx = 2.0 * M_PI / cfg->alpha;
+  c->cfg.lz = 2.0 * M_PI / cfg->sym;
+  c->nx = cfg->nz; c->nz = cfg->ntheta; c->ny = cfg->nr;
+  c->NY = cfg->nr;
+  c->Kx = cfg->kz;
+  c->Kz = cfg->mt;
+  c->MX = 2 * c->Kx + 1;
+  c->MZ = c->Kz + 1;
+  c->Mm = c->MX * c->MZ;
+  c->n_unique = (c->Kx + 1) * c->MZ + c->Kx * (c->MZ - 1);
+  c->alpha = cfg->alpha;
+  c->beta = cfg->sym;
+  c->nu = 1.0 / cfg->re;
+  c->dt = cfg->dt;
+  c->field_cplx = (size_t)3 * c->Mm * c->NY;
+  c->cplx_per_state = c->field_cplx + 1;
+  c->state_len = 2 * c->cplx_per_state;
+  if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(SP_ECUDA, "no device");
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
+  if (c->sm_count <= 0) c->sm_count = 1;
+  if (sp_build_pipe_plan(c) != SP_OK) return bail(SP_EINVAL, c->err);
+  if (!sp_xz_fits(c)) return bail(SP_EINVAL, "grid too large for the plane kernel");
+  if (!alloc_workspaces(c)) return bail(SP_ENOMEM, "workspace allocation");
   *out = c;
   return SP_OK;
 }
@@ -185,6 +248,20 @@ static sp_status step_batch(sp_ctx* c, const double* U, double* G, int n, cudaSt
     const double* u = U + (size_t)d0 * c->state_len;
     double* g = G + (size_t)d0 * c->state_len;
     sp_status s;
+    if (c->geom == 1) {
+      if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_pvals(c, false, u, c->ws6, nb, st); }),
+                       "pvals")) != SP_OK)
+        return s;
+      if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st,
+                                 [&] { return launch_xz(c, false, XZ_STEP, c->ws6, c->ws3, nb, st); }),
+                       "xz step")) != SP_OK)
+        return s;
+      if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st,
+                                 [&] { return launch_psolve(c, false, false, c->ws3, u, g, nb, st); }),
+                       "psolve")) != SP_OK)
+        return s;
+      continue;
+    }
     if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_yinv(c, false, u, c->ws6, nb, st); }), "yinv")) != SP_OK) return s;
     if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_xz(c, false, XZ_STEP, c->ws6, c->ws3, nb, st); }), "xz step")) != SP_OK) return s;
     if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_solve(c, false, c->ws3, u, g, nb, st); }), "solve")) != SP_OK) return s;
@@ -225,11 +302,30 @@ extern "C" sp_status sp_set_base(sp_ctx* c, const double* U, void* stream) {
   sp_status s;
   if ((s = sp_cuda(c, cudaMemcpyAsync(c->U0, U, c->state_len * 8, cudaMemcpyDeviceToDevice, st), "copy")) != SP_OK)
     return s;
-  if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_yinv(c, false, c->U0, c->ws6, 1, st); }), "yinv")) != SP_OK) return s;
+  if (c->geom == 1) {
+    if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_pvals(c, false, c->U0, c->ws6, 1, st); }),
+                     "pvals")) != SP_OK)
+      return s;
+    if ((s = sp_cuda(c, launch_pipe_dz(c, c->U0, c->dzU, st), "dz")) != SP_OK) return s;
+  } else if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_yinv(c, false, c->U0, c->ws6, 1, st); }), "yinv")) != SP_OK) return s;
   if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_xz(c, false, XZ_BASE, c->ws6, nullptr, 1, st); }), "xz base")) != SP_OK) return s;
   if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_base_to_f32(c, st); }), "base f32")) != SP_OK) return s;
   if ((s = step_batch(c, c->U0, c->G0, 1, st)) != SP_OK) return s;
   c->has_base = 1;
+  return SP_OK;
+}
+
+// pipe: the speed slot of a tangent holds the phase condition <d/dz U, du>
+static sp_status pipe_phase(sp_ctx* c, const double* du, double* out, int n_dir, cudaStream_t st) {
+  const int nb = (int)std::max<size_t>(1, std::min<size_t>(c->red_blocks, (c->cplx_per_state + 1023) / 1024));
+  for (int d = 0; d < n_dir; ++d) {
+    double* slot = out + (size_t)d * c->state_len + 2 * c->field_cplx;
+    sp_status s = sp_cuda(c, cudaMemsetAsync(slot, 0, 16, st), "phase clear");
+    if (s != SP_OK) return s;
+    if ((s = sp_cuda(c, launch_dev_dots(c, c->dzU, 1, du + (size_t)d * c->state_len, c->red, nb, slot, nullptr, st),
+                     "phase")) != SP_OK)
+      return s;
+  }
   return SP_OK;
 }
 
@@ -243,6 +339,21 @@ extern "C" sp_status sp_jvp(sp_ctx* c, const double* du, double* Jdu, int n_dir,
     const double* u = du + (size_t)d0 * c->state_len;
     double* g = Jdu + (size_t)d0 * c->state_len;
     sp_status s;
+    if (c->geom == 1) {
+      if ((s = sp_cuda(c, traced(c, SP_STAGE_YINV, st, [&] { return launch_pvals(c, f32, u, c->ws6, nb, st); }),
+                       "pvals")) != SP_OK)
+        return s;
+      if ((s = sp_cuda(c, traced(c, SP_STAGE_XZ, st,
+                                 [&] { return launch_xz(c, f32, XZ_TANGENT, c->ws6, c->ws3, nb, st); }),
+                       "xz tangent")) != SP_OK)
+        return s;
+      if ((s = sp_cuda(c, traced(c, SP_STAGE_SOLVE, st,
+                                 [&] { return launch_psolve(c, f32, true, c->ws3, u, g, nb, st); }),
+                       "psolve")) != SP_OK)
+        return s;
+      if ((s = pipe_phase(c, u, g, nb, st)) != SP_OK) return s;
+      continue;
+    }
     if ((s = sp_cuda(c, traced(c, SP_STAGE_YINV, st, [&] { return launch_yinv(c, f32, u, c->ws6, nb, st); }), "yinv")) != SP_OK) return s;
     if ((s = sp_cuda(c, traced(c, SP_STAGE_XZ, st, [&] { return launch_xz(c, f32, XZ_TANGENT, c->ws6, c->ws3, nb, st); }), "xz tangent")) != SP_OK) return s;
     if ((s = sp_cuda(c, traced(c, SP_STAGE_SOLVE, st, [&] { return launch_solve(c, f32, c->ws3, u, g, nb, st); }), "solve")) != SP_OK) return s;
@@ -253,6 +364,7 @@ extern "C" sp_status sp_jvp(sp_ctx* c, const double* du, double* Jdu, int n_dir,
 static sp_status vjp_impl(sp_ctx* c, const double* r, double* JTr, int n_dir, bool weighted, cudaStream_t st,
                           const char* who) {
   if (!c || !r || !JTr || n_dir < 0 || r == JTr) return sp_fail(c, SP_EINVAL, std::string(who) + ": bad arguments");
+  if (c->geom != 0) return sp_fail(c, SP_EINVAL, std::string(who) + ": the adjoint is built for plane Couette only");
   if (!c->has_base) return sp_fail(c, SP_EINVAL, std::string(who) + ": call sp_set_base first");
   const bool f32 = c->cfg.prec == SP_MIXED;
   for (int d0 = 0; d0 < n_dir; d0 += c->cfg.max_batch) {
@@ -318,6 +430,7 @@ extern "C" sp_status sp_jvp_fd(sp_ctx* c, const double* du, double* Jdu, int n_d
     if ((s = step_batch(c, c->tmp, g, 1, st)) != SP_OK) return s;
     if ((s = sp_cuda(c, launch_axpby(g, 1.0 / eps, g, -1.0 / eps, c->G0, c->state_len, st), "axpby")) != SP_OK)
       return s;
+    if (c->geom == 1 && (s = pipe_phase(c, u, g, 1, st)) != SP_OK) return s;
   }
   return sp_cuda(c, cudaStreamSynchronize(st), "fd sync");
 }
@@ -325,6 +438,7 @@ extern "C" sp_status sp_jvp_fd(sp_ctx* c, const double* du, double* Jdu, int n_d
 extern "C" sp_status sp_seed_state(sp_ctx* c, const double* ra, const double* rb, const double* rc, double amp,
                                    double* U, void* stream) {
   if (!c || !ra || !rb || !rc || !U) return sp_fail(c, SP_EINVAL, "sp_seed_state: bad pointers");
+  if (c->geom != 0) return sp_fail(c, SP_EINVAL, "sp_seed_state: plane Couette only (pipe: sp_pipe_seed_state)");
   cudaStream_t st = (cudaStream_t)stream;
   sp_status s = sp_cuda(c, launch_seed(c, ra, rb, rc, U, st), "seed");
   if (s != SP_OK) return s;
@@ -333,6 +447,32 @@ extern "C" sp_status sp_seed_state(sp_ctx* c, const double* ra, const double* rb
   if (n2 > 0) {
     if ((s = sp_cuda(c, launch_scale(U, amp / std::sqrt(n2), c->state_len, st), "scale")) != SP_OK) return s;
   }
+  return sp_cuda(c, cudaStreamSynchronize(st), "seed sync");
+}
+
+extern "C" sp_status sp_pipe_seed_state(sp_ctx* c, const double* streak, const double* pol, int npoly, double amp,
+                                        double frac, double c0, double* U, void* stream) {
+  if (!c || !streak || !pol || !U || npoly < 1 || npoly > 32) return sp_fail(c, SP_EINVAL, "sp_pipe_seed_state: bad arguments");
+  if (c->geom != 1) return sp_fail(c, SP_EINVAL, "sp_pipe_seed_state: not a pipe context");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t npol = (size_t)c->Mm * npoly * 2, nst = (size_t)c->MZ;
+  // device copies of the random shapes live in the tail of the ws3 workspace
+  double* dstreak = reinterpret_cast<double*>(c->ws3);
+  double* dpol = dstreak + ((nst + 1) / 2) * 2 + 2;  // even offset: pol is read as double2 (16-byte aligned)
+  double* B = c->tmp;
+  sp_status s;
+  if ((s = sp_cuda(c, cudaMemcpyAsync(dstreak, streak, nst * 8, cudaMemcpyHostToDevice, st), "seed copy")) != SP_OK)
+    return s;
+  if ((s = sp_cuda(c, cudaMemcpyAsync(dpol, pol, npol * 8, cudaMemcpyHostToDevice, st), "seed copy")) != SP_OK) return s;
+  if ((s = sp_cuda(c, launch_pipe_seed(c, dstreak, dpol, npoly, U, B, st), "pipe seed")) != SP_OK) return s;
+  double na, nb2;
+  if ((s = inner_many(c, U, 1, U, &na, st)) != SP_OK) return s;
+  if ((s = inner_many(c, B, 1, B, &nb2, st)) != SP_OK) return s;
+  const double sa = na > 0 ? amp / std::sqrt(na) : 0.0, sb = nb2 > 0 ? frac * amp / std::sqrt(nb2) : 0.0;
+  if ((s = sp_cuda(c, launch_axpby(U, sa, U, sb, B, c->state_len, st), "seed combine")) != SP_OK) return s;
+  const double cc[2] = {c0, 0.0};
+  if ((s = sp_cuda(c, cudaMemcpyAsync(U + 2 * c->field_cplx, cc, 16, cudaMemcpyHostToDevice, st), "speed")) != SP_OK)
+    return s;
   return sp_cuda(c, cudaStreamSynchronize(st), "seed sync");
 }
 
@@ -481,6 +621,8 @@ double now_ms() {
 extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts* o, sp_newton_report* rep,
                                      void* stream) {
   if (!c || !U || !o) return sp_fail(c, SP_EINVAL, "sp_newton_gmres: bad arguments");
+  if (o->use_gradient && c->geom != 0)
+    return sp_fail(c, SP_EINVAL, "sp_newton_gmres: use_gradient needs the adjoint (plane Couette only)");
   const int K = o->max_krylov;
   if (K < 1 || K > 4096 || o->max_newton < 0) return sp_fail(c, SP_EINVAL, "sp_newton_gmres: bad options");
   cudaStream_t st = (cudaStream_t)stream;

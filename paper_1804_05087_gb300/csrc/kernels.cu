@@ -215,7 +215,7 @@ struct XzArgs {
   T* base;            // [6][NY][nx][nz] (read for the tangent, written for BASE)
   const C2<T>* twx;   // [nx] exp(-2 pi i k/nx)
   const C2<T>* twz;
-  const double* yv;   // [NY] Gauss-Lobatto points
+  const double* lam;  // [NY][6] laminar U and Omega added on each plane (step and base)
   FftPlan px, pz;
   int nx, nz, NY, Mm, MX, MZ, Kx, Kz;
   int rp, cx;         // row pairs per z chunk, columns per x chunk
@@ -277,7 +277,9 @@ __global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
   }
 
   // ---- phase 2: per pair of x-rows, c2r along z, product, r2c along z
-  const T yj = (T)a.yv[j];
+  T lam[6];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) lam[f] = (T)a.lam[(size_t)j * 6 + f];
   const int rp = a.rp;
   C2<T>* P0 = S;
   C2<T>* P1 = S + (size_t)6 * rp * nz;
@@ -324,13 +326,11 @@ __global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
           for (int f = 0; f < NIN; ++f) F[f] = r ? fv[f].y : fv[f].x;
           const size_t gidx = (size_t)j * nxz + (size_t)(x0 + r) * nz + k;
           if constexpr (MODE == XZ_BASE) {
-            F[0] += yj;
-            F[5] -= (T)1;
 #pragma unroll
-            for (int f = 0; f < 6; ++f) a.base[(size_t)f * a.NY * nxz + gidx] = F[f];
+            for (int f = 0; f < 6; ++f) a.base[(size_t)f * a.NY * nxz + gidx] = F[f] + lam[f];
           } else if constexpr (MODE == XZ_STEP) {
-            const T U0 = F[0] + yj, U1 = F[1], U2 = F[2];
-            const T O0 = F[3], O1 = F[4], O2 = F[5] - (T)1;
+            const T U0 = F[0] + lam[0], U1 = F[1] + lam[1], U2 = F[2] + lam[2];
+            const T O0 = F[3] + lam[3], O1 = F[4] + lam[4], O2 = F[5] + lam[5];
             res[r][0] = U1 * O2 - U2 * O1;
             res[r][1] = U2 * O0 - U0 * O2;
             res[r][2] = U0 * O1 - U1 * O0;
@@ -1162,9 +1162,17 @@ __global__ void k_multi_axpy(const double* V, int k, size_t n, const double* h, 
   }
 }
 
-__global__ void k_f64_to_f32(const double* a, float* b, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+// float copies of the base fields: b in the layout [6][NY][NX][NZ] of a, bt transposed to
+// [6][NY][NZ][NX] for the register-FFT plane kernel
+__global__ void k_f64_to_f32(const double* a, float* b, float* bt, size_t n, int nx, int nz) {
+  const size_t plane = (size_t)nx * nz;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = (float)a[i];
+    b[i] = v;
+    const size_t p = i / plane, r = i - p * plane;
+    const size_t x = r / nz, z = r - x * nz;
+    bt[p * plane + z * nx + x] = v;
+  }
 }
 
 int grid_for(size_t n, int threads, int sms) {
@@ -1258,7 +1266,7 @@ static cudaError_t launch_xz_t(const sp_ctx* c, const void* in6, void* out3, T* 
   a.base = base;
   a.twx = twx;
   a.twz = twz;
-  a.yv = c->yv;
+  a.lam = c->lam6;
   a.px = c->px;
   a.pz = c->pz;
   a.nx = c->nx; a.nz = c->nz; a.NY = c->NY; a.Mm = c->Mm; a.MX = c->MX; a.MZ = c->MZ;
@@ -1418,7 +1426,7 @@ cudaError_t launch_finish_adj(const sp_ctx* c, const double* r, double* out, int
 
 cudaError_t launch_base_to_f32(const sp_ctx* c, cudaStream_t st) {
   size_t n = (size_t)6 * c->NY * c->nx * c->nz;
-  k_f64_to_f32<<<grid_for(n, 256, c->sm_count), 256, 0, st>>>(c->base64, c->base32, n);
+  k_f64_to_f32<<<grid_for(n, 256, c->sm_count), 256, 0, st>>>(c->base64, c->base32, c->base32t, n, c->nx, c->nz);
   return cudaGetLastError();
 }
 

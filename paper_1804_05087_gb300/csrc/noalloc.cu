@@ -47,6 +47,7 @@ cudaError_t scratch_address(int dev, void** out) {
 extern "C" sp_status sp_jvp_static(sp_ctx* c, const double* du, double* Jdu, void* stream) {
   if (!c || !du || !Jdu || du == Jdu) return sp_fail(c, SP_EINVAL, "sp_jvp_static: bad arguments");
   if (!c->has_base) return sp_fail(c, SP_EINVAL, "sp_jvp_static: call sp_set_base first");
+  if (c->geom != 0) return sp_fail(c, SP_EINVAL, "sp_jvp_static: plane Couette contexts only");
   const bool f32 = c->cfg.prec == SP_MIXED;
   const size_t esz = f32 ? 8 : 16;  // one complex value of the transforms
   const size_t b6 = ((size_t)6 * c->NY * c->Mm * esz + 255) / 256 * 256;

@@ -204,7 +204,7 @@ bool build_hop(const ChebOps& C, int Q, double lam, double nu, double* out) {
 }  // namespace
 
 // unique mode u -> (pos, iz): positions 0..Kx keep every iz, negative ix skip iz = 0
-static inline void unique_mode(const sp_ctx* c, int u, int* pos, int* iz) {
+void sp_unique_mode(const sp_ctx* c, int u, int* pos, int* iz) {
   int first = (c->Kx + 1) * c->MZ;
   if (u < first) {
     *pos = u / c->MZ;
@@ -238,20 +238,12 @@ sp_status sp_build_plan(sp_ctx* c) {
     }
   }
   // twiddles exp(-2 pi i k / n)
-  // twiddles exp(-2 pi i k / n); sin(pi m / N) = cos(pi (N - 2m) / (2N))
-  auto tw = [](int n) {
-    std::vector<double2> t(n);
-    for (int k = 0; k < n; ++k) {
-      t[k].x = cospi_frac(2L * k, n);
-      t[k].y = -cospi_frac((long)n - 4L * k, 2L * n);
-    }
-    return t;
-  };
-  std::vector<double2> twx = tw(c->nx), twz = tw(c->nz);
-  std::vector<double> yv(n1);
-  for (int j = 0; j < n1; ++j) yv[j] = cospi_frac(j, N);
-  if (!make_fft_plan(c->nx, &c->px) || !make_fft_plan(c->nz, &c->pz))
-    return sp_fail(c, SP_EINVAL, "Nx and Nz must be products of 2 and 3");
+  std::vector<double> yv(n1), lam6((size_t)n1 * 6, 0.0);
+  for (int j = 0; j < n1; ++j) {
+    yv[j] = cospi_frac(j, N);
+    lam6[(size_t)j * 6 + 0] = yv[j];   // U_lam = y e_x
+    lam6[(size_t)j * 6 + 5] = -1.0;    // curl U_lam = -e_z
+  }
 
   // per-mode operators
   c->nv0 = N / 2 + 1;
@@ -273,7 +265,7 @@ sp_status sp_build_plan(sp_ctx* c) {
   auto work = [&](int tid) {
     for (int u = tid; u < c->n_unique; u += nthreads) {
       int pos, iz;
-      unique_mode(c, u, &pos, &iz);
+      sp_unique_mode(c, u, &pos, &iz);
       int ix = pos <= c->Kx ? pos : pos - c->MX;
       double kx = c->alpha * ix, kz = c->beta * iz;
       double k2 = kx * kx + kz * kz, k = std::sqrt(k2);
@@ -298,9 +290,6 @@ sp_status sp_build_plan(sp_ctx* c) {
   // float copies
   std::vector<float> Thf(Th.begin(), Th.end()), TDhf(TDh.begin(), TDh.end()),
       Cfhf(Cfh.begin(), Cfh.end());
-  std::vector<float2> twxf(c->nx), twzf(c->nz);
-  for (int k = 0; k < c->nx; ++k) twxf[k] = make_float2((float)twx[k].x, (float)twx[k].y);
-  for (int k = 0; k < c->nz; ++k) twzf[k] = make_float2((float)twz[k].x, (float)twz[k].y);
 
   auto up = [&](void** dst, const void* src, size_t bytes) -> bool {
     if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
@@ -309,9 +298,35 @@ sp_status sp_build_plan(sp_ctx* c) {
   bool ok = up((void**)&c->Th, Th.data(), Th.size() * 8) && up((void**)&c->TDh, TDh.data(), TDh.size() * 8) &&
             up((void**)&c->Cfh, Cfh.data(), Cfh.size() * 8) && up((void**)&c->Th_f, Thf.data(), Thf.size() * 4) &&
             up((void**)&c->TDh_f, TDhf.data(), TDhf.size() * 4) && up((void**)&c->Cfh_f, Cfhf.data(), Cfhf.size() * 4) &&
-            up((void**)&c->twx, twx.data(), twx.size() * 16) && up((void**)&c->twz, twz.data(), twz.size() * 16) &&
-            up((void**)&c->twx_f, twxf.data(), twxf.size() * 8) && up((void**)&c->twz_f, twzf.data(), twzf.size() * 8) &&
-            up((void**)&c->ops, ops.data(), ops.size() * 8) && up((void**)&c->yv, yv.data(), yv.size() * 8);
+            up((void**)&c->ops, ops.data(), ops.size() * 8) && up((void**)&c->yv, yv.data(), yv.size() * 8) &&
+            up((void**)&c->lam6, lam6.data(), lam6.size() * 8);
   if (!ok) return sp_fail(c, SP_ENOMEM, "device allocation of plan tables failed");
+  return sp_build_fft_tables(c);
+}
+
+// FFT plans and twiddle tables exp(-2 pi i k / n) of the two periodic directions
+sp_status sp_build_fft_tables(sp_ctx* c) {
+  if (!make_fft_plan(c->nx, &c->px) || !make_fft_plan(c->nz, &c->pz))
+    return sp_fail(c, SP_EINVAL, "the periodic grid sizes must be products of 2 and 3");
+  // twiddles exp(-2 pi i k / n); sin(pi m / N) = cos(pi (N - 2m) / (2N))
+  auto tw = [](int n) {
+    std::vector<double2> t(n);
+    for (int k = 0; k < n; ++k) {
+      t[k].x = cospi_frac(2L * k, n);
+      t[k].y = -cospi_frac((long)n - 4L * k, 2L * n);
+    }
+    return t;
+  };
+  std::vector<double2> twx = tw(c->nx), twz = tw(c->nz);
+  std::vector<float2> twxf(c->nx), twzf(c->nz);
+  for (int k = 0; k < c->nx; ++k) twxf[k] = make_float2((float)twx[k].x, (float)twx[k].y);
+  for (int k = 0; k < c->nz; ++k) twzf[k] = make_float2((float)twz[k].x, (float)twz[k].y);
+  auto up = [&](void** dst, const void* src, size_t bytes) -> bool {
+    if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
+    return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  const bool ok = up((void**)&c->twx, twx.data(), twx.size() * 16) && up((void**)&c->twz, twz.data(), twz.size() * 16) &&
+                  up((void**)&c->twx_f, twxf.data(), twxf.size() * 8) && up((void**)&c->twz_f, twzf.data(), twzf.size() * 8);
+  if (!ok) return sp_fail(c, SP_ENOMEM, "device allocation of twiddle tables failed");
   return SP_OK;
 }

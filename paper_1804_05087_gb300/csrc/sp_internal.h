@@ -50,6 +50,8 @@ struct FftPlan {
 // ------------------------------------------------------------------ context
 struct sp_ctx {
   sp_config cfg;
+  int geom = 0;                  // 0 plane Couette, 1 pipe (sp_pipe_create)
+  sp_pipe_config pcfg{};
   int dev = 0;
   int sm_count = 0;
   int nx = 0, ny = 0, nz = 0;
@@ -58,7 +60,8 @@ struct sp_ctx {
   int n_unique = 0;              // modes solved: (Kx+1) MZ + Kx (MZ-1)
   double alpha = 0, beta = 0, nu = 0, dt = 0;
   size_t state_len = 0;          // doubles per state
-  size_t cplx_per_state = 0;
+  size_t cplx_per_state = 0;     // complex values per state (pipe: + 1 for the speed)
+  size_t field_cplx = 0;         // complex values of the velocity field, 3 Mm NY
   FftPlan px{}, pz{};
   // per-mode solve operators: V0, V1, H0, H1 (row-major), FP64
   int nv0 = 0, nv1 = 0, cv = 0;  // rows of V0 / V1, columns of both (N-1)
@@ -67,16 +70,24 @@ struct sp_ctx {
 
   // device tables
   double *Th = nullptr, *TDh = nullptr, *Cfh = nullptr;
-  double* yv = nullptr;          // [NY] Gauss-Lobatto points cos(pi j / N)
+  double* yv = nullptr;          // [NY] wall-normal points: cos(pi j / N) (Couette), r_j (pipe)
+  double* lam6 = nullptr;        // [NY][6] laminar (U, Omega) per plane: (y,0,0,0,0,-1) / (0,0,1-r^2,0,2r,0)
   float *Th_f = nullptr, *TDh_f = nullptr, *Cfh_f = nullptr;
   double2 *twx = nullptr, *twz = nullptr;
   float2 *twx_f = nullptr, *twz_f = nullptr;
   double* ops = nullptr;
+  // pipe: per-mode dense operators (3 NY x 3 NY), radial FD band (D1) tables
+  double* pops = nullptr;
+  size_t pop_stride = 0;
+  double* fd_w1 = nullptr;       // [2 parities][NY][9] weights of the first derivative
+  int* fd_c1 = nullptr;          // [2][NY][9] columns
+  double* dzU = nullptr;         // d/dz of the (projected) linearisation point, one state
   // device workspaces
   void* ws6 = nullptr;           // [batch][6][NY][Mm] complex (double-sized)
   void* ws3 = nullptr;           // [batch][3][NY][Mm] complex (double-sized)
   double* base64 = nullptr;      // [6][NY][nx][nz]
   float* base32 = nullptr;
+  float* base32t = nullptr;      // [6][NY][nz][nx]: transposed copy for the register-FFT kernel
   double* U0 = nullptr;          // linearisation point
   double* G0 = nullptr;          // G(U0)
   double* tmp = nullptr;         // [batch] states
@@ -112,8 +123,19 @@ cudaError_t traced(sp_ctx* c, int stage, cudaStream_t st, F&& f) {
 sp_status sp_fail(sp_ctx* c, sp_status s, const std::string& msg);
 sp_status sp_cuda(sp_ctx* c, cudaError_t e, const char* what);
 
-// plan building (plan.cpp)
+// plan building (plan.cpp, plan_pipe.cpp)
 sp_status sp_build_plan(sp_ctx* c);
+sp_status sp_build_pipe_plan(sp_ctx* c);
+sp_status sp_build_fft_tables(sp_ctx* c);
+void sp_unique_mode(const sp_ctx* c, int u, int* pos, int* iz);
+
+// pipe kernels (pipe.cu)
+cudaError_t launch_pvals(const sp_ctx* c, bool fp32, const double* in, void* out6, int n_dir, cudaStream_t st);
+cudaError_t launch_psolve(const sp_ctx* c, bool fp32, bool tangent, const void* in3, const double* u,
+                          double* out, int n_dir, cudaStream_t st);
+cudaError_t launch_pipe_dz(const sp_ctx* c, const double* U, double* dzU, cudaStream_t st);
+cudaError_t launch_pipe_seed(const sp_ctx* c, const double* streak, const double* pol, int npoly, double* A,
+                             double* B, cudaStream_t st);
 
 // shared-memory sizing of k_xz; false if even the FP32 variant cannot fit
 bool sp_xz_fits(sp_ctx* c);

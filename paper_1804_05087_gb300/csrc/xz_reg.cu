@@ -154,7 +154,7 @@ __device__ __forceinline__ void fft_reg(C2<float> (&x)[N]) {
 struct XzRegArgs {
   const C2<float>* in;  // [dir][NIN][NY][Mm]
   C2<float>* out;       // [dir][NOUT][NY][Mm]
-  const float* base;    // [6][NY][NX][NZ]
+  const float* base;    // [6][NY][NZ][NX] (transposed float copy of the base fields)
   const double* yv;
   int NY, Mm;
 };
@@ -167,11 +167,12 @@ __global__ void __launch_bounds__(kThreadsReg) k_xz_reg(XzRegArgs a) {
   constexpr int NOUT = MODE == XZ_ADJOINT ? 6 : 3;
   constexpr int KX = (NX - 1) / 3, KZ = (NZ - 1) / 3;
   constexpr int MX = 2 * KX + 1, MZ = KZ + 1;
-  constexpr int FS = MZ + 1, RS = 6 * FS;
+  // row stride = 1 (mod 8): neighbouring row pairs start 4 banks apart
+  constexpr int FS = MZ + 1, RS = ((6 * FS + 7) / 8) * 8 + 1;
   constexpr int NQ = NX / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2<float>* G = reinterpret_cast<C2<float>*>(smem_raw);  // [NX][6][FS]
-  C2<float>* Ph = G + NX * RS;                              // [6][NQ][NZ] packed row pairs
+  C2<float>* G = reinterpret_cast<C2<float>*>(smem_raw);  // [NX][6][FS] (row stride RS)
+  C2<float>* Ph = G + NX * RS;                              // [6][NZ][NQ] packed row pairs, pair fastest
   const int j = blockIdx.x, dir = blockIdx.y;
   const size_t planeMm = (size_t)a.NY * a.Mm;
   const C2<float>* in = a.in + (size_t)dir * NIN * planeMm + (size_t)j * a.Mm;
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(kThreadsReg) k_xz_reg(XzRegArgs a) {
 
   // phase 2a: c2r along z of row pairs (2q, 2q+1) packed as real + i imag
   for (int it = threadIdx.x; it < NIN * NQ; it += blockDim.x) {
-    const int f = it / NQ, q = it - f * NQ;
+    const int f = it / NQ, q = it - f * NQ;  // consecutive threads: consecutive row pairs
     const C2<float>* g0 = G + (2 * q) * RS + f * FS;
     const C2<float>* g1 = g0 + RS;
     C2<float> z[NZ];
@@ -223,28 +224,32 @@ __global__ void __launch_bounds__(kThreadsReg) k_xz_reg(XzRegArgs a) {
       }
     }
     fft_reg<NZ, 1>(z);
-    C2<float>* dst = Ph + (f * NQ + q) * NZ;
+    C2<float>* dst = Ph + f * NZ * NQ + q;
 #pragma unroll
-    for (int k = 0; k < NZ; ++k) dst[k] = z[out_pos<NZ>(k)];
+    for (int k = 0; k < NZ; ++k) dst[k * NQ] = z[out_pos<NZ>(k)];
   }
   __syncthreads();
 
   // phase 2b: pointwise products (in place: each point reads its NIN fields first)
   const size_t nxz = (size_t)NX * NZ;
   for (int it = threadIdx.x; it < NQ * NZ; it += blockDim.x) {
-    const int q = it / NZ, k = it - q * NZ;
+    const int k = it / NQ, q = it - k * NQ;  // pair fastest: conflict-free Ph, coalesced base
     C2<float> fv[NIN];
 #pragma unroll
-    for (int f = 0; f < NIN; ++f) fv[f] = Ph[(f * NQ + q) * NZ + k];
+    for (int f = 0; f < NIN; ++f) fv[f] = Ph[(f * NZ + k) * NQ + q];
+    // base fields in the transposed layout [6][NY][NZ][NX]: rows 2q and 2q+1 are adjacent
+    float2 bp[6];
+    const size_t gidx = (size_t)j * nxz + (size_t)k * NX + 2 * q;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) bp[f] = __ldg(reinterpret_cast<const float2*>(a.base + (size_t)f * a.NY * nxz + gidx));
     float res[2][NOUT];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       float F[NIN], B[6];
 #pragma unroll
       for (int f = 0; f < NIN; ++f) F[f] = r ? fv[f].y : fv[f].x;
-      const size_t gidx = (size_t)j * nxz + (size_t)(2 * q + r) * NZ + k;
 #pragma unroll
-      for (int f = 0; f < 6; ++f) B[f] = __ldg(a.base + (size_t)f * a.NY * nxz + gidx);
+      for (int f = 0; f < 6; ++f) B[f] = r ? bp[f].y : bp[f].x;
       if constexpr (MODE == XZ_TANGENT) {
         res[r][0] = (B[1] * F[5] - B[2] * F[4]) + (F[1] * B[5] - F[2] * B[4]);
         res[r][1] = (B[2] * F[3] - B[0] * F[5]) + (F[2] * B[3] - F[0] * B[5]);
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(kThreadsReg) k_xz_reg(XzRegArgs a) {
       }
     }
 #pragma unroll
-    for (int c = 0; c < NOUT; ++c) Ph[(c * NQ + q) * NZ + k] = mk(res[0][c], res[1][c]);
+    for (int c = 0; c < NOUT; ++c) Ph[(c * NZ + k) * NQ + q] = mk(res[0][c], res[1][c]);
   }
   __syncthreads();
 
@@ -267,9 +272,9 @@ __global__ void __launch_bounds__(kThreadsReg) k_xz_reg(XzRegArgs a) {
   for (int it = threadIdx.x; it < NOUT * NQ; it += blockDim.x) {
     const int c = it / NQ, q = it - c * NQ;
     C2<float> z[NZ];
-    const C2<float>* src = Ph + (c * NQ + q) * NZ;
+    const C2<float>* src = Ph + c * NZ * NQ + q;
 #pragma unroll
-    for (int k = 0; k < NZ; ++k) z[k] = src[k];
+    for (int k = 0; k < NZ; ++k) z[k] = src[k * NQ];
     fft_reg<NZ, -1>(z);
     C2<float>* g0 = G + (2 * q) * RS + c * FS;
     C2<float>* g1 = g0 + RS;
@@ -306,13 +311,13 @@ __global__ void __launch_bounds__(kThreadsReg) k_xz_reg(XzRegArgs a) {
 
 template <int NX, int NZ, int MODE>
 cudaError_t launch_reg(const sp_ctx* c, const void* in, void* out, int n_dir, cudaStream_t st) {
-  constexpr int KZ = (NZ - 1) / 3, MZ = KZ + 1, FS = MZ + 1, RS = 6 * FS;
+  constexpr int KZ = (NZ - 1) / 3, MZ = KZ + 1, FS = MZ + 1, RS = ((6 * FS + 7) / 8) * 8 + 1;
   const size_t smem = sizeof(C2<float>) * ((size_t)NX * RS + (size_t)6 * (NX / 2) * NZ);
   if (smem > 227 * 1024) return cudaErrorNotSupported;
   XzRegArgs a;
   a.in = reinterpret_cast<const C2<float>*>(in);
   a.out = reinterpret_cast<C2<float>*>(out);
-  a.base = c->base32;
+  a.base = c->base32t;
   a.yv = c->yv;
   a.NY = c->NY;
   a.Mm = c->Mm;
