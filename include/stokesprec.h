@@ -251,6 +251,63 @@ typedef struct {
 sp_status sp_newton_gmres(sp_ctx* ctx, double* U_inout, const sp_newton_opts* opts,
                           sp_newton_report* report, void* stream);
 
+/* ---- many independent problems at once -------------------------------------
+ *
+ * A group holds n independent plane Couette problems, each with its own grid,
+ * box, Reynolds number and dt (one precision for all), for instance the
+ * members of a parameter continuation. The paper treats one problem at a time;
+ * a group only batches independent problems so that many small ones fill the
+ * GPU together. It changes no arithmetic: every member's results are those of
+ * its own context.
+ * Group vector: one state per member, member i at sp_group_offset(g, i)
+ * doubles, sp_state_len(sp_group_member(g, i)) doubles long (layout and inner
+ * product as above); the gaps between members (offsets are multiples of 32
+ * doubles) are never read or written. A group vector has sp_group_state_len(g)
+ * doubles. Every stage of sp_group_step and sp_group_jvp is one launch over the
+ * blocks of all members (largest members first); the vector operations of
+ * sp_group_newton_gmres are one launch over all members' slices. */
+typedef struct sp_group sp_group;
+
+/* cfgs: n (1..4096) plane Couette configurations with the same prec; their
+ * max_batch is ignored (each member handles one direction). Uses the current
+ * device. Synchronous. On failure *out is NULL and sp_group_last_error(NULL)
+ * gives the reason. */
+sp_status sp_group_create(const sp_config* cfgs, int n, sp_group** out);
+sp_status sp_group_destroy(sp_group* g);
+const char* sp_group_last_error(const sp_group* g);
+int sp_group_size(const sp_group* g);
+size_t sp_group_state_len(const sp_group* g);
+/* Offset in doubles of member i in a group vector; (size_t)-1 if i is out of range. */
+size_t sp_group_offset(const sp_group* g, int member);
+/* The member's own context (owned by the group: do not destroy it). Every
+ * single-problem call applies to it with pointers into the member's slice, e.g.
+ * sp_seed_state(sp_group_member(g, i), ..., U + sp_group_offset(g, i), s). */
+sp_ctx* sp_group_member(sp_group* g, int member);
+
+/* G = B_dt(U) - U for every member (FP64, as sp_step). */
+sp_status sp_group_step(sp_group* g, const double* U, double* G, void* stream);
+/* Linearisation point of every member (as sp_set_base on each). */
+sp_status sp_group_set_base(sp_group* g, const double* U, void* stream);
+/* Jdu = G_U du for every member, one direction each (as sp_jvp with n_dir = 1,
+ * in the group's precision). Needs sp_group_set_base. */
+sp_status sp_group_jvp(sp_group* g, const double* du, double* Jdu, void* stream);
+/* out_host[i] = <a_i, b_i> for every member (FP64). Synchronous. */
+sp_status sp_group_inner(sp_group* g, const double* a, const double* b, double* out_host, void* stream);
+
+/* Newton-GMRES-hookstep (as sp_newton_gmres) on every member in lock step:
+ * Arnoldi step j of all members whose GMRES is still running is one sequence of
+ * launches, and all hookstep trials of one round are one step of the group.
+ * Each member has its own Krylov basis, trust radius and stopping tests, and
+ * leaves the iteration when |G| < tol (or it fails). use_fd and use_gradient
+ * must be 0. use_graphs = 1 captures the launches of each Arnoldi step j once as
+ * a CUDA graph and replays it (graphs are kept with the group and rebuilt if
+ * max_krylov grows). reports: n entries (or NULL); t_action_ms, t_orth_ms and
+ * t_total_ms are the group's totals. Synchronous. Returns SP_OK when every
+ * member converged, SP_ENAN if any member produced a non-finite value, else
+ * SP_ENOTCONV. */
+sp_status sp_group_newton_gmres(sp_group* g, double* U_inout, const sp_newton_opts* opts, int use_graphs,
+                                sp_newton_report* reports, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

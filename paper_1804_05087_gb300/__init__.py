@@ -81,6 +81,18 @@ def _load():
         "sp_vjp_euclid": ([P, P, P, I, V], I),
         "sp_trace_enable": ([P, I], I),
         "sp_trace_read": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), I], I),
+        "sp_group_create": ([ctypes.POINTER(_Config), I, ctypes.POINTER(ctypes.c_void_p)], I),
+        "sp_group_destroy": ([P], I),
+        "sp_group_last_error": ([P], ctypes.c_char_p),
+        "sp_group_size": ([P], I),
+        "sp_group_state_len": ([P], ctypes.c_size_t),
+        "sp_group_offset": ([P, I], ctypes.c_size_t),
+        "sp_group_member": ([P, I], ctypes.c_void_p),
+        "sp_group_step": ([P, P, P, V], I),
+        "sp_group_set_base": ([P, P, V], I),
+        "sp_group_jvp": ([P, P, P, V], I),
+        "sp_group_inner": ([P, P, P, ctypes.POINTER(D), V], I),
+        "sp_group_newton_gmres": ([P, P, ctypes.POINTER(_NewtonOpts), I, ctypes.POINTER(_NewtonReport), V], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -95,7 +107,9 @@ _lib = _load()
 EXPORTS = ("sp_create", "sp_destroy", "sp_last_error", "sp_state_len", "sp_dims", "sp_seed_state",
            "sp_step", "sp_set_base", "sp_jvp", "sp_vjp", "sp_jvp_fd", "sp_inner", "sp_newton_gmres",
            "sp_trace_enable", "sp_trace_read", "sp_jvp_static", "sp_vjp_euclid", "sp_pipe_create",
-           "sp_pipe_seed_state")
+           "sp_pipe_seed_state", "sp_group_create", "sp_group_destroy", "sp_group_last_error", "sp_group_size",
+           "sp_group_state_len", "sp_group_offset", "sp_group_member", "sp_group_step", "sp_group_set_base",
+           "sp_group_jvp", "sp_group_inner", "sp_group_newton_gmres")
 STAGES = ("k_yinv", "k_xz", "k_solve", "step", "vector")
 
 
@@ -139,11 +153,15 @@ def _stream(stream):
 class Context:
     """One configuration: plans, operators and workspaces on the current GPU."""
 
-    def __init__(self, cfg):
+    def __init__(self, cfg, _borrowed=None):
         self.cfg = cfg
         h = ctypes.c_void_p()
         self.pipe = isinstance(cfg, PipeConfig)
-        if self.pipe:
+        self._owned = _borrowed is None
+        if _borrowed is not None:  # a group member: the group owns the handle
+            h = ctypes.c_void_p(_borrowed)
+            st = 0
+        elif self.pipe:
             c = _PipeConfig(cfg.nr, cfg.mt, cfg.kz, cfg.ntheta, cfg.nz, cfg.sym, cfg.alpha, cfg.re, cfg.dt,
                             cfg.prec, cfg.max_batch)
             st = _lib.sp_pipe_create(ctypes.byref(c), ctypes.byref(h))
@@ -164,7 +182,8 @@ class Context:
 
     def close(self):
         if getattr(self, "_h", None):
-            _lib.sp_destroy(self._h)
+            if self._owned:
+                _lib.sp_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -291,7 +310,7 @@ class Context:
     def sp_newton_gmres(self, U, max_newton=20, max_krylov=30, tol=1e-10, eta=1e-3, delta0=0.0,
                         use_fd=False, use_gradient=False, stream=None):
         pu, _ = self._ptr(U, 1)
-        o = _NewtonOpts(max_newton, max_krylov, tol, eta, delta0, 1 if use_fd else 0, 1 if use_gradient else 0)
+        o = _opts(max_newton, max_krylov, tol, eta, delta0, use_fd, use_gradient)
         r = _NewtonReport()
         st = _lib.sp_newton_gmres(self._h, pu, ctypes.byref(o), ctypes.byref(r), _stream(stream))
         rep = {k: getattr(r, k) for k, _ in _NewtonReport._fields_}
@@ -299,6 +318,96 @@ class Context:
         if st not in (0, 4):
             self._check(st)
         return rep
+
+
+def _opts(max_newton, max_krylov, tol, eta, delta0, use_fd, use_gradient):
+    return _NewtonOpts(max_newton, max_krylov, tol, eta, delta0, 1 if use_fd else 0, 1 if use_gradient else 0)
+
+
+class Group:
+    """Many independent plane Couette problems stepped together (sp_group_*).
+
+    A group vector is a flat complex128 CUDA tensor of state_len // 2 values;
+    member i's state is ``member_view(x, i)`` (shape [3, MX, MZ, NY])."""
+
+    def __init__(self, cfgs):
+        cfgs = list(cfgs)
+        arr = (_Config * len(cfgs))(*[_Config(c.nx, c.ny, c.nz, c.lx, c.lz, c.re, c.dt, c.prec, 1) for c in cfgs])
+        h = ctypes.c_void_p()
+        st = _lib.sp_group_create(arr, len(cfgs), ctypes.byref(h))
+        if st != 0:
+            raise SpError(st, _lib.sp_group_last_error(None).decode())
+        self._h = h
+        self.cfgs = cfgs
+        self.n = int(_lib.sp_group_size(h))
+        self.state_len = int(_lib.sp_group_state_len(h))
+        self.offsets = [int(_lib.sp_group_offset(h, i)) for i in range(self.n)]
+        self.members = [Context(cfgs[i], _borrowed=_lib.sp_group_member(h, i)) for i in range(self.n)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for m in self.members:
+                m._h = None
+            _lib.sp_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            raise SpError(st, _lib.sp_group_last_error(self._h).decode())
+
+    def _ptr(self, t):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex128 \
+                or not t.is_contiguous() or t.numel() * 2 != self.state_len:
+            raise TypeError("expected a contiguous complex128 CUDA group vector")
+        if t.is_conj() or t.is_neg():
+            raise TypeError("tensor carries a lazy conjugate/negative bit")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def zeros(self, device="cuda"):
+        return torch.zeros(self.state_len // 2, dtype=torch.complex128, device=device)
+
+    def member_view(self, x, i):
+        m = self.members[i]
+        o = self.offsets[i] // 2
+        return x[o:o + m.state_len // 2].view(m.shape)
+
+    def sp_group_step(self, U, G, stream=None):
+        self._check(_lib.sp_group_step(self._h, self._ptr(U), self._ptr(G), _stream(stream)))
+        return G
+
+    def sp_group_set_base(self, U, stream=None):
+        self._check(_lib.sp_group_set_base(self._h, self._ptr(U), _stream(stream)))
+
+    def sp_group_jvp(self, du, out, stream=None):
+        self._check(_lib.sp_group_jvp(self._h, self._ptr(du), self._ptr(out), _stream(stream)))
+        return out
+
+    def sp_group_inner(self, a, b, stream=None):
+        out = (ctypes.c_double * self.n)()
+        self._check(_lib.sp_group_inner(self._h, self._ptr(a), self._ptr(b), out, _stream(stream)))
+        return list(out)
+
+    def sp_group_newton_gmres(self, U, max_newton=20, max_krylov=40, tol=1e-10, eta=1e-3, delta0=0.0,
+                              use_graphs=True, stream=None):
+        """Lock-step Newton-GMRES-hookstep on every member; returns (all converged, [reports])."""
+        o = _opts(max_newton, max_krylov, tol, eta, delta0, False, False)
+        reps = (_NewtonReport * self.n)()
+        st = _lib.sp_group_newton_gmres(self._h, self._ptr(U), ctypes.byref(o), 1 if use_graphs else 0, reps,
+                                        _stream(stream))
+        if st not in (0, 4):
+            self._check(st)
+        out = []
+        for r in reps:
+            d = {k: getattr(r, k) for k, _ in _NewtonReport._fields_}
+            d["converged"] = d["norm_F"] < tol
+            out.append(d)
+        return st == 0, out
 
 
 class StokesStep(torch.autograd.Function):

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 
+#include "hookstep.h"
 #include "sp_internal.h"
 
 static thread_local std::string g_create_error;
@@ -479,139 +480,6 @@ extern "C" sp_status sp_pipe_seed_state(sp_ctx* c, const double* streak, const d
 // ================================================================= Newton
 namespace {
 
-// Trust-region subproblem min |g - R y| s.t. |y| <= delta in the Krylov space (the hookstep,
-// Sec. 3.2): R^T R = Q T Q^T by Householder tridiagonalisation (once per Newton step), then
-// for each radius a safeguarded Newton iteration on 1/|z(mu)| - 1/delta with
-// z(mu) = (T + mu I)^-1 Q^T R^T g (two tridiagonal solves per iteration), y = Q z.
-struct TrustRegion {
-  int k = 0;
-  std::vector<double> d, e, c, V;  // diagonal, off-diagonal, Q^T b, Householder vectors (k x k)
-  std::vector<double> beta;        // reflector scalars
-
-  void setup(const double* R, int ld, int k_, const double* g) {
-    k = k_;
-    std::vector<double> M((size_t)k * k, 0.0), b(k, 0.0);
-    for (int i = 0; i < k; ++i)
-      for (int j = i; j < k; ++j) {
-        double acc = 0;
-        for (int l = 0; l <= i; ++l) acc += R[(size_t)i * ld + l] * R[(size_t)j * ld + l];
-        M[(size_t)i * k + j] = M[(size_t)j * k + i] = acc;
-      }
-    for (int j = 0; j < k; ++j) {
-      double acc = 0;
-      for (int l = 0; l <= j; ++l) acc += R[(size_t)j * ld + l] * g[l];
-      b[j] = acc;
-    }
-    V.assign((size_t)k * k, 0.0);
-    beta.assign(k, 0.0);
-    std::vector<double> p(k), wv(k);
-    for (int col = 0; col + 2 < k; ++col) {
-      // reflector zeroing M[col+2.., col]
-      double alpha = 0;
-      for (int i = col + 1; i < k; ++i) alpha += M[(size_t)i * k + col] * M[(size_t)i * k + col];
-      alpha = std::sqrt(alpha);
-      if (alpha == 0.0) continue;
-      const double x0 = M[(size_t)(col + 1) * k + col];
-      const double s = x0 >= 0 ? -alpha : alpha;
-      double* v = V.data() + (size_t)col * k;
-      for (int i = 0; i < k; ++i) v[i] = 0.0;
-      v[col + 1] = x0 - s;
-      for (int i = col + 2; i < k; ++i) v[i] = M[(size_t)i * k + col];
-      double vv = 0;
-      for (int i = col + 1; i < k; ++i) vv += v[i] * v[i];
-      if (vv == 0.0) continue;
-      const double bt = 2.0 / vv;
-      beta[col] = bt;
-      // M <- H M H with H = I - bt v v^T (symmetric rank-2 update)
-      for (int i = col; i < k; ++i) {
-        double acc = 0;
-        for (int j = col + 1; j < k; ++j) acc += M[(size_t)i * k + j] * v[j];
-        p[i] = bt * acc;
-      }
-      double vp = 0;
-      for (int i = col + 1; i < k; ++i) vp += v[i] * p[i];
-      const double kk = 0.5 * bt * vp;
-      for (int i = col; i < k; ++i) wv[i] = p[i] - kk * (i > col ? v[i] : 0.0);
-      for (int i = col; i < k; ++i)
-        for (int j = col; j < k; ++j) {
-          const double vi = i > col ? v[i] : 0.0, vj = j > col ? v[j] : 0.0;
-          M[(size_t)i * k + j] -= vi * wv[j] + wv[i] * vj;
-        }
-    }
-    d.assign(k, 0.0);
-    e.assign(k, 0.0);
-    for (int i = 0; i < k; ++i) d[i] = M[(size_t)i * k + i];
-    for (int i = 0; i + 1 < k; ++i) e[i] = M[(size_t)(i + 1) * k + i];
-    // c = Q^T b, Q = H_0 H_1 ... (apply H_0 first)
-    c = b;
-    for (int col = 0; col + 2 < k; ++col) apply(col, c);
-  }
-
-  void apply(int col, std::vector<double>& x) const {
-    if (beta[col] == 0.0) return;
-    const double* v = V.data() + (size_t)col * k;
-    double acc = 0;
-    for (int i = col + 1; i < k; ++i) acc += v[i] * x[i];
-    acc *= beta[col];
-    for (int i = col + 1; i < k; ++i) x[i] -= acc * v[i];
-  }
-
-  // (T + mu I) z = rhs by the Thomas algorithm (T + mu I is positive definite for mu > 0)
-  void tri_solve(double mu, const std::vector<double>& rhs, std::vector<double>& z) const {
-    std::vector<double> cp(k), dp(k);
-    double den = d[0] + mu;
-    cp[0] = k > 1 ? e[0] / den : 0.0;
-    dp[0] = rhs[0] / den;
-    for (int i = 1; i < k; ++i) {
-      den = d[i] + mu - e[i - 1] * cp[i - 1];
-      cp[i] = i + 1 < k ? e[i] / den : 0.0;
-      dp[i] = (rhs[i] - e[i - 1] * dp[i - 1]) / den;
-    }
-    z.assign(k, 0.0);
-    z[k - 1] = dp[k - 1];
-    for (int i = k - 2; i >= 0; --i) z[i] = dp[i] - cp[i] * z[i + 1];
-  }
-
-  std::vector<double> solve(double delta) const {
-    double tmax = 0;
-    for (int i = 0; i < k; ++i)
-      tmax = std::max(tmax, std::fabs(d[i]) + (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(e[i]) : 0.0));
-    double cn = 0;
-    for (double v : c) cn += v * v;
-    cn = std::sqrt(cn);
-    double lo = 0.0, hi = cn / delta + tmax;   // |z(hi)| <= delta
-    double mu = std::max(1e-12 * tmax, 1e-300);
-    std::vector<double> z, z2;
-    for (int it = 0; it < 100; ++it) {
-      tri_solve(mu, c, z);
-      double nz = 0;
-      for (double v : z) nz += v * v;
-      nz = std::sqrt(nz);
-      if (!std::isfinite(nz)) {  // mu too close to the spectrum's bottom
-        lo = mu;
-        mu = 0.5 * (lo + hi);
-        continue;
-      }
-      if (std::fabs(nz - delta) <= 1e-10 * delta) break;
-      if (nz > delta) lo = mu;
-      else hi = mu;
-      tri_solve(mu, z, z2);
-      double zz2 = 0;
-      for (int i = 0; i < k; ++i) zz2 += z[i] * z2[i];
-      // Newton step on phi(mu) = 1/|z| - 1/delta, phi' = (z . z2)/|z|^3
-      double step = (1.0 / nz - 1.0 / delta) * nz * nz * nz / std::max(zz2, 1e-300);
-      double next = mu - step;
-      if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
-      if (hi - lo <= 1e-15 * hi) { mu = hi; tri_solve(mu, c, z); break; }
-      mu = next;
-    }
-    // y = Q z: apply the reflectors in reverse order
-    std::vector<double> y = z;
-    for (int col = k - 3; col >= 0; --col) apply(col, y);
-    return y;
-  }
-};
-
 double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -703,19 +571,7 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
       double* Rc = R.data() + (size_t)j * LD;
       for (int i = 0; i <= j; ++i) Hc[i] = hbuf[i] + hbuf[K + 3 + i];
       Hc[j + 1] = hn;
-      for (int i = 0; i <= j + 1; ++i) Rc[i] = Hc[i];
-      for (int i = 0; i < j; ++i) {  // earlier rotations, then a new one for (j, j+1)
-        const double x = Rc[i], y = Rc[i + 1];
-        Rc[i] = cs[i] * x + sn[i] * y;
-        Rc[i + 1] = -sn[i] * x + cs[i] * y;
-      }
-      const double rr = std::hypot(Rc[j], Rc[j + 1]);
-      cs[j] = rr > 0 ? Rc[j] / rr : 1.0;
-      sn[j] = rr > 0 ? Rc[j + 1] / rr : 0.0;
-      Rc[j] = rr;
-      Rc[j + 1] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
+      givens_column(Hc, Rc, j, cs.data(), sn.data(), g.data());
       *hn_out = hn;
       return SP_OK;
     };
@@ -768,41 +624,13 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     // hookstep: minimise |g - R y| (R = rotated k x k Hessenberg) subject to |y| <= delta.
     // The constrained minimiser is y(mu) = (R^T R + mu I)^-1 R^T g with mu >= 0 chosen so that
     // |y(mu)| = delta; R^T R = Q T Q^T (tridiagonal T) makes every |y(mu)| an O(k) solve.
-    std::vector<double> y0(k, 0.0);
-    for (int i = k - 1; i >= 0; --i) {
-      double acc = g[i];
-      for (int jj = i + 1; jj < k; ++jj) acc -= R[(size_t)jj * LD + i] * y0[jj];
-      y0[i] = R[(size_t)i * LD + i] != 0.0 ? acc / R[(size_t)i * LD + i] : 0.0;
-    }
-    double ny0 = 0;
-    for (double v : y0) ny0 += v * v;
-    ny0 = std::sqrt(ny0);
-    TrustRegion tr;
-    bool have_tr = false;
+    Hookstep hs;
+    hs.init(R.data(), LD, k, g.data());
     bool accepted = false;
     double nT = nF;
     for (int trial = 0; trial < 12; ++trial) {
-      std::vector<double> y;
-      if (ny0 <= delta) {
-        y = y0;
-      } else {
-        if (!have_tr) {
-          tr.setup(R.data(), LD, k, g.data());
-          have_tr = true;
-        }
-        y = tr.solve(delta);
-      }
-      // predicted residual |g - R y|^2 + g_k^2
-      double pred2 = g[k] * g[k];
-      for (int i = 0; i < k; ++i) {
-        double acc = g[i];
-        for (int jj = i; jj < k; ++jj) acc -= R[(size_t)jj * LD + i] * y[jj];
-        pred2 += acc * acc;
-      }
-      double ylen = 0;
-      for (double v : y) ylen += v * v;
-      ylen = std::sqrt(ylen);
-      const double pred = std::sqrt(pred2);
+      double pred = 0, ylen = 0;
+      const std::vector<double> y = hs.solve(delta, &pred, &ylen);
       if ((s = sp_cuda(c, cudaMemcpyAsync(Ut, U, L * 8, cudaMemcpyDeviceToDevice, st), "copy")) != SP_OK) return s;
       if ((s = sp_cuda(c, cudaMemcpyAsync(dhn + 2, y.data(), (size_t)k * 8, cudaMemcpyHostToDevice, st), "y copy")) !=
           SP_OK)
@@ -816,14 +644,7 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
       r.total_steps++;
       if ((s = norm(F, &nT)) != SP_OK) return s;
       nT = std::sqrt(nT);
-      const double denom = nF * nF - pred * pred;
-      const double rho = denom > 0 ? (nF * nF - nT * nT) / denom : -1.0;
-      if (!(rho >= 0.01) || !std::isfinite(nT)) {
-        delta = 0.5 * ylen;
-        continue;
-      }
-      if (rho > 0.75 && ylen >= 0.99 * delta) delta *= 2.0;
-      else if (rho < 0.25) delta *= 0.5;
+      if (!trust_update(nF, pred, nT, ylen, &delta)) continue;
       accepted = true;
       break;
     }

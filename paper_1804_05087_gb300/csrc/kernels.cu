@@ -15,6 +15,7 @@
 //            the precomputed per-mode operators, and G = u_new - u.
 // T is the real type of the transforms and the product (double or float);
 // the solve and everything after it are double.
+#include <algorithm>
 #include <cstdio>
 
 #include "sp_internal.h"
@@ -123,16 +124,16 @@ struct YinvArgs {
 
 // in : [dir][3][Mm][NY] complex double (the boundary state layout)
 // out: [dir][6][NY][Mm] complex T, fields u, v, w, wx, wy, wz
+// (bx, by, bz): mode tile, Gauss-Lobatto chunk, direction
 template <typename T>
-__global__ void __launch_bounds__(kThreadsYinv) k_yinv(const double2* __restrict__ in,
-                                                      C2<T>* __restrict__ out,
-                                                      const T* __restrict__ Th,
-                                                      const T* __restrict__ TDh, YinvArgs a) {
+__device__ __forceinline__ void yinv_body(const double2* __restrict__ in, C2<T>* __restrict__ out,
+                                          const T* __restrict__ Th, const T* __restrict__ TDh,
+                                          const YinvArgs& a, int bx, int by, int bz) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* sc = reinterpret_cast<C2<T>*>(smem_raw);  // [3][NY][TM]
   const int TM = kTileYinv;
-  const int m0 = blockIdx.x * TM;
-  const int dir = blockIdx.z;
+  const int m0 = bx * TM;
+  const int dir = bz;
   const int NY = a.NY, Mm = a.Mm;
   const double2* src = in + (size_t)dir * 3 * Mm * NY;
   for (int idx = threadIdx.x; idx < 3 * TM * NY; idx += blockDim.x) {
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(kThreadsYinv) k_yinv(const double2* __restrict
     sc[(c * NY + n) * TM + t] = v;
   }
   __syncthreads();
-  const int j_lo = blockIdx.y * a.jchunk;
+  const int j_lo = by * a.jchunk;
   const int j_hi = min(a.NH, j_lo + a.jchunk);
   const int items = TM * (j_hi - j_lo);
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
@@ -207,6 +208,14 @@ __global__ void __launch_bounds__(kThreadsYinv) k_yinv(const double2* __restrict
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreadsYinv) k_yinv(const double2* __restrict__ in,
+                                                      C2<T>* __restrict__ out,
+                                                      const T* __restrict__ Th,
+                                                      const T* __restrict__ TDh, YinvArgs a) {
+  yinv_body<T>(in, out, Th, TDh, a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // -------------------------------------------------------------- k_xz
 template <typename T>
 struct XzArgs {
@@ -228,8 +237,9 @@ struct XzArgs {
 // halved and the 1/(Nx Nz) factor), the transposed product
 // (u* = Omega_tot x a, omega* = a x U_tot) and the transpose of the inverse
 // FFT (a forward FFT weighted by 1 for iz = 0 and 2 for iz > 0).
+// (bx, by): Gauss-Lobatto plane, direction
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
+__device__ __forceinline__ void xz_body(const XzArgs<T>& a, int bx, int by) {
   constexpr int NIN = MODE == XZ_ADJOINT ? 3 : 6;
   constexpr int NOUT = MODE == XZ_ADJOINT ? 6 : 3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -237,10 +247,10 @@ __global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
   C2<T>* stwz = stwx + a.nx;
   // plane buffer G [nx][6][FS] (row stride RS): in shared memory, or in global
   // memory (L2-resident) for grids whose plane does not fit on chip
-  C2<T>* G = a.Gg ? a.Gg + ((size_t)blockIdx.y * a.NY + blockIdx.x) * a.nx * a.RS : stwz + a.nz;
+  C2<T>* G = a.Gg ? a.Gg + ((size_t)by * a.NY + bx) * a.nx * a.RS : stwz + a.nz;
   C2<T>* S = a.Gg ? stwz + a.nz : G + (size_t)a.nx * a.RS;  // scratch
-  const int j = blockIdx.x;
-  const int dir = blockIdx.y;
+  const int j = bx;
+  const int dir = by;
   const int nx = a.nx, nz = a.nz, MZ = a.MZ, Kx = a.Kx, Kz = a.Kz;
   const int FS = a.FS, RS = a.RS;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) stwx[i] = ld_c2(a.twx + i);
@@ -410,6 +420,11 @@ __global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
   }
 }
 
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreadsXZ) k_xz(XzArgs<T> a) {
+  xz_body<T, MODE>(a, blockIdx.x, blockIdx.y);
+}
+
 // ------------------------------------------------------------ k_solve
 struct SolveArgs {
   const double* ops;
@@ -434,10 +449,10 @@ __device__ __forceinline__ void unique_to_mode(int u, int Kx, int MZ, int* pos, 
 
 // in3: [dir][3][NY][Mm] complex T (values of N at the Gauss-Lobatto points)
 // du : [dir][3][Mm][NY] complex double; out: same layout (G = u_new - u)
+// (bx, by): tile of solved modes, direction
 template <typename T>
-__global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict__ in3,
-                                                         const double2* __restrict__ du,
-                                                         double2* __restrict__ out, SolveArgs a) {
+__device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const double2* __restrict__ du,
+                                           double2* __restrict__ out, const SolveArgs& a, int bx, int by) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TM = kTileSolve;
   const int NY = a.NY, N = a.N, NH = a.NH, Mm = a.Mm, MZ = a.MZ;
@@ -452,8 +467,8 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict
   double2* sb = sv + TM * NY;                 // [TM][NY]
   __shared__ int s_pos[kTileSolve], s_iz[kTileSolve], s_u[kTileSolve];
   __shared__ double s_kx[kTileSolve], s_kz[kTileSolve], s_ik[kTileSolve];
-  const int u0 = blockIdx.x * TM;
-  const int dir = blockIdx.y;
+  const int u0 = bx * TM;
+  const int dir = by;
   if (threadIdx.x < TM) {
     const int u = u0 + threadIdx.x;
     int pos = 0, iz = 0;
@@ -659,6 +674,13 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict
       }
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict__ in3,
+                                                         const double2* __restrict__ du,
+                                                         double2* __restrict__ out, SolveArgs a) {
+  solve_body<T>(in3, du, out, a, blockIdx.x, blockIdx.y);
 }
 
 
@@ -1175,6 +1197,70 @@ __global__ void k_f64_to_f32(const double* a, float* b, float* bt, size_t n, int
   }
 }
 
+// ------------------------------------------------------------ grouped kernels
+// One launch over several independent problems: block b runs block
+// b - first[inst[b]] of member inst[b]'s own launch (with a single direction),
+// reading that member's launch record. The stage bodies are the ones above.
+template <typename T>
+struct GYinv {
+  size_t off;  // offset (doubles) of the member's state in a group vector
+  C2<T>* out;
+  const T* Th;
+  const T* TDh;
+  YinvArgs a;
+  int gx;      // mode tiles of the member's launch
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsYinv) k_yinv_grp(const double* __restrict__ in_base,
+                                                          const GYinv<T>* __restrict__ recs,
+                                                          const int* __restrict__ inst,
+                                                          const int* __restrict__ first,
+                                                          const int* __restrict__ active) {
+  const int i = inst[blockIdx.x];
+  if (active && !active[i]) return;
+  __shared__ GYinv<T> r;
+  if (threadIdx.x == 0) r = recs[i];
+  __syncthreads();
+  const int b = blockIdx.x - first[i];
+  yinv_body<T>(reinterpret_cast<const double2*>(in_base + r.off), r.out, r.Th, r.TDh, r.a, b % r.gx, b / r.gx, 0);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreadsXZ) k_xz_grp(const XzArgs<T>* __restrict__ recs,
+                                                      const int* __restrict__ inst,
+                                                      const int* __restrict__ first,
+                                                      const int* __restrict__ active) {
+  const int i = inst[blockIdx.x];
+  if (active && !active[i]) return;
+  __shared__ XzArgs<T> r;
+  if (threadIdx.x == 0) r = recs[i];
+  __syncthreads();
+  xz_body<T, MODE>(r, blockIdx.x - first[i], 0);
+}
+
+struct GSolve {
+  size_t off;
+  const void* in3;  // the member's product values
+  SolveArgs a;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsSolve) k_solve_grp(const double* __restrict__ du_base,
+                                                            double* __restrict__ out_base,
+                                                            const GSolve* __restrict__ recs,
+                                                            const int* __restrict__ inst,
+                                                            const int* __restrict__ first,
+                                                            const int* __restrict__ active) {
+  const int i = inst[blockIdx.x];
+  if (active && !active[i]) return;
+  __shared__ GSolve r;
+  if (threadIdx.x == 0) r = recs[i];
+  __syncthreads();
+  solve_body<T>(reinterpret_cast<const C2<T>*>(r.in3), reinterpret_cast<const double2*>(du_base + r.off),
+                reinterpret_cast<double2*>(out_base + r.off), r.a, blockIdx.x - first[i], 0);
+}
+
 int grid_for(size_t n, int threads, int sms) {
   size_t g = (n + threads - 1) / threads;
   size_t cap = (size_t)sms * 8;
@@ -1257,9 +1343,9 @@ cudaError_t launch_yinv(const sp_ctx* c, bool fp32, const double* in, void* out6
   return cudaGetLastError();
 }
 
-template <typename T, int MODE>
-static cudaError_t launch_xz_t(const sp_ctx* c, const void* in6, void* out3, T* base, const C2<T>* twx,
-                               const C2<T>* twz, int rp, int cx, size_t smem, int n_dir, cudaStream_t st) {
+template <typename T>
+static XzArgs<T> make_xz_args(const sp_ctx* c, const void* in6, void* out3, T* base, const C2<T>* twx,
+                              const C2<T>* twz, int rp, int cx) {
   XzArgs<T> a;
   a.in6 = reinterpret_cast<const C2<T>*>(in6);
   a.out3 = reinterpret_cast<C2<T>*>(out3);
@@ -1276,7 +1362,14 @@ static cudaError_t launch_xz_t(const sp_ctx* c, const void* in6, void* out3, T* 
   a.RS = 6 * a.FS;
   const bool glob = sizeof(T) == 8 ? c->xz_gglob64 : c->xz_gglob32;
   a.Gg = glob ? reinterpret_cast<C2<T>*>(c->wsG) : nullptr;
-  if (glob && n_dir > c->cfg.max_batch) return cudaErrorInvalidValue;
+  return a;
+}
+
+template <typename T, int MODE>
+static cudaError_t launch_xz_t(const sp_ctx* c, const void* in6, void* out3, T* base, const C2<T>* twx,
+                               const C2<T>* twz, int rp, int cx, size_t smem, int n_dir, cudaStream_t st) {
+  XzArgs<T> a = make_xz_args<T>(c, in6, out3, base, twx, twz, rp, cx);
+  if (a.Gg && n_dir > c->cfg.max_batch) return cudaErrorInvalidValue;
   cudaFuncSetAttribute(k_xz<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid(c->NY, n_dir);
   k_xz<T, MODE><<<grid, kThreadsXZ, smem, st>>>(a);
@@ -1493,5 +1586,197 @@ cudaError_t launch_scale_dev(const sp_ctx* c, double* x, const double* s, cudaSt
 cudaError_t launch_multi_axpy(const sp_ctx* c, const double* V, int k, const double* h, double* w,
                               cudaStream_t st) {
   k_multi_axpy<<<grid_for(c->state_len, 256, c->sm_count), 256, 0, st>>>(V, k, c->state_len, h, w);
+  return cudaGetLastError();
+}
+
+
+// ================================================================ grouped launches
+cudaError_t grp_upload(void** dst, const void* src, size_t bytes) {
+  *dst = nullptr;
+  if (bytes == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(dst, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+}
+
+void grp_kernel_free(GrpKernel* k) {
+  if (k->recs) cudaFree(k->recs);
+  if (k->inst) cudaFree(k->inst);
+  if (k->first) cudaFree(k->first);
+  *k = GrpKernel{};
+}
+
+void grp_plan_free(GrpPlan* p) {
+  for (GrpKernel* k : {&p->yinv64, &p->yinv32, &p->xz64, &p->xz32, &p->solve64, &p->solve32}) grp_kernel_free(k);
+  for (GrpKernel& k : p->xzr) grp_kernel_free(&k);
+  p->n = 0;
+}
+
+// lay the members' blocks out in `order`, upload the records and the block maps
+template <typename R>
+static cudaError_t grp_make(GrpKernel* k, const std::vector<R>& recs, const std::vector<int>& nblk, const int* order,
+                            int n, size_t smem) {
+  std::vector<int> inst, first(n, 0);
+  for (int q = 0; q < n; ++q) {
+    const int m = order[q];
+    first[m] = (int)inst.size();
+    for (int b = 0; b < nblk[m]; ++b) inst.push_back(m);
+  }
+  k->blocks = (int)inst.size();
+  k->smem = smem;
+  cudaError_t e;
+  if ((e = grp_upload(&k->recs, recs.data(), recs.size() * sizeof(R))) != cudaSuccess) return e;
+  if ((e = grp_upload((void**)&k->inst, inst.data(), inst.size() * sizeof(int))) != cudaSuccess) return e;
+  return grp_upload((void**)&k->first, first.data(), first.size() * sizeof(int));
+}
+
+template <typename T>
+static cudaError_t grp_build_yinv(GrpKernel* k, sp_ctx* const* mem, int n, const size_t* offs, const int* order,
+                                  int jsplit) {
+  std::vector<GYinv<T>> recs(n);
+  std::vector<int> nblk(n);
+  size_t smem = 0;
+  for (int m = 0; m < n; ++m) {
+    const sp_ctx* c = mem[m];
+    GYinv<T>& r = recs[m];
+    r.off = offs[m];
+    r.out = reinterpret_cast<C2<T>*>(c->ws6);
+    if constexpr (sizeof(T) == 8) {
+      r.Th = c->Th;
+      r.TDh = c->TDh;
+    } else {
+      r.Th = c->Th_f;
+      r.TDh = c->TDh_f;
+    }
+    YinvArgs& a = r.a;
+    a.Mm = c->Mm; a.MZ = c->MZ; a.MX = c->MX; a.Kx = c->Kx; a.NY = c->NY; a.N = c->N; a.NH = c->NH;
+    a.alpha = c->alpha; a.beta = c->beta;
+    a.jchunk = (c->NH + jsplit - 1) / jsplit;
+    r.gx = (c->Mm + kTileYinv - 1) / kTileYinv;
+    nblk[m] = r.gx * ((c->NH + a.jchunk - 1) / a.jchunk);
+    smem = std::max(smem, (size_t)3 * c->NY * kTileYinv * sizeof(C2<T>));
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_yinv_grp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return grp_make(k, recs, nblk, order, n, smem);
+}
+
+// skip[m] != 0 leaves member m out of this launch (its plane stage runs elsewhere)
+template <typename T>
+static cudaError_t grp_build_xz(GrpKernel* k, sp_ctx* const* mem, int n, const int* order,
+                                const std::vector<int>* skip = nullptr) {
+  std::vector<XzArgs<T>> recs(n);
+  std::vector<int> nblk(n);
+  size_t smem = 0;
+  for (int m = 0; m < n; ++m) {
+    const sp_ctx* c = mem[m];
+    if constexpr (sizeof(T) == 8) {
+      recs[m] = make_xz_args<double>(c, c->ws6, c->ws3, c->base64, reinterpret_cast<const C2<double>*>(c->twx),
+                                     reinterpret_cast<const C2<double>*>(c->twz), c->xz_rp64, c->xz_cx64);
+      smem = std::max(smem, c->smem_xz64);
+    } else {
+      recs[m] = make_xz_args<float>(c, c->ws6, c->ws3, c->base32, reinterpret_cast<const C2<float>*>(c->twx_f),
+                                    reinterpret_cast<const C2<float>*>(c->twz_f), c->xz_rp32, c->xz_cx32);
+      smem = std::max(smem, c->smem_xz32);
+    }
+    nblk[m] = skip && (*skip)[m] ? 0 : c->NY;
+  }
+  for (auto fn : {k_xz_grp<T, XZ_STEP>, k_xz_grp<T, XZ_BASE>, k_xz_grp<T, XZ_TANGENT>}) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  return grp_make(k, recs, nblk, order, n, smem);
+}
+
+static cudaError_t grp_build_solve(GrpKernel* k, sp_ctx* const* mem, int n, const size_t* offs, const int* order,
+                                   int esize) {
+  std::vector<GSolve> recs(n);
+  std::vector<int> nblk(n);
+  size_t smem = 0;
+  for (int m = 0; m < n; ++m) {
+    const sp_ctx* c = mem[m];
+    recs[m].off = offs[m];
+    recs[m].in3 = c->ws3;
+    recs[m].a = solve_args(c);
+    nblk[m] = (c->n_unique + kTileSolve - 1) / kTileSolve;
+    smem = std::max(smem, solve_smem(c, esize));
+  }
+  cudaError_t e = esize == 8
+                      ? cudaFuncSetAttribute(k_solve_grp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                      : cudaFuncSetAttribute(k_solve_grp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return grp_make(k, recs, nblk, order, n, smem);
+}
+
+cudaError_t grp_plan_build(GrpPlan* p, sp_ctx* const* mem, int n, const size_t* offs, const int* order) {
+  p->n = n;
+  // split the Gauss-Lobatto points of k_yinv only when the whole group has too few mode tiles
+  int tiles = 0, nh_min = 1 << 30;
+  for (int m = 0; m < n; ++m) {
+    tiles += (mem[m]->Mm + kTileYinv - 1) / kTileYinv;
+    nh_min = std::min(nh_min, mem[m]->NH);
+  }
+  int jsplit = 1;
+  while (tiles * jsplit < 2 * mem[0]->sm_count && jsplit < nh_min) ++jsplit;
+  cudaError_t e;
+  if ((e = grp_build_yinv<double>(&p->yinv64, mem, n, offs, order, jsplit)) != cudaSuccess) return e;
+  if ((e = grp_build_yinv<float>(&p->yinv32, mem, n, offs, order, jsplit)) != cudaSuccess) return e;
+  if ((e = grp_build_xz<double>(&p->xz64, mem, n, order)) != cudaSuccess) return e;
+  // float plane stage: the register-FFT kernel for the members whose own context uses it,
+  // the generic kernel for the others (so every member computes exactly as on its own)
+  std::vector<int> reg(n);
+  for (int m = 0; m < n; ++m) reg[m] = mem[m]->use_xz_reg && sp_xz_reg_supported(mem[m]);
+  if ((e = grp_build_xz_reg(p->xzr, mem, n, order, reg)) != cudaSuccess) return e;
+  if ((e = grp_build_xz<float>(&p->xz32, mem, n, order, &reg)) != cudaSuccess) return e;
+  if ((e = grp_build_solve(&p->solve64, mem, n, offs, order, 8)) != cudaSuccess) return e;
+  return grp_build_solve(&p->solve32, mem, n, offs, order, 4);
+}
+
+cudaError_t grp_launch_yinv(const GrpPlan& p, bool fp32, const double* in_base, const int* active, cudaStream_t st) {
+  const GrpKernel& k = fp32 ? p.yinv32 : p.yinv64;
+  if (k.blocks == 0) return cudaSuccess;
+  if (fp32)
+    k_yinv_grp<float><<<k.blocks, kThreadsYinv, k.smem, st>>>(in_base, static_cast<const GYinv<float>*>(k.recs),
+                                                               k.inst, k.first, active);
+  else
+    k_yinv_grp<double><<<k.blocks, kThreadsYinv, k.smem, st>>>(in_base, static_cast<const GYinv<double>*>(k.recs),
+                                                                k.inst, k.first, active);
+  return cudaGetLastError();
+}
+
+cudaError_t grp_launch_xz(const GrpPlan& p, bool fp32, int mode, const int* active, cudaStream_t st) {
+  if (fp32) {
+    if (mode != XZ_TANGENT) return cudaErrorInvalidValue;  // the step and the base are always FP64
+    cudaError_t e = grp_launch_xz_reg(p.xzr, active, st);
+    if (e != cudaSuccess) return e;
+    const GrpKernel& k = p.xz32;
+    if (k.blocks == 0) return cudaSuccess;
+    k_xz_grp<float, XZ_TANGENT><<<k.blocks, kThreadsXZ, k.smem, st>>>(static_cast<const XzArgs<float>*>(k.recs),
+                                                                       k.inst, k.first, active);
+    return cudaGetLastError();
+  }
+  const GrpKernel& k = p.xz64;
+  if (k.blocks == 0) return cudaSuccess;
+  const XzArgs<double>* r = static_cast<const XzArgs<double>*>(k.recs);
+  switch (mode) {
+    case XZ_STEP: k_xz_grp<double, XZ_STEP><<<k.blocks, kThreadsXZ, k.smem, st>>>(r, k.inst, k.first, active); break;
+    case XZ_BASE: k_xz_grp<double, XZ_BASE><<<k.blocks, kThreadsXZ, k.smem, st>>>(r, k.inst, k.first, active); break;
+    case XZ_TANGENT:
+      k_xz_grp<double, XZ_TANGENT><<<k.blocks, kThreadsXZ, k.smem, st>>>(r, k.inst, k.first, active);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t grp_launch_solve(const GrpPlan& p, bool fp32, const double* du_base, double* out_base, const int* active,
+                             cudaStream_t st) {
+  const GrpKernel& k = fp32 ? p.solve32 : p.solve64;
+  if (k.blocks == 0) return cudaSuccess;
+  const GSolve* r = static_cast<const GSolve*>(k.recs);
+  if (fp32)
+    k_solve_grp<float><<<k.blocks, kThreadsSolve, k.smem, st>>>(du_base, out_base, r, k.inst, k.first, active);
+  else
+    k_solve_grp<double><<<k.blocks, kThreadsSolve, k.smem, st>>>(du_base, out_base, r, k.inst, k.first, active);
   return cudaGetLastError();
 }

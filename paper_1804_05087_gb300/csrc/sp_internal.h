@@ -141,6 +141,42 @@ cudaError_t launch_pipe_seed(const sp_ctx* c, const double* streak, const double
 bool sp_xz_fits(sp_ctx* c);
 size_t sp_xz_global_plane_bytes(const sp_ctx* c);  // per direction, 0 if every plane fits on chip
 
+// ------------------------------------------------------------ grouped launches
+// One launch over the blocks of several contexts (the members of an sp_group):
+// block b belongs to member inst[b] and is that member's block b - first[inst[b]]
+// of its own launch. recs is a device array of per-member launch records.
+struct GrpKernel {
+  void* recs = nullptr;
+  int* inst = nullptr;
+  int* first = nullptr;
+  int blocks = 0;
+  size_t smem = 0;
+};
+constexpr int kGrpRegClasses = 5;  // register-FFT plane kernels: grids 16, 24, 32, 48, 64
+struct GrpPlan {
+  int n = 0;
+  GrpKernel yinv64, yinv32, xz64, solve64, solve32;
+  GrpKernel xz32;                 // float plane stage of the members without a register-FFT kernel
+  GrpKernel xzr[kGrpRegClasses];  // float plane stage of the others, per grid size class (xz_reg.cu)
+};
+// members: n contexts; offs: offset (doubles) of each member's state in a group
+// vector; order: member indices, largest first (blocks are laid out in this order)
+cudaError_t grp_plan_build(GrpPlan* p, sp_ctx* const* members, int n, const size_t* offs, const int* order);
+void grp_plan_free(GrpPlan* p);
+// active: device int [n] (nonzero = run this member) or null for all
+cudaError_t grp_launch_yinv(const GrpPlan& p, bool fp32, const double* in_base, const int* active, cudaStream_t st);
+cudaError_t grp_launch_xz(const GrpPlan& p, bool fp32, int mode, const int* active, cudaStream_t st);
+cudaError_t grp_launch_solve(const GrpPlan& p, bool fp32, const double* du_base, double* out_base,
+                             const int* active, cudaStream_t st);
+// register-FFT plane stage over the members with use[m] != 0, one launch per grid
+// size class (xz_reg.cu); ks: kGrpRegClasses kernels
+cudaError_t grp_build_xz_reg(GrpKernel* ks, sp_ctx* const* members, int n, const int* order,
+                             const std::vector<int>& use);
+cudaError_t grp_launch_xz_reg(const GrpKernel* ks, const int* active, cudaStream_t st);
+// device copy of a host table; frees nothing on failure
+cudaError_t grp_upload(void** dst, const void* src, size_t bytes);
+void grp_kernel_free(GrpKernel* k);
+
 // kernel launchers (kernels.cu); all asynchronous on `st`
 enum XzMode { XZ_STEP = 0, XZ_TANGENT = 1, XZ_BASE = 2, XZ_ADJOINT = 3 };
 cudaError_t launch_yinv(const sp_ctx* c, bool fp32, const double* in, void* out6, int n_dir,

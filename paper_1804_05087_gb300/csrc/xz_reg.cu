@@ -12,7 +12,9 @@
 // in digit-reversed positions resolved by a compile-time index map, twiddles
 // as compile-time constants (sine and cosine evaluated by Taylor series at
 // compile time).
+#include <algorithm>
 #include <utility>
+#include <vector>
 
 #include "sp_internal.h"
 
@@ -161,8 +163,9 @@ struct XzRegArgs {
 
 constexpr int kThreadsReg = 256;
 
+// (bx, by): Gauss-Lobatto plane, direction
 template <int NX, int NZ, int MODE>
-__global__ void __launch_bounds__(kThreadsReg) k_xz_reg(XzRegArgs a) {
+__device__ __forceinline__ void xz_reg_body(const XzRegArgs& a, int bx, int by) {
   constexpr int NIN = MODE == XZ_ADJOINT ? 3 : 6;
   constexpr int NOUT = MODE == XZ_ADJOINT ? 6 : 3;
   constexpr int KX = (NX - 1) / 3, KZ = (NZ - 1) / 3;
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(kThreadsReg) k_xz_reg(XzRegArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<float>* G = reinterpret_cast<C2<float>*>(smem_raw);  // [NX][6][FS] (row stride RS)
   C2<float>* Ph = G + NX * RS;                              // [6][NZ][NQ] packed row pairs, pair fastest
-  const int j = blockIdx.x, dir = blockIdx.y;
+  const int j = bx, dir = by;
   const size_t planeMm = (size_t)a.NY * a.Mm;
   const C2<float>* in = a.in + (size_t)dir * NIN * planeMm + (size_t)j * a.Mm;
   const float inv = (float)(1.0 / ((double)NX * (double)NZ));
@@ -310,6 +313,36 @@ __global__ void __launch_bounds__(kThreadsReg) k_xz_reg(XzRegArgs a) {
 }
 
 template <int NX, int NZ, int MODE>
+__global__ void __launch_bounds__(kThreadsReg) k_xz_reg(XzRegArgs a) {
+  xz_reg_body<NX, NZ, MODE>(a, blockIdx.x, blockIdx.y);
+}
+
+// one launch over the members of a group that share the grid size NX = NZ
+// (one such launch per size class keeps each class at its own register count)
+struct GXzReg {
+  XzRegArgs a;
+};
+
+template <int NX, int NZ, int MODE>
+__global__ void __launch_bounds__(kThreadsReg) k_xz_reg_grp(const GXzReg* __restrict__ recs,
+                                                           const int* __restrict__ inst,
+                                                           const int* __restrict__ first,
+                                                           const int* __restrict__ active) {
+  const int i = inst[blockIdx.x];
+  if (active && !active[i]) return;
+  __shared__ GXzReg r;
+  if (threadIdx.x == 0) r = recs[i];
+  __syncthreads();
+  xz_reg_body<NX, NZ, MODE>(r.a, blockIdx.x - first[i], 0);
+}
+
+constexpr int kRegSizes[5] = {16, 24, 32, 48, 64};
+
+constexpr size_t reg_smem(int n) {
+  return sizeof(C2<float>) * ((size_t)n * ((6 * ((n - 1) / 3 + 2) + 7) / 8 * 8 + 1) + (size_t)6 * (n / 2) * n);
+}
+
+template <int NX, int NZ, int MODE>
 cudaError_t launch_reg(const sp_ctx* c, const void* in, void* out, int n_dir, cudaStream_t st) {
   constexpr int KZ = (NZ - 1) / 3, MZ = KZ + 1, FS = MZ + 1, RS = ((6 * FS + 7) / 8) * 8 + 1;
   const size_t smem = sizeof(C2<float>) * ((size_t)NX * RS + (size_t)6 * (NX / 2) * NZ);
@@ -341,6 +374,75 @@ cudaError_t dispatch_reg(const sp_ctx* c, const void* in, void* out, int n_dir, 
 }
 
 }  // namespace
+
+template <int NX>
+static cudaError_t reg_grp_attr(size_t smem) {
+  return cudaFuncSetAttribute(k_xz_reg_grp<NX, NX, XZ_TANGENT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t grp_build_xz_reg(GrpKernel* ks, sp_ctx* const* mem, int n, const int* order,
+                             const std::vector<int>& use) {
+  std::vector<GXzReg> recs(n);
+  for (int m = 0; m < n; ++m) {
+    const sp_ctx* c = mem[m];
+    recs[m] = GXzReg{};
+    if (!use[m]) continue;
+    if (!sp_xz_reg_supported(c)) return cudaErrorNotSupported;
+    recs[m].a.in = reinterpret_cast<const C2<float>*>(c->ws6);
+    recs[m].a.out = reinterpret_cast<C2<float>*>(c->ws3);
+    recs[m].a.base = c->base32t;
+    recs[m].a.yv = c->yv;
+    recs[m].a.NY = c->NY;
+    recs[m].a.Mm = c->Mm;
+  }
+  for (int cls = 0; cls < kGrpRegClasses; ++cls) {
+    const int nx = kRegSizes[cls];
+    std::vector<int> inst, first(n, 0);
+    for (int q = 0; q < n; ++q) {
+      const int m = order[q];
+      if (!use[m] || mem[m]->nx != nx) continue;
+      first[m] = (int)inst.size();
+      for (int b = 0; b < mem[m]->NY; ++b) inst.push_back(m);
+    }
+    GrpKernel* k = ks + cls;
+    if (inst.empty()) continue;
+    const size_t smem = reg_smem(nx);
+    cudaError_t e;
+    switch (nx) {
+      case 16: e = reg_grp_attr<16>(smem); break;
+      case 24: e = reg_grp_attr<24>(smem); break;
+      case 32: e = reg_grp_attr<32>(smem); break;
+      case 48: e = reg_grp_attr<48>(smem); break;
+      default: e = reg_grp_attr<64>(smem); break;
+    }
+    if (e != cudaSuccess) return e;
+    k->blocks = (int)inst.size();
+    k->smem = smem;
+    if ((e = grp_upload(&k->recs, recs.data(), recs.size() * sizeof(GXzReg))) != cudaSuccess) return e;
+    if ((e = grp_upload((void**)&k->inst, inst.data(), inst.size() * sizeof(int))) != cudaSuccess) return e;
+    if ((e = grp_upload((void**)&k->first, first.data(), first.size() * sizeof(int))) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t grp_launch_xz_reg(const GrpKernel* ks, const int* active, cudaStream_t st) {
+  // largest grids first
+  for (int cls = kGrpRegClasses - 1; cls >= 0; --cls) {
+    const GrpKernel& k = ks[cls];
+    if (k.blocks == 0) continue;
+    const GXzReg* r = static_cast<const GXzReg*>(k.recs);
+    switch (kRegSizes[cls]) {
+      case 16: k_xz_reg_grp<16, 16, XZ_TANGENT><<<k.blocks, kThreadsReg, k.smem, st>>>(r, k.inst, k.first, active); break;
+      case 24: k_xz_reg_grp<24, 24, XZ_TANGENT><<<k.blocks, kThreadsReg, k.smem, st>>>(r, k.inst, k.first, active); break;
+      case 32: k_xz_reg_grp<32, 32, XZ_TANGENT><<<k.blocks, kThreadsReg, k.smem, st>>>(r, k.inst, k.first, active); break;
+      case 48: k_xz_reg_grp<48, 48, XZ_TANGENT><<<k.blocks, kThreadsReg, k.smem, st>>>(r, k.inst, k.first, active); break;
+      default: k_xz_reg_grp<64, 64, XZ_TANGENT><<<k.blocks, kThreadsReg, k.smem, st>>>(r, k.inst, k.first, active); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 bool sp_xz_reg_supported(const sp_ctx* c) {
   if (c->nx != c->nz) return false;
