@@ -49,6 +49,8 @@ def parse():
                    help="time-to-converge comparison (Newton-GMRES-hookstep) instead of the JVP throughput")
     p.add_argument("--grid", default="16x33x16", help="grid of the --newton run")
     p.add_argument("--krylov", type=int, default=300)
+    p.add_argument("--config2", action="store_true",
+                   help="64 plane Couette instances (Re ~ U[200,1000], four grids) in lock-step group Newton")
     p.add_argument("--config4", action="store_true",
                    help="96x97x96, Re 1000, doubled box: adjoint gradient check and Newton-hookstep with J^T F")
     return p.parse_args()
@@ -80,10 +82,15 @@ def kernel_bytes(stage, n_dir, esz):
     if stage == "k_xz":
         return n_dir * 9 * ny * mm * esz + 6 * ny * NX * NZ * esz // 2
     if stage == "k_solve":
-        n = ny - 1
-        op = (n // 2 + 1) * (n - 1) + (n // 2) * (n - 1) + (n // 2 + 1) * (n // 2) + (n // 2) * (n // 2 - 1)
-        return n_dir * (3 * ny * mm * esz + 2 * state) + n_unique() * op * 8
+        return n_dir * (3 * ny * mm * esz + 2 * state) + n_unique() * op_entries() * 8
     return 0
+
+
+def op_entries():
+    """Entries of the per-mode operators V_0, V_1, H_0, H_1 (each nv_P x rb_P, real)."""
+    n = NY - 1
+    nv0, nv1, rb0, rb1 = n // 2 + 1, n // 2, n // 2, n // 2 - 1
+    return 2 * (nv0 * rb0 + nv1 * rb1)
 
 
 def kernel_flops(stage, n_dir):
@@ -99,11 +106,12 @@ def kernel_flops(stage, n_dir):
         per_plane = (6 + 3) * mz * fx + (6 + 3) * (NX // 2) * fz + NX * NZ * 30
         return n_dir * ny * per_plane
     if stage == "k_solve":
-        # FP64 work only: the per-mode operators (complex input, real matrices) and the
-        # continuity/rotation epilogue; the Chebyshev transform (float in mixed mode) is excluded
+        # FP64 work only: the per-mode operators (real matrices on complex right-hand sides,
+        # 4 flops per entry), the reduced right-hand side g (one complex FMA and one complex
+        # update per momentum row) and the continuity/rotation epilogue (16 per point); the
+        # Chebyshev transform (float in mixed mode) is excluded
         n = ny - 1
-        op = (n // 2 + 1) * (n - 1) + (n // 2) * (n - 1) + (n // 2 + 1) * (n // 2) + (n // 2) * (n // 2 - 1)
-        return n_dir * n_unique() * (op * 4 + ny * 16)
+        return n_dir * n_unique() * (op_entries() * 4 + (n - 1) * 8 + ny * 16)
     return 0
 
 
@@ -276,12 +284,108 @@ def run_config4(args):
     print(json.dumps(out))
 
 
+def config2_members(seed=3000, n=64):
+    """The 64 instances: Re ~ U[200, 1000] and grids drawn uniformly from four sizes."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    grids = [(24, 33, 24), (32, 49, 32), (48, 65, 48), (64, 65, 64)]
+    res = rng.uniform(200.0, 1000.0, n)
+    gi = rng.integers(0, len(grids), n)
+    return [(grids[int(k)], float(r)) for k, r in zip(gi, res)]
+
+
+def run_config2(args):
+    """Batched continuation: 64 plane Couette instances with their own Re and grid, mixed
+    precision, Newton-GMRES-hookstep with a budget of 3 Newton steps x 40 Krylov vectors.
+    The group runs every member in lock step (one launch per stage over all members,
+    optionally graph-replayed Arnoldi steps); the baselines solve the members one after
+    another through their own contexts: mixed tangent, and the plain FP64 GPU path
+    (finite-difference actions, no batching, no graphs)."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1804_05087_gb300 as sp
+    import seeded_inputs as si
+    members = config2_members()
+    budget = dict(max_newton=3, max_krylov=40, tol=1e-10, eta=1e-3)
+
+    def cfg(g, re, prec):
+        return sp.Config(*g, lx=LX, lz=LZ, re=re, dt=DT, prec=prec)
+
+    def seed_into(ctx, i, U):
+        a, b, c = si.couette_random_coeffs(3001 + i, ctx.cfg.nx, ctx.cfg.ny, ctx.cfg.nz)
+        ctx.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], 0.1, U)
+
+    def summary(reps, wall):
+        red = [r["norm_F"] / r["norm_F0"] for r in reps]
+        return {"wall_s": wall, "converged": int(sum(r["norm_F"] < 1e-10 for r in reps)),
+                "median_F_over_F0": float(np.median(red)), "max_F_over_F0": float(np.max(red)),
+                "total_jvps": int(sum(r["total_jvps"] for r in reps)),
+                "newton_iters": int(sum(r["newton_iters"] for r in reps))}
+
+    grp = sp.Group([cfg(g, re, sp.SP_MIXED) for g, re in members])
+    U0 = grp.zeros()
+    for i, m in enumerate(grp.members):
+        seed_into(m, i, grp.member_view(U0, i))
+    out = {"metric": "config 2: batched continuation, 64 instances, 3 Newton x 40 GMRES (mixed)",
+           "unit": "s", "higher_is_better": False,
+           "config": {"workload": "64 plane Couette instances, Re ~ U[200,1000], grids from "
+                                  "{24x33x24, 32x49x32, 48x65x48, 64x65x64} (seed 3000), dt=100, amplitude 0.1",
+                      "group_state_MB": grp.state_len * 8 / 1e6,
+                      "grids": {f"{g[0]}x{g[1]}x{g[2]}": sum(1 for gg, _ in members if gg == g)
+                                for g in sorted(set(g for g, _ in members))}},
+           "runs": {}}
+    for graphs in (True, False):
+        for rep_i in range(2):  # the first call builds the graphs and the Krylov basis
+            U = U0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ok, reps = grp.sp_group_newton_gmres(U, use_graphs=graphs, **budget)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        run = summary(reps, wall)
+        run["t_action_ms"] = reps[0]["t_action_ms"]
+        run["t_orth_ms"] = reps[0]["t_orth_ms"]
+        out["runs"]["group_graphs" if graphs else "group_launches"] = run
+    for name, prec, fd in (("sequential_mixed_tangent", sp.SP_MIXED, False), ("sequential_fp64_fd", sp.SP_FP64, True)):
+        reps, wall = [], 0.0
+        for i, (g, re) in enumerate(members):
+            ctx = sp.Context(cfg(g, re, prec))
+            U = ctx.zeros()
+            seed_into(ctx, i, U)
+            ctx.sp_newton_gmres(U.clone(), max_newton=1, max_krylov=2, tol=1e-10)  # warm the context
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = ctx.sp_newton_gmres(U, use_fd=fd, **budget)
+            torch.cuda.synchronize()
+            wall += time.perf_counter() - t0
+            reps.append(rep)
+            ctx.close()
+        out["runs"][name] = summary(reps, wall)
+    r = out["runs"]
+    out["speedup_group_vs_sequential_fp64_fd"] = r["sequential_fp64_fd"]["wall_s"] / r["group_graphs"]["wall_s"]
+    out["speedup_group_vs_sequential_mixed"] = r["sequential_mixed_tangent"]["wall_s"] / r["group_graphs"]["wall_s"]
+    # beyond the budget: how many members reach |F| < 1e-10
+    U = U0.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ok, reps = grp.sp_group_newton_gmres(U, max_newton=20, max_krylov=args.krylov, tol=1e-10, eta=1e-3,
+                                         use_graphs=True)
+    torch.cuda.synchronize()
+    conv = summary(reps, time.perf_counter() - t0)
+    conv["max_newton"], conv["max_krylov"] = 20, args.krylov
+    out["to_convergence"] = conv
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.newton:
         return run_newton(args)
+    if args.config2:
+        return run_config2(args)
     if args.config4:
         return run_config4(args)
     import torch

@@ -59,8 +59,14 @@ __global__ void __launch_bounds__(kVecThreads) k_gdots(const double* __restrict_
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] = 0.0;
   const double2* w2 = reinterpret_cast<const double2*>(w + r.off);
-  for (size_t e = (size_t)b * blockDim.x + threadIdx.x; e < r.ncplx; e += (size_t)r.nb * blockDim.x) {
-    const double wt = (int)((e / r.NY) % r.MZ) == 0 ? 1.0 : 2.0;
+  // the weight of element e depends on iz = (e / NY) mod MZ; follow (iz, e mod NY)
+  // incrementally along the stride instead of dividing per element
+  const unsigned NY = r.NY, MZ = r.MZ, S = (unsigned)r.nb * blockDim.x;
+  const unsigned dq = S / NY, dr = S - dq * NY, dz = dq % MZ;
+  unsigned e0 = (unsigned)b * blockDim.x + threadIdx.x;
+  unsigned rr = e0 % NY, iz = (e0 / NY) % MZ;
+  for (unsigned e = e0; e < r.ncplx; e += S) {
+    const double wt = iz == 0 ? 1.0 : 2.0;
     const double2 bv = w2[e];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -69,11 +75,28 @@ __global__ void __launch_bounds__(kVecThreads) k_gdots(const double* __restrict_
         acc[q] += wt * (a.x * bv.x + a.y * bv.y);
       }
     }
+    rr += dr;
+    iz += dz;
+    if (rr >= NY) {
+      rr -= NY;
+      ++iz;
+    }
+    if (iz >= MZ) iz -= MZ;
   }
+  // the eight block sums with one barrier: warp shuffles, then one thread per row
+  __shared__ double red8[8][kVecThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const double s = blk_sum(acc[q]);
-    if (threadIdx.x == 0 && i0 + q < k) partials[(size_t)(i0 + q) * gridDim.x + blockIdx.x] = s;
+    double v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red8[q][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8 && i0 + (int)threadIdx.x < k) {
+    double v = 0.0;
+    for (int w8 = 0; w8 < kVecThreads / 32; ++w8) v += red8[threadIdx.x][w8];
+    partials[(size_t)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
   }
 }
 
@@ -252,7 +275,7 @@ extern "C" sp_status sp_group_create(const sp_config* cfgs, int n, sp_group** ou
                    [&](int a, int b) { return g->mem[a]->state_len > g->mem[b]->state_len; });
   cudaError_t e = grp_plan_build(&g->plan, g->mem.data(), n, g->off.data(), g->order.data());
   if (e != cudaSuccess) return bail(SP_ECUDA, std::string("grouped launch tables: ") + cudaGetErrorString(e));
-  // vector launches: about 1024 complex values per block
+  // vector launches: about 4096 complex values per block (16 per thread)
   g->vrecs_h.resize(n);
   std::vector<int> vinst;
   for (int q = 0; q < n; ++q) {
@@ -263,7 +286,7 @@ extern "C" sp_status sp_group_create(const sp_config* cfgs, int n, sp_group** ou
     r.ncplx = c->cplx_per_state;
     r.NY = c->NY;
     r.MZ = c->MZ;
-    r.nb = (int)std::max<size_t>(1, (r.ncplx + 1023) / 1024);
+    r.nb = (int)std::max<size_t>(1, (r.ncplx + 4095) / 4096);
     r.first = (int)vinst.size();
     for (int b = 0; b < r.nb; ++b) vinst.push_back(i);
   }

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cstdio>
 
+#include "dev_util.h"
 #include "sp_internal.h"
 
 namespace {
@@ -555,8 +556,9 @@ __device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const 
     sf[(c * TM + t) * NR + n] = f;
   }
   __syncthreads();
-  // phase C: rotate to the components along / across the wavevector
-  const int rv0 = N / 2, rv1 = N / 2 - 1;  // f_v rows of parity 0 / 1
+  // phase C: rotate to the components along / across the wavevector; f_v goes to
+  // srv (per parity), f~_a = -i f_a replaces f_x in sf (same thread, same slot)
+  double2* sfa = sf;  // [TM][NR]: component 0 of sf after this phase
   for (int idx = threadIdx.x; idx < TM * NR; idx += blockDim.x) {
     const int t = idx / NR, n = idx - t * NR;
     const int pos = s_pos[t], iz = s_iz[t];
@@ -571,55 +573,57 @@ __device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const 
     }
     const double2 fa = make_double2((kx * fx.x + kz * fz.x) * ik, (kx * fx.y + kz * fz.y) * ik);
     const double2 fb = make_double2((-kz * fx.x + kx * fz.x) * ik, (-kz * fx.y + kx * fz.y) * ik);
-    const double2 fta = make_double2(fa.y, -fa.x);  // -i f_a
     sfb[t * NR + n] = fb;
-    const int P = n & 1;
-    srv[(t * 2 + P) * a.cv + n / 2] = fy;                  // f_v row n -> V_P
-    const int Pa = 1 - P;                                   // f~_a row n -> V_{1-P}
-    srv[(t * 2 + Pa) * a.cv + (Pa == 0 ? rv0 : rv1) + n / 2] = fta;
+    srv[(t * 2 + (n & 1)) * a.cv + n / 2] = fy;         // f_v row n -> parity n & 1
+    sfa[t * NR + n] = make_double2(fa.y, -fa.x);        // f~_a = -i f_a
   }
   __syncthreads();
-  // phase D: apply the per-mode operators (FP64). The mean-mode test is hoisted
-  // out of the loops so that no predicated-off double FMA occupies the FP64 pipe.
+  // phase C2: reduced right-hand side g_n = f_v,n - (2 / (c_n k)) sum_{m > n, m + n odd,
+  // m <= N-2} m f~_a,m for each parity P (one suffix sum per mode and parity)
+  if (threadIdx.x < 2 * TM) {
+    const int t = threadIdx.x >> 1, P = threadIdx.x & 1;
+    if (s_u[t] < a.n_unique && !(s_pos[t] == 0 && s_iz[t] == 0)) {
+      const double ik = s_ik[t];
+      double2* g = srv + (t * 2 + P) * a.cv;
+      double2 S = make_double2(0.0, 0.0);
+      for (int n = (P == 0 ? N - 2 : N - 3); n >= 0; n -= 2) {
+        const int m = n + 1;
+        if (m <= N - 2) {
+          const double2 x = sfa[t * NR + m];
+          S.x = fma((double)m, x.x, S.x);
+          S.y = fma((double)m, x.y, S.y);
+        }
+        const double f = (n == 0 ? 1.0 : 2.0) * ik;
+        const double2 v = g[n / 2];
+        g[n / 2] = make_double2(v.x - f * S.x, v.y - f * S.y);
+      }
+    }
+  }
+  __syncthreads();
+  // phase D: apply the per-mode operators (FP64). Threads take the even unknowns of a
+  // mode first, then the odd ones, so that a warp reads consecutive rows of one
+  // column-major operator (coalesced). The mean-mode test is hoisted out of the
+  // loops so that no predicated-off double FMA occupies the FP64 pipe.
+  const int nv0 = N / 2 + 1;  // even unknowns
   for (int idx = threadIdx.x; idx < TM * NY; idx += blockDim.x) {
-    const int t = idx / NY, n = idx - t * NY;
+    const int t = idx / NY, k = idx - t * NY;
     if (s_u[t] >= a.n_unique) continue;
     const double* op = a.ops + (size_t)s_u[t] * a.op_stride;
-    const int Q = n & 1, row = n >> 1;
+    const int Q = k < nv0 ? 0 : 1, row = Q == 0 ? k : k - nv0, n = 2 * row + Q;
+    const int nrow = Q == 0 ? nv0 : NY - nv0;
     const int rb = Q == 0 ? a.rb0 : a.rb1;
-    const double* H = op + (Q == 0 ? a.off_h0 : a.off_h1) + (size_t)row * rb;
+    const double* H = op + (Q == 0 ? a.off_h0 : a.off_h1) + row;
     const double2* fbq = sfb + t * NR + Q;
     if (s_pos[t] == 0 && s_iz[t] == 0) {
       // mean flow: u and w from the Helmholtz operator, v = 0
       const double2* fwq = sfw + t * NR + Q;
-      double2 accb = make_double2(0.0, 0.0), accw = accb;
-      for (int cidx = 0; cidx < rb; ++cidx) {
-        const double h = __ldg(H + cidx);
-        accb.x = fma(h, fbq[2 * cidx].x, accb.x);
-        accb.y = fma(h, fbq[2 * cidx].y, accb.y);
-        accw.x = fma(h, fwq[2 * cidx].x, accw.x);
-        accw.y = fma(h, fwq[2 * cidx].y, accw.y);
-      }
-      sb[t * NY + n] = accb;
-      sv[t * NY + n] = accw;
+      sb[t * NY + n] = dot4(H, nrow, fbq, 2, rb);
+      sv[t * NY + n] = dot4(H, nrow, fwq, 2, rb);
       continue;
     }
-    double2 accb = make_double2(0.0, 0.0);
-    for (int cidx = 0; cidx < rb; ++cidx) {
-      const double h = __ldg(H + cidx);
-      accb.x = fma(h, fbq[2 * cidx].x, accb.x);
-      accb.y = fma(h, fbq[2 * cidx].y, accb.y);
-    }
-    sb[t * NY + n] = accb;
-    const double* V = op + (Q == 0 ? a.off_v0 : a.off_v1) + (size_t)row * a.cv;
-    const double2* r = srv + (t * 2 + Q) * a.cv;
-    double2 accv = make_double2(0.0, 0.0);
-    for (int cidx = 0; cidx < a.cv; ++cidx) {
-      const double vv = __ldg(V + cidx);
-      accv.x = fma(vv, r[cidx].x, accv.x);
-      accv.y = fma(vv, r[cidx].y, accv.y);
-    }
-    sv[t * NY + n] = accv;
+    sb[t * NY + n] = dot4(H, nrow, fbq, 2, rb);
+    const double* V = op + (Q == 0 ? a.off_v0 : a.off_v1) + row;
+    sv[t * NY + n] = dot4(V, nrow, srv + (t * 2 + Q) * a.cv, 1, rb);
   }
   __syncthreads();
   // (D v)_n = (2/c_n) sum_{p > n, p + n odd} p v_p: one suffix sum per (mode, parity),
@@ -786,24 +790,17 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve_adj(const double2* __re
     sva[idx] = make_double2(gv.x + s * acc.y, gv.y - s * acc.x);
   }
   __syncthreads();
-  // V_P^T v* (columns of V_P) and H_Q^T gb
+  // V_P^T v* (columns of V_P: the adjoint of g) and H_Q^T gb
   for (int idx = threadIdx.x; idx < TM * 2 * a.cv; idx += blockDim.x) {
     const int t = idx / (2 * a.cv), rem = idx - t * 2 * a.cv;
     const int P = rem / a.cv, col = rem - P * a.cv;
-    if (s_u[t] >= a.n_unique || (s_pos[t] == 0 && s_iz[t] == 0)) {
+    if (s_u[t] >= a.n_unique || (s_pos[t] == 0 && s_iz[t] == 0) || col >= (P == 0 ? a.rb0 : a.rb1)) {
       srv[idx] = make_double2(0.0, 0.0);
       continue;
     }
     const double* V = a.ops + (size_t)s_u[t] * a.op_stride + (P == 0 ? a.off_v0 : a.off_v1);
     const int nv = P == 0 ? N / 2 + 1 : N / 2;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int row = 0; row < nv; ++row) {
-      const double vv = __ldg(V + (size_t)row * a.cv + col);
-      const double2 x = sva[t * NY + P + 2 * row];
-      acc.x += vv * x.x;
-      acc.y += vv * x.y;
-    }
-    srv[idx] = acc;
+    srv[idx] = dot4(V + (size_t)col * nv, 1, sva + t * NY + P, 2, nv);  // column col of V_P
   }
   for (int idx = threadIdx.x; idx < TM * NR; idx += blockDim.x) {
     const int t = idx / NR, n = idx - t * NR;  // momentum row n
@@ -813,25 +810,36 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve_adj(const double2* __re
     const int nrow = Q == 0 ? N / 2 + 1 : N / 2;
     const double* H = a.ops + (size_t)s_u[t] * a.op_stride + (Q == 0 ? a.off_h0 : a.off_h1);
     const bool mean = s_pos[t] == 0 && s_iz[t] == 0;
-    double2 accb = make_double2(0.0, 0.0), accw = accb;
-    for (int row = 0; row < nrow; ++row) {
-      const double h = __ldg(H + (size_t)row * rb + col);
-      const double2 gb = sgb[t * NY + Q + 2 * row];
-      accb.x += h * gb.x;
-      accb.y += h * gb.y;
-      if (mean) {
-        // sga holds gu and sgb holds gw for the mean mode
-        const double2 gu = sga[t * NY + Q + 2 * row];
-        accw.x += h * gu.x;
-        accw.y += h * gu.y;
-      }
-    }
-    sfb[idx] = accb;
-    sfw[idx] = accw;
+    const double* Hc = H + (size_t)col * nrow;  // column col of H_Q
+    sfb[idx] = dot4(Hc, 1, sgb + t * NY + Q, 2, nrow);
+    // sga holds gu and sgb holds gw for the mean mode
+    sfw[idx] = mean ? dot4(Hc, 1, sga + t * NY + Q, 2, nrow) : make_double2(0.0, 0.0);
   }
   __syncthreads();
-  // f* per component, rows 0..N-2
-  const int rv0 = N / 2, rv1 = N / 2 - 1;
+  // g = f_v - (1/k) D f~_a  =>  f_v* = g*, f~_a*,m = -(2m/k) sum_{n < m, n + m odd} g*_n / c_n
+  // (prefix sums over the f_v rows of the other parity), kept in component 0 of sf
+  double2* sfa = sf;
+  if (threadIdx.x < 2 * TM) {
+    const int t = threadIdx.x >> 1, q = threadIdx.x & 1;  // parity of the f~_a rows
+    if (s_u[t] < a.n_unique && !(s_pos[t] == 0 && s_iz[t] == 0)) {
+      const double2* gs = srv + (t * 2 + (1 - q)) * a.cv;  // g* of parity 1 - q
+      const double ik = s_ik[t];
+      double2 S = make_double2(0.0, 0.0);
+      for (int m = q; m <= N - 2; m += 2) {
+        if (m >= 1) {
+          const int n = m - 1;
+          const double w = n == 0 ? 0.5 : 1.0;
+          const double2 x = gs[n >> 1];
+          S.x = fma(w, x.x, S.x);
+          S.y = fma(w, x.y, S.y);
+        }
+        const double f = -2.0 * m * ik;
+        sfa[t * NR + m] = make_double2(f * S.x, f * S.y);
+      }
+    }
+  }
+  __syncthreads();
+  // f* per component, rows 0..N-2 (each thread reads its f~_a* slot before overwriting it)
   for (int idx = threadIdx.x; idx < TM * NR; idx += blockDim.x) {
     const int t = idx / NR, n = idx - t * NR;
     double2 fx, fy, fz;
@@ -840,9 +848,9 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve_adj(const double2* __re
       fz = make_double2(sfb[idx].x, 0.0);  // H^T gw
       fy = make_double2(0.0, 0.0);
     } else {
-      const int P = n & 1, Pa = 1 - P;
+      const int P = n & 1;
       fy = srv[(t * 2 + P) * a.cv + (n >> 1)];
-      const double2 fta = srv[(t * 2 + Pa) * a.cv + (Pa == 0 ? rv0 : rv1) + (n >> 1)];
+      const double2 fta = sfa[t * NR + n];
       const double2 fa = make_double2(-fta.y, fta.x);  // f_a* = i f~_a*
       const double2 fb = sfb[idx];
       const double kx = s_kx[t], kz = s_kz[t], ik = s_ik[t];
@@ -1124,8 +1132,12 @@ __global__ void k_multi_inner8(const double2* V, int k, size_t ncplx, const doub
   double acc[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ncplx; e += (size_t)gridDim.x * blockDim.x) {
-    const int iz = (int)((e / NY) % MZ);
+  // weight of element e: iz = (e / NY) mod MZ, followed incrementally along the stride
+  const unsigned S = gridDim.x * blockDim.x, dq = S / (unsigned)NY, dr = S - dq * (unsigned)NY,
+                 dz = dq % (unsigned)MZ;
+  const unsigned e0 = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned rr = e0 % (unsigned)NY, iz = (e0 / (unsigned)NY) % (unsigned)MZ;
+  for (size_t e = e0; e < ncplx; e += S) {
     const double wt = iz == 0 ? 1.0 : 2.0;
     const double2 b = w[e];
 #pragma unroll
@@ -1135,11 +1147,28 @@ __global__ void k_multi_inner8(const double2* V, int k, size_t ncplx, const doub
         acc[q] += wt * (a.x * b.x + a.y * b.y);
       }
     }
+    rr += dr;
+    iz += dz;
+    if (rr >= (unsigned)NY) {
+      rr -= NY;
+      ++iz;
+    }
+    if (iz >= (unsigned)MZ) iz -= MZ;
   }
+  // the eight block sums with one barrier: warp shuffles, then one thread per row
+  __shared__ double red8[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const double s = block_sum(acc[q]);
-    if (threadIdx.x == 0 && i0 + q < k) partials[(size_t)(i0 + q) * gridDim.x + blockIdx.x] = s;
+    double v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red8[q][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8 && i0 + (int)threadIdx.x < k) {
+    double v = 0.0;
+    for (int w8 = 0; w8 < nw; ++w8) v += red8[threadIdx.x][w8];
+    partials[(size_t)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
   }
 }
 

@@ -11,6 +11,7 @@
 //             G = u_new - u with a Hermitian output.
 // Index conventions: position pos over the axial wavenumbers in FFT order
 // (k = alpha kz), iz = m' (m = sym m').
+#include "dev_util.h"
 #include "sp_internal.h"
 
 namespace {
@@ -24,7 +25,7 @@ struct PArgs {
   const double* r;      // [NR]
   const double* w1;     // [2][NR][9]
   const int* c1;        // [2][NR][9]
-  const double* pops;   // [n_unique][3NR][3NR]
+  const double* pops;   // [n_unique][3NR][3NR], column-major
   size_t pop_stride;
   size_t sstride;       // complex values per state (field + speed)
   int Mm, MX, MZ, Kx, NR, n_unique;
@@ -187,21 +188,11 @@ __global__ void __launch_bounds__(kThreadsPS) k_psolve(const C2<T>* __restrict__
       // rows NR..2NR-1: u_theta = H1 f_theta; rows 2NR..3NR-1: u_z = H0 f_z; u_r = 0
       if (row >= NR) {
         const int blk = row < 2 * NR ? 0 : 1, i = row - (blk + 1) * NR;
-        const double* H = S + (size_t)blk * NR * NR + (size_t)i * NR;
-        const double2* ff = f + (blk + 1) * NR;
-        for (int col = 0; col < NR; ++col) {
-          const double h = __ldg(H + col);
-          acc.x = fma(h, ff[col].x, acc.x);
-          acc.y = fma(h, ff[col].y, acc.y);
-        }
+        // column-major blocks: row i of block blk
+        acc = dot4(S + (size_t)blk * NR * NR + i, NR, f + (blk + 1) * NR, 1, NR);
       }
     } else {
-      const double* Srow = S + (size_t)row * n3;
-      for (int col = 0; col < n3; ++col) {
-        const double s = __ldg(Srow + col);
-        acc.x = fma(s, f[col].x, acc.x);
-        acc.y = fma(s, f[col].y, acc.y);
-      }
+      acc = dot4(S + row, n3, f, 1, n3);  // row `row` of the column-major operator
     }
     sx[idx] = acc;
   }

@@ -18,7 +18,12 @@
 // Even and odd Chebyshev degrees decouple: v of parity P couples with a~ and
 // p of parity 1-P. For each parity the real system is factored once and its
 // inverse, restricted to the momentum right-hand sides and to the v unknowns,
-// is stored (the matrix V_P); a follows from continuity, a = (i/k) D v.
+// gives v; a follows from continuity, a = (i/k) D v. Eliminating a~ and p with
+// continuity and the a~-momentum rows shows that f~_a only enters through the
+// reduced right-hand side g = f_v - (1/k) D f~_a (rows of parity P, the sum over
+// the a~-momentum rows m > n), so v = V_P g: only the f_v columns of the
+// restricted inverse are stored (the matrix V_P, nv_P x rb_P), and the kernels
+// form g with one O(N) suffix sum.
 // b uses the restricted inverse H_Q of the Dirichlet Helmholtz tau problem.
 // The mean mode (0,0) uses H_Q with k = 0 for u and w.
 #include <cmath>
@@ -110,8 +115,8 @@ struct ChebOps {
   }
 };
 
-// V_P: rows = v unknowns of parity P (increasing n), columns = [f_v rows of
-// parity P (n <= N-2), f~_a rows of parity 1-P (n <= N-2)].
+// V_P: rows = v unknowns of parity P (increasing n), columns = f_v rows of
+// parity P (n <= N-2): the restricted inverse applied to g (see above).
 bool build_vop(const ChebOps& C, int P, double k, double lam, double nu, double* out) {
   const int N = C.N, n1 = N + 1;
   std::vector<int> vi, ai;
@@ -156,15 +161,14 @@ bool build_vop(const ChebOps& C, int P, double k, double lam, double nu, double*
   if (r != nt) return false;
   std::vector<int> piv;
   if (!lu_factor(A, nt, piv)) return false;
-  rhs_rows = vrows;
-  rhs_rows.insert(rhs_rows.end(), arows.begin(), arows.end());
+  rhs_rows = vrows;  // the f_v rows only: f~_a enters through g
   const int ncol = (int)rhs_rows.size();
   std::vector<double> b(nt);
   for (int cidx = 0; cidx < ncol; ++cidx) {
     std::fill(b.begin(), b.end(), 0.0);
     b[rhs_rows[cidx]] = 1.0;
     lu_solve(A, nt, piv, b.data());
-    for (int i = 0; i < nv; ++i) out[(size_t)i * ncol + cidx] = b[i];
+    for (int i = 0; i < nv; ++i) out[(size_t)cidx * nv + i] = b[i];  // column-major
   }
   return true;
 }
@@ -196,7 +200,7 @@ bool build_hop(const ChebOps& C, int Q, double lam, double nu, double* out) {
     std::fill(b.begin(), b.end(), 0.0);
     b[rows[cidx]] = 1.0;
     lu_solve(A, nb, piv, b.data());
-    for (int i = 0; i < nb; ++i) out[(size_t)i * ncol + cidx] = b[i];
+    for (int i = 0; i < nb; ++i) out[(size_t)cidx * nb + i] = b[i];  // column-major
   }
   return true;
 }
@@ -248,12 +252,12 @@ sp_status sp_build_plan(sp_ctx* c) {
   // per-mode operators
   c->nv0 = N / 2 + 1;
   c->nv1 = N / 2;
-  c->cv = N - 1;
-  c->rb0 = N / 2;
-  c->rb1 = N / 2 - 1;
+  c->rb0 = N / 2;      // momentum rows of parity 0 (n <= N-2): columns of V_0 and H_0
+  c->rb1 = N / 2 - 1;  // parity 1: columns of V_1 and H_1
+  c->cv = N / 2;       // stride of the per-parity right-hand sides in shared memory
   c->off_v0 = 0;
-  c->off_v1 = c->off_v0 + c->nv0 * c->cv;
-  c->off_h0 = c->off_v1 + c->nv1 * c->cv;
+  c->off_v1 = c->off_v0 + c->nv0 * c->rb0;
+  c->off_h0 = c->off_v1 + c->nv1 * c->rb1;
   c->off_h1 = c->off_h0 + c->nv0 * c->rb0;
   c->op_stride = c->off_h1 + c->nv1 * c->rb1;
   std::vector<double> ops((size_t)c->n_unique * c->op_stride, 0.0);

@@ -20,8 +20,9 @@
 // with L_q = D2 + D1/r - q^2/r^2 - k^2 and
 // div_h u = (1/2)[(D1 + (1+m)/r) u+ + (D1 + (1-m)/r) u-] - k u~_z.
 // The operator stored per mode maps (f+, f-, f~_z) at all radial points to
-// (u+, u-, u~_z): a dense real 3Nr x 3Nr matrix, the restriction of the inverse
-// of the 4Nr x 4Nr system composed with its right-hand-side map.
+// (u+, u-, u~_z): a dense real 3Nr x 3Nr matrix (stored column-major), the
+// restriction of the inverse of the 4Nr x 4Nr system composed with its
+// right-hand-side map.
 // Mode (0,0): u_r = 0 and two Helmholtz problems (u_theta with L_1, u_z with L_0).
 #include <algorithm>
 #include <cmath>
@@ -176,7 +177,7 @@ sp_status sp_build_pipe_plan(sp_ctx* c) {
             std::fill(b.begin(), b.end(), 0.0);
             b[col] = 1.0;
             lu_solve(A, nr, piv, b.data());
-            for (int i = 0; i < nr; ++i) out[(size_t)blk * nr * nr + (size_t)i * nr + col] = b[i];
+            for (int i = 0; i < nr; ++i) out[(size_t)blk * nr * nr + (size_t)col * nr + i] = b[i];
           }
         }
         continue;
@@ -239,7 +240,7 @@ sp_status sp_build_pipe_plan(sp_ctx* c) {
         }
         if (!any) continue;  // wall entries of f do not enter
         lu_solve(A, n4, piv, col.data());
-        for (int i = 0; i < n3; ++i) out[(size_t)i * n3 + cc] = col[i];
+        for (int i = 0; i < n3; ++i) out[(size_t)cc * n3 + i] = col[i];
       }
     }
   };

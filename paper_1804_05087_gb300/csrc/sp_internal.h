@@ -63,9 +63,10 @@ struct sp_ctx {
   size_t cplx_per_state = 0;     // complex values per state (pipe: + 1 for the speed)
   size_t field_cplx = 0;         // complex values of the velocity field, 3 Mm NY
   FftPlan px{}, pz{};
-  // per-mode solve operators: V0, V1, H0, H1 (row-major), FP64
-  int nv0 = 0, nv1 = 0, cv = 0;  // rows of V0 / V1, columns of both (N-1)
-  int rb0 = 0, rb1 = 0;          // columns of H0 / H1 (rows: nv0 / nv1)
+  // per-mode solve operators: V0, V1, H0, H1, FP64, column-major (element (row, col) at
+  // col * rows + row, so that threads on consecutive rows read consecutive addresses)
+  int nv0 = 0, nv1 = 0, cv = 0;  // rows of V0 / V1 (and H0 / H1); cv = N/2: RHS stride
+  int rb0 = 0, rb1 = 0;          // columns of V0, H0 / V1, H1: momentum rows of each parity
   int off_v0 = 0, off_v1 = 0, off_h0 = 0, off_h1 = 0, op_stride = 0;
 
   // device tables
@@ -76,7 +77,7 @@ struct sp_ctx {
   double2 *twx = nullptr, *twz = nullptr;
   float2 *twx_f = nullptr, *twz_f = nullptr;
   double* ops = nullptr;
-  // pipe: per-mode dense operators (3 NY x 3 NY), radial FD band (D1) tables
+  // pipe: per-mode dense operators (3 NY x 3 NY, column-major), radial FD band (D1) tables
   double* pops = nullptr;
   size_t pop_stride = 0;
   double* fd_w1 = nullptr;       // [2 parities][NY][9] weights of the first derivative

@@ -130,4 +130,6 @@ def test_group_newton_matches_single_contexts():
         rep = m.sp_newton_gmres(u, max_newton=20, max_krylov=200, tol=1e-10)
         assert rep["converged"]
         assert rep["newton_iters"] == reps[i]["newton_iters"]
-        assert rep["total_jvps"] == reps[i]["total_jvps"]
+        # the group's weighted dot products sum over other partial blocks than the single
+        # context's: a GMRES stopping test may flip by one action at the threshold
+        assert abs(rep["total_jvps"] - reps[i]["total_jvps"]) <= rep["newton_iters"]
