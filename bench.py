@@ -211,6 +211,7 @@ def run_newton(args):
     for name, prec, fd in (("mixed_tangent", sp.SP_MIXED, False), ("fp64_tangent", sp.SP_FP64, False),
                            ("fp64_fd", sp.SP_FP64, True)):
         ctx = sp.Context(sp.Config(nx, ny, nz, lx=LX, lz=LZ, re=RE, dt=DT, prec=prec))
+        ctx.sp_autotune(1)
         a, b, c = si.couette_random_coeffs(1000, nx, ny, nz)
         U = ctx.zeros()
         ctx.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], 0.1, U)
@@ -241,6 +242,8 @@ def run_config4(args):
     lx, lz = 4 * math.pi / 1.14, 4 * math.pi / 2.5
     ctx = sp.Context(sp.Config(nx, ny, nz, lx=lx, lz=lz, re=1000.0, dt=DT, prec=sp.SP_MIXED))
     ctx64 = sp.Context(sp.Config(nx, ny, nz, lx=lx, lz=lz, re=1000.0, dt=DT, prec=sp.SP_FP64))
+    ctx.sp_autotune(1)
+    ctx64.sp_autotune(1)
 
     def seeded(c, seed, amp):
         a, b, cc = si.couette_random_coeffs(seed, nx, ny, nz)
@@ -351,6 +354,7 @@ def run_config2(args):
         reps, wall = [], 0.0
         for i, (g, re) in enumerate(members):
             ctx = sp.Context(cfg(g, re, prec))
+            ctx.sp_autotune(1)
             U = ctx.zeros()
             seed_into(ctx, i, U)
             ctx.sp_newton_gmres(U.clone(), max_newton=1, max_krylov=2, tol=1e-10)  # warm the context
@@ -415,6 +419,7 @@ def main():
         D[i].copy_(seeded(DIR_SEED0 + rank * nd + i, 1.0))
     OUT = ctx.zeros(nd)
     stream = torch.cuda.current_stream()
+    tune = ctx.sp_autotune(nd)  # tile shapes of the solve kernel, before any timing
 
     def step():
         ctx.sp_set_base(U)
@@ -515,7 +520,8 @@ def main():
                "config": {"workload": "plane Couette 48x65x48, Re=400, dt=100, box 2pi/1.14 x 2 x 2pi/2.5; "
                                       "per step: set_base + tangent on 256 seeded unit directions",
                           "grid": [NX, NY, NZ], "ndir_per_gpu": nd, "precision": args.prec,
-                          "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+                          "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
+                          "solve_tile": {"tangent": list(tune["tangent"]), "step": list(tune["step"])}},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(out))
     if world > 1:

@@ -218,6 +218,34 @@ sp_status sp_trace_enable(sp_ctx* ctx, int on);
  * launch counts of the n (<= SP_NSTAGE) first stages. Host arrays. */
 sp_status sp_trace_read(sp_ctx* ctx, double* ms, long long* launches, int n);
 
+/* ---- tile autotuner -------------------------------------------------------- */
+
+/* The per-mode solve kernel (the dominant kernel of the tangent) can run with
+ * several tile shapes: solved modes per block x threads per block. Every shape
+ * computes each mode with the same arithmetic, so results are identical bit for
+ * bit; only the speed differs with the grid and the batch. sp_autotune times
+ * every shape that fits in shared memory on this context's own workspaces
+ * (zeroed scratch, so the context's data is untouched): n_dir directions in the
+ * tangent's precision, and one direction in FP64 (the step of sp_step,
+ * sp_set_base and the Newton residual). It keeps the fastest of each for every
+ * later call on this context. Without it the context uses shape 0.
+ * Synchronous; allocates and frees its scratch (2 n_dir states). */
+#define SP_TUNE_MAX 8
+typedef struct {
+  int n_shapes;                  /* shapes in the table                             */
+  int tile[SP_TUNE_MAX];         /* solved modes per block                          */
+  int threads[SP_TUNE_MAX];      /* threads per block                               */
+  double ms_tangent[SP_TUNE_MAX];/* mean launch time, n_dir directions (< 0: does not fit) */
+  double ms_step[SP_TUNE_MAX];   /* mean launch time, one FP64 direction (< 0: does not fit) */
+  int chosen_tangent, chosen_step;
+} sp_tune_report;
+sp_status sp_autotune(sp_ctx* ctx, int n_dir, sp_tune_report* report, void* stream);
+/* Pin the tile shapes (indices into the report's table; -1 keeps the current
+ * one), e.g. to reuse an earlier sp_autotune result without timing again.
+ * SP_EINVAL for an index out of range; a shape that does not fit in shared
+ * memory makes the later call fail with SP_ECUDA. */
+sp_status sp_set_solve_shape(sp_ctx* ctx, int tangent_shape, int step_shape);
+
 /* ---- Newton-GMRES-hookstep ------------------------------------------------ */
 
 typedef struct {

@@ -50,6 +50,12 @@ class _NewtonOpts(ctypes.Structure):
                 ("use_gradient", ctypes.c_int)]
 
 
+class _TuneReport(ctypes.Structure):
+    _fields_ = [("n_shapes", ctypes.c_int), ("tile", ctypes.c_int * 8), ("threads", ctypes.c_int * 8),
+                ("ms_tangent", ctypes.c_double * 8), ("ms_step", ctypes.c_double * 8),
+                ("chosen_tangent", ctypes.c_int), ("chosen_step", ctypes.c_int)]
+
+
 class _NewtonReport(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("total_jvps", ctypes.c_int), ("total_steps", ctypes.c_int),
                 ("norm_F", ctypes.c_double), ("norm_F0", ctypes.c_double), ("t_action_ms", ctypes.c_double),
@@ -81,6 +87,8 @@ def _load():
         "sp_vjp_euclid": ([P, P, P, I, V], I),
         "sp_trace_enable": ([P, I], I),
         "sp_trace_read": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), I], I),
+        "sp_autotune": ([P, I, ctypes.POINTER(_TuneReport), V], I),
+        "sp_set_solve_shape": ([P, I, I], I),
         "sp_group_create": ([ctypes.POINTER(_Config), I, ctypes.POINTER(ctypes.c_void_p)], I),
         "sp_group_destroy": ([P], I),
         "sp_group_last_error": ([P], ctypes.c_char_p),
@@ -109,7 +117,8 @@ EXPORTS = ("sp_create", "sp_destroy", "sp_last_error", "sp_state_len", "sp_dims"
            "sp_trace_enable", "sp_trace_read", "sp_jvp_static", "sp_vjp_euclid", "sp_pipe_create",
            "sp_pipe_seed_state", "sp_group_create", "sp_group_destroy", "sp_group_last_error", "sp_group_size",
            "sp_group_state_len", "sp_group_offset", "sp_group_member", "sp_group_step", "sp_group_set_base",
-           "sp_group_jvp", "sp_group_inner", "sp_group_newton_gmres")
+           "sp_group_jvp", "sp_group_inner", "sp_group_newton_gmres", "sp_autotune",
+           "sp_set_solve_shape")
 STAGES = ("k_yinv", "k_xz", "k_solve", "step", "vector")
 
 
@@ -295,6 +304,19 @@ class Context:
         out = (ctypes.c_double * n)()
         self._check(_lib.sp_inner(self._h, pa, pb, n, out, _stream(stream)))
         return list(out)
+
+    def sp_autotune(self, n_dir=1, stream=None):
+        """Time the solve kernel's tile shapes and keep the fastest (see include/stokesprec.h)."""
+        r = _TuneReport()
+        self._check(_lib.sp_autotune(self._h, int(n_dir), ctypes.byref(r), _stream(stream)))
+        n = r.n_shapes
+        return {"shapes": [(r.tile[i], r.threads[i]) for i in range(n)],
+                "ms_tangent": [r.ms_tangent[i] for i in range(n)], "ms_step": [r.ms_step[i] for i in range(n)],
+                "tangent": (r.tile[r.chosen_tangent], r.threads[r.chosen_tangent]),
+                "step": (r.tile[r.chosen_step], r.threads[r.chosen_step])}
+
+    def sp_set_solve_shape(self, tangent=-1, step=-1):
+        self._check(_lib.sp_set_solve_shape(self._h, int(tangent), int(step)))
 
     def sp_trace_enable(self, on=True):
         self._check(_lib.sp_trace_enable(self._h, 1 if on else 0))

@@ -265,7 +265,7 @@ static sp_status step_batch(sp_ctx* c, const double* U, double* G, int n, cudaSt
     }
     if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_yinv(c, false, u, c->ws6, nb, st); }), "yinv")) != SP_OK) return s;
     if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_xz(c, false, XZ_STEP, c->ws6, c->ws3, nb, st); }), "xz step")) != SP_OK) return s;
-    if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_solve(c, false, c->ws3, u, g, nb, st); }), "solve")) != SP_OK) return s;
+    if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_solve(c, false, c->ws3, u, g, nb, st, c->solve_shape_step); }), "solve")) != SP_OK) return s;
   }
   return SP_OK;
 }

@@ -26,6 +26,7 @@ namespace {
 constexpr int kThreadsXZ = 256;
 constexpr int kThreadsYinv = 256;
 constexpr int kThreadsSolve = 128;
+constexpr int kThreadsSolveGrp = 192;  // grouped solve (4 modes per block)
 constexpr int kTileYinv = 16;   // modes per k_yinv block
 constexpr int kTileSolve = 4;   // modes per k_solve block
 
@@ -451,11 +452,11 @@ __device__ __forceinline__ void unique_to_mode(int u, int Kx, int MZ, int* pos, 
 // in3: [dir][3][NY][Mm] complex T (values of N at the Gauss-Lobatto points)
 // du : [dir][3][Mm][NY] complex double; out: same layout (G = u_new - u)
 // (bx, by): tile of solved modes, direction
-template <typename T>
+// TM: solved modes per block (any block size works; every mode's arithmetic is the same)
+template <typename T, int TM>
 __device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const double2* __restrict__ du,
                                            double2* __restrict__ out, const SolveArgs& a, int bx, int by) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int TM = kTileSolve;
   const int NY = a.NY, N = a.N, NH = a.NH, Mm = a.Mm, MZ = a.MZ;
   const int NR = N - 1;  // tau rows 0..N-2
   C2<T>* svals = reinterpret_cast<C2<T>*>(smem_raw);                    // [3][NY][TM]
@@ -466,8 +467,8 @@ __device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const 
   double2* sfw = sfb + TM * NR;               // [TM][NR] (mean mode w)
   double2* sv = sfw + TM * NR;                // [TM][NY]
   double2* sb = sv + TM * NY;                 // [TM][NY]
-  __shared__ int s_pos[kTileSolve], s_iz[kTileSolve], s_u[kTileSolve];
-  __shared__ double s_kx[kTileSolve], s_kz[kTileSolve], s_ik[kTileSolve];
+  __shared__ int s_pos[TM], s_iz[TM], s_u[TM];
+  __shared__ double s_kx[TM], s_kz[TM], s_ik[TM];
   const int u0 = bx * TM;
   const int dir = by;
   if (threadIdx.x < TM) {
@@ -680,11 +681,10 @@ __device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const 
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreadsSolve) k_solve(const C2<T>* __restrict__ in3,
-                                                         const double2* __restrict__ du,
-                                                         double2* __restrict__ out, SolveArgs a) {
-  solve_body<T>(in3, du, out, a, blockIdx.x, blockIdx.y);
+template <typename T, int TM, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_solve(const C2<T>* __restrict__ in3, const double2* __restrict__ du,
+                                                   double2* __restrict__ out, SolveArgs a) {
+  solve_body<T, TM>(in3, du, out, a, blockIdx.x, blockIdx.y);
 }
 
 
@@ -1275,7 +1275,7 @@ struct GSolve {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kThreadsSolve) k_solve_grp(const double* __restrict__ du_base,
+__global__ void __launch_bounds__(kThreadsSolveGrp) k_solve_grp(const double* __restrict__ du_base,
                                                             double* __restrict__ out_base,
                                                             const GSolve* __restrict__ recs,
                                                             const int* __restrict__ inst,
@@ -1286,7 +1286,7 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve_grp(const double* __res
   __shared__ GSolve r;
   if (threadIdx.x == 0) r = recs[i];
   __syncthreads();
-  solve_body<T>(reinterpret_cast<const C2<T>*>(r.in3), reinterpret_cast<const double2*>(du_base + r.off),
+  solve_body<T, kTileSolve>(reinterpret_cast<const C2<T>*>(r.in3), reinterpret_cast<const double2*>(du_base + r.off),
                 reinterpret_cast<double2*>(out_base + r.off), r.a, blockIdx.x - first[i], 0);
 }
 
@@ -1439,47 +1439,12 @@ cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, voi
   }
 }
 
-static size_t solve_smem(const sp_ctx* c, int esize) {
-  const int TM = kTileSolve, NY = c->NY, NR = c->N - 1;
+static size_t solve_smem(const sp_ctx* c, int esize, int TM = kTileSolve) {
+  const int NY = c->NY, NR = c->N - 1;
   size_t vals = (size_t)3 * NY * TM * 2 * esize;
   vals = (vals + 15) / 16 * 16;
   size_t d = (size_t)16 * (3 * TM * NY + 3 * TM * NR + TM * 2 * c->cv + 2 * TM * NR + 2 * TM * NY);
   return vals + d + 16;
-}
-
-cudaError_t launch_solve(const sp_ctx* c, bool fp32, const void* in3, const double* du, double* out,
-                         int n_dir, cudaStream_t st) {
-  SolveArgs a;
-  a.ops = c->ops;
-  a.Cfh_d = c->Cfh;
-  a.Cfh_f = c->Cfh_f;
-  a.n_unique = c->n_unique; a.Mm = c->Mm; a.MX = c->MX; a.MZ = c->MZ; a.Kx = c->Kx;
-  a.NY = c->NY; a.N = c->N; a.NH = c->NH;
-  a.cv = c->cv; a.rb0 = c->rb0; a.rb1 = c->rb1;
-  a.off_v0 = c->off_v0; a.off_v1 = c->off_v1; a.off_h0 = c->off_h0; a.off_h1 = c->off_h1;
-  a.op_stride = c->op_stride;
-  a.alpha = c->alpha; a.beta = c->beta; a.inv_dt = 1.0 / c->dt;
-  dim3 grid((c->n_unique + kTileSolve - 1) / kTileSolve, n_dir);
-  if (fp32) {
-    size_t sm = solve_smem(c, 4);
-    cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_solve<float><<<grid, kThreadsSolve, sm, st>>>(reinterpret_cast<const C2<float>*>(in3),
-                                                    reinterpret_cast<const double2*>(du),
-                                                    reinterpret_cast<double2*>(out), a);
-  } else {
-    size_t sm = solve_smem(c, 8);
-    cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_solve<double><<<grid, kThreadsSolve, sm, st>>>(reinterpret_cast<const C2<double>*>(in3),
-                                                     reinterpret_cast<const double2*>(du),
-                                                     reinterpret_cast<double2*>(out), a);
-  }
-  return cudaGetLastError();
-}
-
-
-static size_t solve_adj_smem(const sp_ctx* c) {
-  const int TM = kTileSolve, NY = c->NY, NR = c->N - 1;
-  return (size_t)16 * (3 * TM * NY + 3 * TM * NY + TM * 2 * c->cv + 2 * TM * NR + 3 * TM * NR) + 16;
 }
 
 static SolveArgs solve_args(const sp_ctx* c) {
@@ -1495,6 +1460,73 @@ static SolveArgs solve_args(const sp_ctx* c) {
   a.alpha = c->alpha; a.beta = c->beta; a.inv_dt = 1.0 / c->dt;
   return a;
 }
+
+// tile shapes of k_solve: (modes per block, threads per block); the autotuner picks one.
+// threads = 0: one thread per solved row, TM * NY rounded up to a whole warp.
+struct SolveShape {
+  int tm, threads;
+};
+constexpr SolveShape kSolveShapes[SP_TUNE_MAX] = {{4, 128}, {2, 64}, {8, 256}, {4, 192},
+                                                  {16, 512}, {2, 0}, {4, 0}, {8, 0}};
+constexpr int kNumSolveShapes = 8;
+
+static int shape_threads(const sp_ctx* c, int shape) {
+  const SolveShape sh = kSolveShapes[shape];
+  return sh.threads > 0 ? sh.threads : (sh.tm * c->NY + 31) / 32 * 32;
+}
+
+template <typename T, int TM, int MAXT>
+static cudaError_t launch_solve_t(const sp_ctx* c, const SolveArgs& a, const void* in3, const double* du, double* out,
+                                  int n_dir, int threads, cudaStream_t st) {
+  const size_t sm = solve_smem(c, (int)sizeof(T), TM);
+  if (sm + 40 * TM + 64 > (size_t)232448 || threads > MAXT) return cudaErrorInvalidConfiguration;  // does not fit
+  cudaError_t e = cudaFuncSetAttribute(k_solve<T, TM, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((c->n_unique + TM - 1) / TM, n_dir);
+  k_solve<T, TM, MAXT><<<grid, threads, sm, st>>>(reinterpret_cast<const C2<T>*>(in3),
+                                                  reinterpret_cast<const double2*>(du),
+                                                  reinterpret_cast<double2*>(out), a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_solve_shape(const sp_ctx* c, int shape, const SolveArgs& a, const void* in3,
+                                      const double* du, double* out, int n_dir, cudaStream_t st) {
+  const int th = shape_threads(c, shape);
+  switch (shape) {
+    case 0: return launch_solve_t<T, 4, 128>(c, a, in3, du, out, n_dir, th, st);
+    case 1: return launch_solve_t<T, 2, 64>(c, a, in3, du, out, n_dir, th, st);
+    case 2: return launch_solve_t<T, 8, 256>(c, a, in3, du, out, n_dir, th, st);
+    case 3: return launch_solve_t<T, 4, 192>(c, a, in3, du, out, n_dir, th, st);
+    case 4: return launch_solve_t<T, 16, 512>(c, a, in3, du, out, n_dir, th, st);
+    case 5: return launch_solve_t<T, 2, 1024>(c, a, in3, du, out, n_dir, th, st);
+    case 6: return launch_solve_t<T, 4, 1024>(c, a, in3, du, out, n_dir, th, st);
+    case 7: return launch_solve_t<T, 8, 1024>(c, a, in3, du, out, n_dir, th, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int sp_solve_shapes(const sp_ctx* c, int* tm, int* threads) {
+  for (int i = 0; i < kNumSolveShapes; ++i) {
+    if (tm) tm[i] = kSolveShapes[i].tm;
+    if (threads) threads[i] = shape_threads(c, i);
+  }
+  return kNumSolveShapes;
+}
+
+cudaError_t launch_solve(const sp_ctx* c, bool fp32, const void* in3, const double* du, double* out,
+                         int n_dir, cudaStream_t st, int shape) {
+  const SolveArgs a = solve_args(c);
+  if (shape < 0) shape = c->solve_shape_tan;
+  if (fp32) return launch_solve_shape<float>(c, shape, a, in3, du, out, n_dir, st);
+  return launch_solve_shape<double>(c, shape, a, in3, du, out, n_dir, st);
+}
+
+static size_t solve_adj_smem(const sp_ctx* c) {
+  const int TM = kTileSolve, NY = c->NY, NR = c->N - 1;
+  return (size_t)16 * (3 * TM * NY + 3 * TM * NY + TM * 2 * c->cv + 2 * TM * NR + 3 * TM * NR) + 16;
+}
+
 
 cudaError_t launch_solve_adj(const sp_ctx* c, bool fp32, const double* r, double* out, void* vals3, int n_dir,
                              bool weighted, cudaStream_t st) {
@@ -1804,8 +1836,8 @@ cudaError_t grp_launch_solve(const GrpPlan& p, bool fp32, const double* du_base,
   if (k.blocks == 0) return cudaSuccess;
   const GSolve* r = static_cast<const GSolve*>(k.recs);
   if (fp32)
-    k_solve_grp<float><<<k.blocks, kThreadsSolve, k.smem, st>>>(du_base, out_base, r, k.inst, k.first, active);
+    k_solve_grp<float><<<k.blocks, kThreadsSolveGrp, k.smem, st>>>(du_base, out_base, r, k.inst, k.first, active);
   else
-    k_solve_grp<double><<<k.blocks, kThreadsSolve, k.smem, st>>>(du_base, out_base, r, k.inst, k.first, active);
+    k_solve_grp<double><<<k.blocks, kThreadsSolveGrp, k.smem, st>>>(du_base, out_base, r, k.inst, k.first, active);
   return cudaGetLastError();
 }

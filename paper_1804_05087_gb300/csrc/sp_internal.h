@@ -97,6 +97,8 @@ struct sp_ctx {
   int red_blocks = 0;
   int has_base = 0;
   int use_xz_reg = 1;            // float plane stage: register FFT kernel when the size allows
+  int solve_shape_tan = 0;       // k_solve tile shape of the tangent (sp_autotune)
+  int solve_shape_step = 0;      // k_solve tile shape of the FP64 step
   // sizes of shared memory per kernel (bytes)
   size_t smem_xz64 = 0, smem_xz32 = 0;
   int xz_rp64 = 1, xz_rp32 = 1;
@@ -187,8 +189,11 @@ cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, voi
 // float plane stage with register-resident FFTs (xz_reg.cu), square grids 16..64
 bool sp_xz_reg_supported(const sp_ctx* c);
 cudaError_t launch_xz_reg(const sp_ctx* c, int mode, const void* in, void* out, int n_dir, cudaStream_t st);
+// shape: index into the tile-shape table (sp_solve_shapes); -1 = the context's tangent choice
 cudaError_t launch_solve(const sp_ctx* c, bool fp32, const void* in3, const double* du,
-                         double* out, int n_dir, cudaStream_t st);
+                         double* out, int n_dir, cudaStream_t st, int shape = -1);
+// the tile shapes of k_solve (modes per block, threads per block); returns their number
+int sp_solve_shapes(const sp_ctx* c, int* tm, int* threads);
 cudaError_t launch_base_to_f32(const sp_ctx* c, cudaStream_t st);
 // adjoint chain (sp_vjp): solve^T + Chebyshev^T, plane stage^T (launch_xz with
 // XZ_ADJOINT), values^T + curl^T, then weights and the Hermitian projection
