@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--krylov", type=int, default=300)
     p.add_argument("--config2", action="store_true",
                    help="64 plane Couette instances (Re ~ U[200,1000], four grids) in lock-step group Newton")
+    p.add_argument("--config3", action="store_true",
+                   help="pipe flow, Re 2500, Nr 64, m<=24, |k|<=24: tangent throughput and traveling-wave Newton")
     p.add_argument("--config4", action="store_true",
                    help="96x97x96, Re 1000, doubled box: adjoint gradient check and Newton-hookstep with J^T F")
     return p.parse_args()
@@ -382,6 +384,63 @@ def run_config2(args):
     print(json.dumps(out))
 
 
+def run_config3(args):
+    """Pipe flow in the frame moving with the wave (config 3): Re 2500, alpha 1.25, 2-fold
+    symmetry, Nr 64, m' <= 12 (m <= 24), |kz| <= 24, 48 x 96 physical grid, dt 50.
+    (1) tangent throughput (set_base + 64 directions) in mixed and FP64 precision;
+    (2) Newton-GMRES-hookstep from Hagen-Poiseuille plus seeded streaks (amplitude 0.05 and a
+    10 % divergence-free k != 0 part, c0 = 0.5) with the speed as an unknown."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1804_05087_gb300 as sp
+    import seeded_inputs as si
+    nd = 64
+    out = {"metric": "config 3: pipe traveling-wave tangent throughput and Newton", "unit": "JVP/s",
+           "config": {"workload": "pipe Re=2500, alpha=1.25, sym 2, Nr=64, m'<=12, |kz|<=24, 48x96, dt=50",
+                      "directions": nd}, "throughput": {}}
+    for name, prec in (("mixed", sp.SP_MIXED), ("fp64", sp.SP_FP64)):
+        ctx = sp.Context(sp.PipeConfig(prec=prec, max_batch=nd))
+        def seeded(seed, amp, frac, c0):
+            st, pol = si.pipe_random_coeffs(seed, ctx.cfg.kz, ctx.cfg.mt)
+            U = ctx.zeros()
+            return ctx.sp_pipe_seed_state(st, pol, amp, frac, c0, U)
+        U = seeded(4000, 0.05, 0.1, 0.5)
+        D = ctx.zeros(nd)
+        for i in range(nd):
+            D[i].copy_(seeded(4100 + i, 1.0, 1.0, 0.1))
+        J = ctx.zeros(nd)
+        for _ in range(3):
+            ctx.sp_set_base(U)
+            ctx.sp_jvp(D, J)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            ctx.sp_set_base(U)
+            ctx.sp_jvp(D, J)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out["throughput"][name] = {"ms_per_step": ms, "jvp_per_s": nd / (ms * 1e-3)}
+        if prec == sp.SP_MIXED:
+            U0 = U.clone()
+            G = ctx.zeros()
+            ctx.sp_step(U0, G)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = ctx.sp_newton_gmres(U, max_newton=20, max_krylov=args.krylov, tol=1e-10, eta=1e-3)
+            torch.cuda.synchronize()
+            rep["wall_s"] = time.perf_counter() - t0
+            u, c = ctx.pipe_split(U)
+            rep["speed_c"] = c
+            rep["deviation_norm"] = float(torch.linalg.vector_norm(u))
+            out["newton"] = rep
+        ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -390,6 +449,8 @@ def main():
         return run_newton(args)
     if args.config2:
         return run_config2(args)
+    if args.config3:
+        return run_config3(args)
     if args.config4:
         return run_config4(args)
     import torch

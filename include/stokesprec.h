@@ -175,6 +175,26 @@ sp_status sp_vjp_euclid(sp_ctx* ctx, const double* g, double* JTg, int n_dir, vo
  * Needs sp_set_base. Synchronous (reads the norms on the host). */
 sp_status sp_jvp_fd(sp_ctx* ctx, const double* du, double* Jdu, int n_dir, void* stream);
 
+/* ---- the multi-step operator G^int (Eq. Gint) ----------------------------
+ *
+ * G^int_T = (B_dt)^n - I with T = n dt: n BEFE steps of the context's dt, the
+ * time-integration operator the paper compares Stokes preconditioning with
+ * (Sec. 2, Sec. 3.3). n > 1 needs a plane Couette context; n = 1 is the
+ * single step of any context. */
+
+/* G = B^n(U) - U, FP64. U and G: one state each (may not alias). */
+sp_status sp_step_n(sp_ctx* ctx, const double* U, double* G, int n, void* stream);
+/* Linearisation point of G^int: stores the trajectory U_k = B^k(U), k < n (n
+ * states of device memory held by the context), U, and G^int(U) for
+ * sp_jvp_fd. n = 1 is sp_set_base. Calling sp_set_base afterwards returns to
+ * the single step. */
+sp_status sp_set_base_n(sp_ctx* ctx, const double* U, int n, void* stream);
+/* Jdu = G^int_U du = (prod_k (I + G_{U_k})) du - du for n_dir directions: the
+ * chain rule along the stored trajectory, one tangent step (as sp_jvp, in
+ * cfg.prec) per k, the total fields of U_k recomputed from the stored state.
+ * After sp_set_base_n; sp_jvp_fd then differentiates G^int as well. */
+sp_status sp_jvp_n(sp_ctx* ctx, const double* du, double* Jdu, int n_dir, void* stream);
+
 /* ---- tangent step without allocation ------------------------------------ */
 
 /* Jdu = G_U du for ONE direction, exactly as sp_jvp computes it, but with the
@@ -259,6 +279,9 @@ typedef struct {
                          sp_vjp and one more action) to the Krylov space of the
                          hookstep, so the trust-region step also spans the
                          Cauchy (dogleg) direction                             */
+  int int_steps;      /* <= 1: G = G^Stokes = B_dt - I (one step, Eq. Gstokes);
+                         n > 1: G = G^int = (B_dt)^n - I (n steps of cfg.dt,
+                         Eq. Gint; plane Couette, use_gradient = 0)            */
 } sp_newton_opts;
 
 typedef struct {
@@ -327,7 +350,7 @@ sp_status sp_group_inner(sp_group* g, const double* a, const double* b, double* 
  * launches, and all hookstep trials of one round are one step of the group.
  * Each member has its own Krylov basis, trust radius and stopping tests, and
  * leaves the iteration when |G| < tol (or it fails). use_fd and use_gradient
- * must be 0. use_graphs = 1 captures the launches of each Arnoldi step j once as
+ * must be 0 and int_steps <= 1. use_graphs = 1 captures the launches of each Arnoldi step j once as
  * a CUDA graph and replays it (graphs are kept with the group and rebuilt if
  * max_krylov grows). reports: n entries (or NULL); t_action_ms, t_orth_ms and
  * t_total_ms are the group's totals. Synchronous. Returns SP_OK when every

@@ -47,7 +47,7 @@ class _PipeConfig(ctypes.Structure):
 class _NewtonOpts(ctypes.Structure):
     _fields_ = [("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int), ("tol", ctypes.c_double),
                 ("eta", ctypes.c_double), ("delta0", ctypes.c_double), ("use_fd", ctypes.c_int),
-                ("use_gradient", ctypes.c_int)]
+                ("use_gradient", ctypes.c_int), ("int_steps", ctypes.c_int)]
 
 
 class _TuneReport(ctypes.Structure):
@@ -88,6 +88,9 @@ def _load():
         "sp_trace_enable": ([P, I], I),
         "sp_trace_read": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), I], I),
         "sp_autotune": ([P, I, ctypes.POINTER(_TuneReport), V], I),
+        "sp_step_n": ([P, P, P, I, V], I),
+        "sp_set_base_n": ([P, P, I, V], I),
+        "sp_jvp_n": ([P, P, P, I, V], I),
         "sp_set_solve_shape": ([P, I, I], I),
         "sp_group_create": ([ctypes.POINTER(_Config), I, ctypes.POINTER(ctypes.c_void_p)], I),
         "sp_group_destroy": ([P], I),
@@ -118,7 +121,7 @@ EXPORTS = ("sp_create", "sp_destroy", "sp_last_error", "sp_state_len", "sp_dims"
            "sp_pipe_seed_state", "sp_group_create", "sp_group_destroy", "sp_group_last_error", "sp_group_size",
            "sp_group_state_len", "sp_group_offset", "sp_group_member", "sp_group_step", "sp_group_set_base",
            "sp_group_jvp", "sp_group_inner", "sp_group_newton_gmres", "sp_autotune",
-           "sp_set_solve_shape")
+           "sp_set_solve_shape", "sp_step_n", "sp_set_base_n", "sp_jvp_n")
 STAGES = ("k_yinv", "k_xz", "k_solve", "step", "vector")
 
 
@@ -273,6 +276,23 @@ class Context:
         self._check(_lib.sp_jvp(self._h, pd, po, n, _stream(stream)))
         return out
 
+    def sp_step_n(self, U, G, n, stream=None):
+        """G = B^n(U) - U: n steps of the context's dt (Eq. Gint)."""
+        pu, _ = self._ptr(U, 1)
+        pg, _ = self._ptr(G, 1)
+        self._check(_lib.sp_step_n(self._h, pu, pg, int(n), _stream(stream)))
+        return G
+
+    def sp_set_base_n(self, U, n, stream=None):
+        pu, _ = self._ptr(U, 1)
+        self._check(_lib.sp_set_base_n(self._h, pu, int(n), _stream(stream)))
+
+    def sp_jvp_n(self, du, out, stream=None):
+        pd, n = self._ptr(du)
+        po, _ = self._ptr(out, n)
+        self._check(_lib.sp_jvp_n(self._h, pd, po, n, _stream(stream)))
+        return out
+
     def sp_jvp_static(self, du, out, stream=None):
         """One tangent action that allocates nothing (see include/stokesprec.h)."""
         pd, _ = self._ptr(du, 1)
@@ -330,9 +350,9 @@ class Context:
         return {STAGES[i]: (ms[i], cnt[i]) for i in range(n)}
 
     def sp_newton_gmres(self, U, max_newton=20, max_krylov=30, tol=1e-10, eta=1e-3, delta0=0.0,
-                        use_fd=False, use_gradient=False, stream=None):
+                        use_fd=False, use_gradient=False, int_steps=1, stream=None):
         pu, _ = self._ptr(U, 1)
-        o = _opts(max_newton, max_krylov, tol, eta, delta0, use_fd, use_gradient)
+        o = _opts(max_newton, max_krylov, tol, eta, delta0, use_fd, use_gradient, int_steps)
         r = _NewtonReport()
         st = _lib.sp_newton_gmres(self._h, pu, ctypes.byref(o), ctypes.byref(r), _stream(stream))
         rep = {k: getattr(r, k) for k, _ in _NewtonReport._fields_}
@@ -342,8 +362,9 @@ class Context:
         return rep
 
 
-def _opts(max_newton, max_krylov, tol, eta, delta0, use_fd, use_gradient):
-    return _NewtonOpts(max_newton, max_krylov, tol, eta, delta0, 1 if use_fd else 0, 1 if use_gradient else 0)
+def _opts(max_newton, max_krylov, tol, eta, delta0, use_fd, use_gradient, int_steps=1):
+    return _NewtonOpts(max_newton, max_krylov, tol, eta, delta0, 1 if use_fd else 0, 1 if use_gradient else 0,
+                       int(int_steps))
 
 
 class Group:

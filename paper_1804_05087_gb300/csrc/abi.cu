@@ -87,7 +87,8 @@ static bool good_fft_len(int n) {
 static void free_ctx(sp_ctx* c) {
   void* ptrs[] = {c->Th, c->TDh, c->Cfh, c->yv, c->lam6, c->Th_f, c->TDh_f, c->Cfh_f, c->twx, c->twz, c->base32t,
                   c->twx_f, c->twz_f, c->ops, c->ws6, c->ws3, c->base64, c->base32, c->U0,
-                  c->G0, c->tmp, c->red, c->kry, c->wsG, c->pops, c->fd_w1, c->fd_c1, c->dzU};
+                  c->G0, c->tmp, c->red, c->kry, c->wsG, c->pops, c->fd_w1, c->fd_c1, c->dzU,
+                  c->traj, c->nbuf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -313,6 +314,7 @@ extern "C" sp_status sp_set_base(sp_ctx* c, const double* U, void* stream) {
   if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_base_to_f32(c, st); }), "base f32")) != SP_OK) return s;
   if ((s = step_batch(c, c->U0, c->G0, 1, st)) != SP_OK) return s;
   c->has_base = 1;
+  c->traj_n = 1;
   return SP_OK;
 }
 
@@ -408,9 +410,118 @@ extern "C" sp_status sp_inner(sp_ctx* c, const double* a, const double* b, int n
   return SP_OK;
 }
 
+// ---------------------------------------------------------------- multi-step map
+// G^int = B^n - I (Eq. Gint): n BEFE steps of the context's dt. The tangent is the
+// chain rule along the trajectory U_k = B^k(U): d_{k+1} = d_k + G_{U_k} d_k, so
+// G^int_U du = d_n - d_0. The trajectory states are stored by sp_set_base_n; the
+// total fields of each U_k are recomputed from them at every tangent step.
+static sp_status ensure_buf(sp_ctx* c, double** buf, int* cap, int n, const char* what) {
+  if (*cap >= n) return SP_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  if (cudaMalloc((void**)buf, (size_t)n * c->state_len * 8) != cudaSuccess) {
+    cudaGetLastError();
+    return sp_fail(c, SP_ENOMEM, what);
+  }
+  *cap = n;
+  return SP_OK;
+}
+
+static sp_status step_n(sp_ctx* c, const double* U, double* G, int n, cudaStream_t st) {
+  if (n == 1) return step_batch(c, U, G, 1, st);
+  int cap = c->nbuf ? 2 : 0;
+  sp_status s = ensure_buf(c, &c->nbuf, &cap, 2, "multi-step scratch");
+  if (s != SP_OK) return s;
+  double* X = c->nbuf;
+  double* D = c->nbuf + c->state_len;
+  const size_t L = c->state_len;
+  if ((s = sp_cuda(c, cudaMemcpyAsync(X, U, L * 8, cudaMemcpyDeviceToDevice, st), "copy")) != SP_OK) return s;
+  for (int k = 0; k < n; ++k) {
+    if ((s = step_batch(c, X, D, 1, st)) != SP_OK) return s;
+    if ((s = sp_cuda(c, launch_axpby(X, 1.0, X, 1.0, D, L, st), "axpby")) != SP_OK) return s;
+  }
+  return sp_cuda(c, launch_axpby(G, 1.0, X, -1.0, U, L, st), "axpby");
+}
+
+// total fields of state X on the grid (FP64 and the float copies)
+static sp_status base_fields(sp_ctx* c, const double* X, cudaStream_t st) {
+  sp_status s;
+  if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_yinv(c, false, X, c->ws6, 1, st); }), "yinv")) != SP_OK)
+    return s;
+  if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_xz(c, false, XZ_BASE, c->ws6, nullptr, 1, st); }),
+                   "xz base")) != SP_OK)
+    return s;
+  return sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_base_to_f32(c, st); }), "base f32");
+}
+
+extern "C" sp_status sp_step_n(sp_ctx* c, const double* U, double* G, int n, void* stream) {
+  if (!c || !U || !G || U == G || n < 1) return sp_fail(c, SP_EINVAL, "sp_step_n: bad arguments");
+  if (n > 1 && c->geom != 0) return sp_fail(c, SP_EINVAL, "sp_step_n: n > 1 needs a plane Couette context");
+  return step_n(c, U, G, n, (cudaStream_t)stream);
+}
+
+extern "C" sp_status sp_set_base_n(sp_ctx* c, const double* U, int n, void* stream) {
+  if (!c || !U || n < 1) return sp_fail(c, SP_EINVAL, "sp_set_base_n: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  sp_status s;
+  if (n == 1) return sp_set_base(c, U, stream);  // any geometry
+  if (c->geom != 0) return sp_fail(c, SP_EINVAL, "sp_set_base_n: n > 1 needs a plane Couette context");
+  if ((s = ensure_buf(c, &c->traj, &c->traj_cap, n, "trajectory allocation")) != SP_OK) return s;
+  const size_t L = c->state_len;
+  if ((s = sp_cuda(c, cudaMemcpyAsync(c->traj, U, L * 8, cudaMemcpyDeviceToDevice, st), "copy")) != SP_OK) return s;
+  if ((s = sp_cuda(c, cudaMemcpyAsync(c->U0, U, L * 8, cudaMemcpyDeviceToDevice, st), "copy")) != SP_OK) return s;
+  double* D = c->G0;  // step increments, then G^int(U) for the finite-difference action
+  for (int k = 0; k + 1 < n; ++k) {
+    const double* Xk = c->traj + (size_t)k * L;
+    if ((s = step_batch(c, Xk, D, 1, st)) != SP_OK) return s;
+    if ((s = sp_cuda(c, launch_axpby(c->traj + (size_t)(k + 1) * L, 1.0, Xk, 1.0, D, L, st), "axpby")) != SP_OK)
+      return s;
+  }
+  const double* Xl = c->traj + (size_t)(n - 1) * L;
+  if ((s = step_batch(c, Xl, D, 1, st)) != SP_OK) return s;  // D = U_n - U_{n-1}
+  // G0 = U_n - U_0 = (U_{n-1} - U_0) + D
+  if ((s = sp_cuda(c, launch_axpby(D, 1.0, D, 1.0, Xl, L, st), "axpby")) != SP_OK) return s;
+  if ((s = sp_cuda(c, launch_axpby(D, 1.0, D, -1.0, U, L, st), "axpby")) != SP_OK) return s;
+  c->traj_n = n;
+  c->has_base = 0;  // the single-step base fields are overwritten along the trajectory
+  return SP_OK;
+}
+
+extern "C" sp_status sp_jvp_n(sp_ctx* c, const double* du, double* Jdu, int n_dir, void* stream) {
+  if (!c || !du || !Jdu || n_dir < 0 || du == Jdu) return sp_fail(c, SP_EINVAL, "sp_jvp_n: bad arguments");
+  if (c->traj_n < 1) return sp_fail(c, SP_EINVAL, "sp_jvp_n: call sp_set_base_n first");
+  if (c->traj_n == 1) return sp_jvp(c, du, Jdu, n_dir, stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f32 = c->cfg.prec == SP_MIXED;
+  const size_t L = c->state_len;
+  sp_status s;
+  for (int d0 = 0; d0 < n_dir; d0 += c->cfg.max_batch) {
+    const int nb = std::min(c->cfg.max_batch, n_dir - d0);
+    const double* u = du + (size_t)d0 * L;
+    double* g = Jdu + (size_t)d0 * L;  // holds d_k
+    if ((s = sp_cuda(c, cudaMemcpyAsync(g, u, (size_t)nb * L * 8, cudaMemcpyDeviceToDevice, st), "copy")) != SP_OK)
+      return s;
+    for (int k = 0; k < c->traj_n; ++k) {
+      if ((s = base_fields(c, c->traj + (size_t)k * L, st)) != SP_OK) return s;
+      if ((s = sp_cuda(c, traced(c, SP_STAGE_YINV, st, [&] { return launch_yinv(c, f32, g, c->ws6, nb, st); }), "yinv")) != SP_OK)
+        return s;
+      if ((s = sp_cuda(c, traced(c, SP_STAGE_XZ, st, [&] { return launch_xz(c, f32, XZ_TANGENT, c->ws6, c->ws3, nb, st); }),
+                       "xz tangent")) != SP_OK)
+        return s;
+      if ((s = sp_cuda(c, traced(c, SP_STAGE_SOLVE, st, [&] { return launch_solve(c, f32, c->ws3, g, c->tmp, nb, st); }),
+                       "solve")) != SP_OK)
+        return s;
+      if ((s = sp_cuda(c, launch_axpby(g, 1.0, g, 1.0, c->tmp, (size_t)nb * L, st), "axpby")) != SP_OK) return s;
+    }
+    if ((s = sp_cuda(c, launch_axpby(g, 1.0, g, -1.0, u, (size_t)nb * L, st), "axpby")) != SP_OK) return s;
+  }
+  return SP_OK;
+}
+
 extern "C" sp_status sp_jvp_fd(sp_ctx* c, const double* du, double* Jdu, int n_dir, void* stream) {
   if (!c || !du || !Jdu || n_dir < 0 || du == Jdu) return sp_fail(c, SP_EINVAL, "sp_jvp_fd: bad arguments");
-  if (!c->has_base) return sp_fail(c, SP_EINVAL, "sp_jvp_fd: call sp_set_base first");
+  if (!c->has_base && c->traj_n < 2) return sp_fail(c, SP_EINVAL, "sp_jvp_fd: call sp_set_base first");
   cudaStream_t st = (cudaStream_t)stream;
   double nU;
   sp_status s = inner_many(c, c->U0, 1, c->U0, &nU, st);
@@ -428,7 +539,7 @@ extern "C" sp_status sp_jvp_fd(sp_ctx* c, const double* du, double* Jdu, int n_d
     }
     const double eps = 1e-7 * (1.0 + nU) / nd;
     if ((s = sp_cuda(c, launch_axpby(c->tmp, 1.0, c->U0, eps, u, c->state_len, st), "axpby")) != SP_OK) return s;
-    if ((s = step_batch(c, c->tmp, g, 1, st)) != SP_OK) return s;
+    if ((s = step_n(c, c->tmp, g, c->traj_n > 1 ? c->traj_n : 1, st)) != SP_OK) return s;
     if ((s = sp_cuda(c, launch_axpby(g, 1.0 / eps, g, -1.0 / eps, c->G0, c->state_len, st), "axpby")) != SP_OK)
       return s;
     if (c->geom == 1 && (s = pipe_phase(c, u, g, 1, st)) != SP_OK) return s;
@@ -491,6 +602,9 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   if (!c || !U || !o) return sp_fail(c, SP_EINVAL, "sp_newton_gmres: bad arguments");
   if (o->use_gradient && c->geom != 0)
     return sp_fail(c, SP_EINVAL, "sp_newton_gmres: use_gradient needs the adjoint (plane Couette only)");
+  const int ns = o->int_steps > 1 ? o->int_steps : 1;  // 1: G^Stokes; > 1: G^int = B^ns - I
+  if (ns > 1 && (c->geom != 0 || o->use_gradient))
+    return sp_fail(c, SP_EINVAL, "sp_newton_gmres: int_steps > 1 needs a plane Couette context, no use_gradient");
   const int K = o->max_krylov;
   if (K < 1 || K > 4096 || o->max_newton < 0) return sp_fail(c, SP_EINVAL, "sp_newton_gmres: bad options");
   cudaStream_t st = (cudaStream_t)stream;
@@ -524,8 +638,8 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   const double t0 = now_ms();
   sp_status s;
   auto norm = [&](const double* x, double* out) { return inner_many(c, x, 1, x, out, st); };
-  if ((s = step_batch(c, U, F, 1, st)) != SP_OK) return s;
-  r.total_steps++;
+  if ((s = step_n(c, U, F, ns, st)) != SP_OK) return s;
+  r.total_steps += ns;
   double nF;
   if ((s = norm(F, &nF)) != SP_OK) return s;
   nF = std::sqrt(nF);
@@ -541,8 +655,8 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     if (!std::isfinite(nF)) { result = SP_ENAN; break; }
     if (nF < o->tol) { result = SP_OK; break; }
     if (it == o->max_newton) break;
-    if ((s = sp_set_base(c, U, st)) != SP_OK) return s;
-    r.total_steps++;
+    if ((s = sp_set_base_n(c, U, ns, st)) != SP_OK) return s;
+    r.total_steps += ns;
     // GMRES without restarts; classical Gram-Schmidt applied twice, all reductions on the device
     if ((s = sp_cuda(c, launch_axpby(V, 1.0 / nF, F, 0.0, nullptr, L, st), "v0")) != SP_OK) return s;
     std::fill(g.begin(), g.end(), 0.0);
@@ -580,7 +694,7 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
       double* w = V + (size_t)(j + 1) * L;
       double ta = now_ms();
       if (o->use_fd) s = sp_jvp_fd(c, vj, w, 1, st);
-      else s = sp_jvp(c, vj, w, 1, st);
+      else s = ns > 1 ? sp_jvp_n(c, vj, w, 1, st) : sp_jvp(c, vj, w, 1, st);
       if (s != SP_OK) return s;
       if (r.t_action_ms >= 0) {
         if ((s = sp_cuda(c, cudaStreamSynchronize(st), "jvp sync")) != SP_OK) return s;
@@ -640,8 +754,8 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
       if ((s = sp_cuda(c, launch_multi_axpy(c, V, kv, dhn + 2, Ut, st), "update")) != SP_OK) return s;
       if (grad_col)
         if ((s = sp_cuda(c, launch_multi_axpy(c, Zg, 1, dhn + 2 + kv, Ut, st), "update")) != SP_OK) return s;
-      if ((s = step_batch(c, Ut, F, 1, st)) != SP_OK) return s;
-      r.total_steps++;
+      if ((s = step_n(c, Ut, F, ns, st)) != SP_OK) return s;
+      r.total_steps += ns;
       if ((s = norm(F, &nT)) != SP_OK) return s;
       nT = std::sqrt(nT);
       if (!trust_update(nF, pred, nT, ylen, &delta)) continue;
@@ -649,7 +763,7 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
       break;
     }
     if (!accepted) {
-      if ((s = step_batch(c, U, F, 1, st)) != SP_OK) return s;
+      if ((s = step_n(c, U, F, ns, st)) != SP_OK) return s;
       break;
     }
     if ((s = sp_cuda(c, cudaMemcpyAsync(U, Ut, L * 8, cudaMemcpyDeviceToDevice, st), "accept")) != SP_OK) return s;

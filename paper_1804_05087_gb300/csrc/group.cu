@@ -27,8 +27,10 @@ struct GVec {
   size_t off;    // doubles
   size_t ncplx;  // complex values of the state
   int NY, MZ;    // for the weights w(iz) of the inner product
-  int nb;        // blocks of the vector launches
+  int nb;        // blocks of the reduction launches (dots, norms)
   int first;     // first of those blocks
+  int nb_el;     // blocks of the elementwise launches (axpy, scale)
+  int first_el;
 };
 
 __device__ __forceinline__ double blk_sum(double v) {
@@ -136,11 +138,11 @@ __global__ void __launch_bounds__(kVecThreads) k_gaxpy(const double* __restrict_
   const int i = inst[blockIdx.x];
   if (active && !active[i]) return;
   const GVec r = recs[i];
-  const int b = blockIdx.x - r.first;
+  const int b = blockIdx.x - r.first_el;
   const size_t len = 2 * r.ncplx;
   double* wi = w + r.off;
   const double* Vi = V + r.off;
-  for (size_t e = (size_t)b * blockDim.x + threadIdx.x; e < len; e += (size_t)r.nb * blockDim.x) {
+  for (size_t e = (size_t)b * blockDim.x + threadIdx.x; e < len; e += (size_t)r.nb_el * blockDim.x) {
     double acc[8] = {wi[e], 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     int q = 0;
     for (; q + 8 <= k; q += 8) {
@@ -159,10 +161,10 @@ __global__ void __launch_bounds__(kVecThreads) k_gscale(double* __restrict__ dst
   const int i = inst[blockIdx.x];
   if (mask && !mask[i]) return;
   const GVec r = recs[i];
-  const int b = blockIdx.x - r.first;
+  const int b = blockIdx.x - r.first_el;
   const size_t len = 2 * r.ncplx;
   const double f = s ? s[i] : 1.0;
-  for (size_t e = (size_t)b * blockDim.x + threadIdx.x; e < len; e += (size_t)r.nb * blockDim.x)
+  for (size_t e = (size_t)b * blockDim.x + threadIdx.x; e < len; e += (size_t)r.nb_el * blockDim.x)
     dst[r.off + e] = f * src[r.off + e];
 }
 
@@ -184,8 +186,10 @@ struct sp_group {
   GrpPlan plan;
   // vector launches
   GVec* vrecs = nullptr;
-  int* vinst = nullptr;
+  int* vinst = nullptr;     // block -> member, reduction launches
   int vblocks = 0;
+  int* einst = nullptr;     // block -> member, elementwise launches
+  int eblocks = 0;
   std::vector<GVec> vrecs_h;
   // scratch: masks, per-member scalars, partial sums
   int* act = nullptr;       // device [n]
@@ -225,7 +229,7 @@ static void drop_graphs(sp_group* g) {
 static void free_group(sp_group* g) {
   drop_graphs(g);
   grp_plan_free(&g->plan);
-  for (void* p : {(void*)g->vrecs, (void*)g->vinst, (void*)g->act, (void*)g->scal, (void*)g->part, (void*)g->tmpv,
+  for (void* p : {(void*)g->vrecs, (void*)g->vinst, (void*)g->einst, (void*)g->act, (void*)g->scal, (void*)g->part, (void*)g->tmpv,
                   (void*)g->kry})
     if (p) cudaFree(p);
   if (g->act_h) cudaFreeHost(g->act_h);
@@ -275,9 +279,10 @@ extern "C" sp_status sp_group_create(const sp_config* cfgs, int n, sp_group** ou
                    [&](int a, int b) { return g->mem[a]->state_len > g->mem[b]->state_len; });
   cudaError_t e = grp_plan_build(&g->plan, g->mem.data(), n, g->off.data(), g->order.data());
   if (e != cudaSuccess) return bail(SP_ECUDA, std::string("grouped launch tables: ") + cudaGetErrorString(e));
-  // vector launches: about 4096 complex values per block (16 per thread)
+  // reduction launches: 2048-4096 complex values per block; elementwise launches: two
+  // doubles per thread
   g->vrecs_h.resize(n);
-  std::vector<int> vinst;
+  std::vector<int> vinst, einst;
   for (int q = 0; q < n; ++q) {
     const int i = g->order[q];
     const sp_ctx* c = g->mem[i];
@@ -286,13 +291,19 @@ extern "C" sp_status sp_group_create(const sp_config* cfgs, int n, sp_group** ou
     r.ncplx = c->cplx_per_state;
     r.NY = c->NY;
     r.MZ = c->MZ;
-    r.nb = (int)std::max<size_t>(1, (r.ncplx + 4095) / 4096);
+    const size_t per = r.ncplx > 65536 ? 4096 : 2048;  // small states: more blocks for parallelism
+    r.nb = (int)std::max<size_t>(1, (r.ncplx + per - 1) / per);
     r.first = (int)vinst.size();
     for (int b = 0; b < r.nb; ++b) vinst.push_back(i);
+    r.nb_el = (int)std::max<size_t>(1, (2 * r.ncplx + 511) / 512);  // two doubles per thread
+    r.first_el = (int)einst.size();
+    for (int b = 0; b < r.nb_el; ++b) einst.push_back(i);
   }
   g->vblocks = (int)vinst.size();
+  g->eblocks = (int)einst.size();
   if ((e = grp_upload((void**)&g->vrecs, g->vrecs_h.data(), n * sizeof(GVec))) != cudaSuccess ||
-      (e = grp_upload((void**)&g->vinst, vinst.data(), vinst.size() * sizeof(int))) != cudaSuccess)
+      (e = grp_upload((void**)&g->vinst, vinst.data(), vinst.size() * sizeof(int))) != cudaSuccess ||
+      (e = grp_upload((void**)&g->einst, einst.data(), einst.size() * sizeof(int))) != cudaSuccess)
     return bail(SP_ECUDA, std::string("vector tables: ") + cudaGetErrorString(e));
   bool ok = cudaMalloc((void**)&g->act, n * sizeof(int)) == cudaSuccess &&
             cudaMallocHost((void**)&g->act_h, n * sizeof(int)) == cudaSuccess &&
@@ -404,13 +415,13 @@ static cudaError_t launch_gnorm(const sp_group* g, const double* w, const int* a
 static cudaError_t launch_gaxpy(const sp_group* g, const double* V, int k, const double* h, double* w, const int* act,
                                 cudaStream_t st) {
   if (k <= 0) return cudaSuccess;
-  k_gaxpy<<<g->vblocks, kVecThreads, 0, st>>>(V, g->len, k, h, g->n, w, g->vrecs, g->vinst, act);
+  k_gaxpy<<<g->eblocks, kVecThreads, 0, st>>>(V, g->len, k, h, g->n, w, g->vrecs, g->einst, act);
   return cudaGetLastError();
 }
 
 static cudaError_t launch_gscale(const sp_group* g, double* dst, const double* src, const double* s, const int* mask,
                                  cudaStream_t st) {
-  k_gscale<<<g->vblocks, kVecThreads, 0, st>>>(dst, src, s, g->vrecs, g->vinst, mask);
+  k_gscale<<<g->eblocks, kVecThreads, 0, st>>>(dst, src, s, g->vrecs, g->einst, mask);
   return cudaGetLastError();
 }
 
@@ -549,8 +560,9 @@ static sp_status group_arnoldi(sp_group* g, const GNewtonMem& m, int j, bool cap
 extern "C" sp_status sp_group_newton_gmres(sp_group* g, double* U, const sp_newton_opts* o, int use_graphs,
                                            sp_newton_report* reps, void* stream) {
   if (!g || !U || !o) return gfail(g, SP_EINVAL, "sp_group_newton_gmres: bad arguments");
-  if (o->use_fd || o->use_gradient)
-    return gfail(g, SP_EINVAL, "sp_group_newton_gmres: tangent actions only (use_fd = use_gradient = 0)");
+  if (o->use_fd || o->use_gradient || o->int_steps > 1)
+    return gfail(g, SP_EINVAL, "sp_group_newton_gmres: single-step tangent actions only "
+                               "(use_fd = use_gradient = 0, int_steps <= 1)");
   const int K = o->max_krylov;
   if (K < 1 || K > 4096 || o->max_newton < 0) return gfail(g, SP_EINVAL, "sp_group_newton_gmres: bad options");
   const int n = g->n;

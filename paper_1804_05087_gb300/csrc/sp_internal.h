@@ -113,6 +113,11 @@ struct sp_ctx {
   // Newton scratch
   double* kry = nullptr;         // Krylov basis [max_krylov+1] states
   int kry_cap = 0;
+  // multi-step map B^n (sp_step_n / sp_set_base_n / sp_jvp_n)
+  double* traj = nullptr;        // [traj_cap] states: U_0 .. U_{n-1} of the last sp_set_base_n
+  int traj_cap = 0;
+  int traj_n = 0;                // steps of the stored trajectory (0: none)
+  double* nbuf = nullptr;        // [2] states: scratch of sp_step_n
 };
 
 // run `launch` (returning cudaError_t) bracketed by trace events when tracing
