@@ -51,6 +51,10 @@ def parse():
     p.add_argument("--krylov", type=int, default=300)
     p.add_argument("--config2", action="store_true",
                    help="64 plane Couette instances (Re ~ U[200,1000], four grids) in lock-step group Newton")
+    p.add_argument("--gint", action="store_true",
+                   help="Newton with G^Stokes_T (one step of size T) vs G^int_T (T/dt steps of dt = 1/32)")
+    p.add_argument("--spectra", action="store_true",
+                   help="dense Jacobian spectra of G^Stokes_T and G^int_T at laminar flow, Re 500 and 1750")
     p.add_argument("--config3", action="store_true",
                    help="pipe flow, Re 2500, Nr 64, m<=24, |k|<=24: tangent throughput and traveling-wave Newton")
     p.add_argument("--config4", action="store_true",
@@ -384,6 +388,168 @@ def run_config2(args):
     print(json.dumps(out))
 
 
+def run_gint(args):
+    """The paper's comparison (Sec. 3.3, Fig. 2 and the K-vs-T figure) on a synthetic stand-in:
+    Newton-GMRES-hookstep on G^Stokes_T = B_T - I (one BEFE step of size T) and on
+    G^int_T = (B_dt)^(T/dt) - I with dt = 1/32, for several T, at the paper's resolution
+    48 x 35 x 48 and Re = 380, from a seeded perturbed-laminar state (amplitude 0.1; the
+    paper's EQ1 field is not available). Reported per run: Newton steps, actions (GMRES
+    iterations), timesteps (residual and trajectory steps plus T/dt per action) and wall time."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1804_05087_gb300 as sp
+    import seeded_inputs as si
+    nx, ny, nz, re, dt_int = 48, 35, 48, 380.0, 1.0 / 32
+    runs = []
+    for kind, T in (("stokes", 1.0), ("stokes", 10.0), ("stokes", 100.0), ("int", 0.125), ("int", 0.25),
+                    ("int", 1.0)):
+        dt = T if kind == "stokes" else dt_int
+        n = 1 if kind == "stokes" else int(round(T / dt_int))
+        ctx = sp.Context(sp.Config(nx, ny, nz, lx=LX, lz=LZ, re=re, dt=dt, prec=sp.SP_MIXED))
+        ctx.sp_autotune(1)
+        a, b, c = si.couette_random_coeffs(1000, nx, ny, nz)
+        U = ctx.zeros()
+        ctx.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], 0.1, U)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = ctx.sp_newton_gmres(U, max_newton=30, max_krylov=args.krylov, tol=1e-10, eta=1e-3, int_steps=n)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        steps = rep["total_steps"] + rep["total_jvps"] * n
+        runs.append({"operator": "G^Stokes" if kind == "stokes" else "G^int", "T": T, "dt": dt,
+                     "steps_per_action": n, "converged": rep["converged"], "newton_iters": rep["newton_iters"],
+                     "actions": rep["total_jvps"],
+                     "K_per_newton": rep["total_jvps"] / max(rep["newton_iters"], 1), "timesteps": steps,
+                     "norm_F": rep["norm_F"], "wall_s": wall})
+        ctx.close()
+    best = {op: min((r for r in runs if r["operator"] == op and r["converged"]), key=lambda r: r["timesteps"],
+                    default=None) for op in ("G^Stokes", "G^int")}
+    out = {"metric": "timesteps and time to |G|<1e-10: G^Stokes_T vs G^int_T (dt = 1/32)", "unit": "timesteps",
+           "higher_is_better": False,
+           "config": {"workload": "plane Couette 48x35x48, Re=380, box 2pi/1.14 x 2 x 2pi/2.5, mixed precision, "
+                                  "seeded perturbed-laminar state (amplitude 0.1, seed 1000)",
+                      "max_krylov": args.krylov, "eta": 1e-3},
+           "runs": runs}
+    if best["G^Stokes"] and best["G^int"]:
+        out["timestep_ratio_best_int_over_best_stokes"] = best["G^int"]["timesteps"] / best["G^Stokes"]["timesteps"]
+        out["time_ratio_best_int_over_best_stokes"] = best["G^int"]["wall_s"] / best["G^Stokes"]["wall_s"]
+    print(json.dumps(out))
+
+
+def dense_jacobian(ctx, n_steps, batch=256):
+    """Real Jacobian (state_len x state_len) of G (n_steps = 1: G^Stokes, > 1: G^int) at the
+    linearisation point already set, one batched tangent launch per block of unit vectors."""
+    import numpy as np
+    import torch
+    L = ctx.state_len
+    J = np.empty((L, L))
+    for i0 in range(0, L, batch):
+        nb = min(batch, L - i0)
+        D = ctx.zeros(nb)
+        Dr = torch.view_as_real(D).reshape(nb, L)
+        Dr[torch.arange(nb), torch.arange(i0, i0 + nb)] = 1.0
+        out = ctx.zeros(nb)
+        if n_steps > 1:
+            ctx.sp_jvp_n(D, out)
+        else:
+            ctx.sp_jvp(D, out)
+        J[:, i0:i0 + nb] = torch.view_as_real(out).reshape(nb, L).cpu().numpy().T
+    return J
+
+
+def hermitian_projection(ctx):
+    """Matrix (real coordinates) of the projection onto Hermitian-consistent states that every
+    map of the library applies to its input: in the kz = 0 plane, (a(ix) + conj a(-ix)) / 2.
+    The tangent is J = P S P - P, so B_U = J + P and G_U vanishes on the range of I - P."""
+    import numpy as np
+    mx, mz, ny = ctx.MX, ctx.MZ, ctx.NY
+    L = ctx.state_len
+    P = np.eye(L)
+    def idx(c, pos, iz, n):
+        return 2 * (((c * mx + pos) * mz + iz) * ny + n)
+    for c in range(3):
+        for pos in range(mx):
+            mpos = (mx - pos) % mx
+            for n in range(ny):
+                i, j = idx(c, pos, 0, n), idx(c, mpos, 0, n)
+                P[i, i] = P[i + 1, i + 1] = 0.0
+                P[i, i] += 0.5
+                P[i, j] += 0.5          # Re: (a_re + b_re) / 2
+                P[i + 1, i + 1] += 0.5
+                P[i + 1, j + 1] -= 0.5  # Im: (a_im - b_im) / 2
+    return P
+
+
+def run_spectra(args):
+    """Spectra of the Jacobians G_U (Sec. 3.3, the spectra figures and Eqs. beaumescale, lims,
+    model, TRe) at laminar plane Couette flow on a 12 x 17 x 12 grid, FP64, Re 500 and 1750.
+    Each Jacobian is built column by column from batched tangent actions on unit vectors and
+    restricted to the physical subspace S (divergence-free, no-slip, Hermitian states: the range
+    of one BEFE step), where G_U acts invariantly; outside S, G_U = -I. Eigenvalues on the host.
+    Checks of the paper's model lambda_k = -k^2/Re +- i k U:
+      * the most negative real eigenvalue of G^Stokes_(T = 1e-4), rescaled by (1 + T)/T, scales as
+        1/Re;
+      * the largest imaginary part of G^Stokes_100 (rescaled) scales as Re;
+      * the radius r around -1 holding 95 % of the eigenvalues of G^int_T (dt = 1/32) obeys
+        T/Re = ln(1/r)/k*^2: ln(1/r) ratios equal T ratios at fixed Re and inverse Re ratios at
+        fixed T."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1804_05087_gb300 as sp
+    nx, ny, nz = 12, 17, 12
+    dt_int = 1.0 / 32
+    Q = None
+    res = {}
+    for re in (500.0, 1750.0):
+        specs = {}
+        for kind, T in (("stokes", 1e-4), ("stokes", 0.1), ("stokes", 100.0), ("int", 1.0), ("int", 10.0)):
+            dt = T if kind == "stokes" else dt_int
+            n = 1 if kind == "stokes" else int(round(T / dt_int))
+            ctx = sp.Context(sp.Config(nx, ny, nz, lx=LX, lz=LZ, re=re, dt=dt, prec=sp.SP_FP64, max_batch=256))
+            U = ctx.zeros()  # laminar flow
+            ctx.sp_set_base_n(U, n)
+            J = dense_jacobian(ctx, n)
+            if Q is None:  # S = range of B_U = J + P (the same subspace for every T and Re)
+                u_, sv, _ = np.linalg.svd(J + hermitian_projection(ctx))
+                d = int(np.sum(sv > 1e-10 * sv[0]))
+                Q = u_[:, :d]
+            A = Q.T @ J @ Q
+            inv = float(np.linalg.norm(J @ Q - Q @ A) / np.linalg.norm(J @ Q))
+            ev = np.linalg.eigvals(A)
+            if kind == "stokes":
+                ev = ev * (1 + T) / T  # Eq. beaumescale
+            specs[(kind, T)] = (ev, inv)
+            ctx.close()
+        st4, st100 = specs[("stokes", 1e-4)][0], specs[("stokes", 100.0)][0]
+        r95 = {}
+        for T in (1.0, 10.0):
+            dist = np.sort(np.abs(specs[("int", T)][0] + 1.0))
+            r95[T] = float(dist[int(np.ceil(0.95 * len(dist))) - 1])
+        res[re] = {"subspace_dim": int(Q.shape[1]),
+                   "invariance_residual_max": max(v[1] for v in specs.values()),
+                   "stokes_1e-4_most_negative_real": float(st4.real.min()),
+                   "stokes_0.1_real_range": [float(specs[("stokes", 0.1)][0].real.min()),
+                                             float(specs[("stokes", 0.1)][0].real.max())],
+                   "stokes_100_max_imag": float(np.abs(st100.imag).max()),
+                   "stokes_100_frac_real_within_0.2_of_-1": float(np.mean(np.abs(st100.real + 1) < 0.2)),
+                   "int_r95": r95}
+    a, b = res[500.0], res[1750.0]
+    out = {"metric": "Jacobian spectra: model scalings (Sec. 3.3)", "config": {
+        "workload": "laminar plane Couette flow, 12x17x12, box 2pi/1.14 x 2 x 2pi/2.5, FP64; G^Stokes_T for "
+                    "T = 1e-4, 0.1, 100 (rescaled by (1+T)/T), G^int_T for T = 1, 10 with dt = 1/32"},
+        "Re500": a, "Re1750": b,
+        "checks": {
+            "most_negative_ratio_500_over_1750 (model: 3.5)": a["stokes_1e-4_most_negative_real"]
+            / b["stokes_1e-4_most_negative_real"],
+            "max_imag_ratio_1750_over_500 (model: 3.5)": b["stokes_100_max_imag"] / a["stokes_100_max_imag"],
+            "ln(1/r95) ratio T=10 over T=1 at Re 500 (model: 10)": math.log(1 / a["int_r95"][10.0])
+            / math.log(1 / a["int_r95"][1.0]),
+            "ln(1/r95) ratio Re 500 over 1750 at T=10 (model: 3.5)": math.log(1 / a["int_r95"][10.0])
+            / math.log(1 / b["int_r95"][10.0])}}
+    print(json.dumps(out))
+
+
 def run_config3(args):
     """Pipe flow in the frame moving with the wave (config 3): Re 2500, alpha 1.25, 2-fold
     symmetry, Nr 64, m' <= 12 (m <= 24), |kz| <= 24, 48 x 96 physical grid, dt 50.
@@ -451,6 +617,10 @@ def main():
         return run_config2(args)
     if args.config3:
         return run_config3(args)
+    if args.gint:
+        return run_gint(args)
+    if args.spectra:
+        return run_spectra(args)
     if args.config4:
         return run_config4(args)
     import torch
