@@ -160,6 +160,17 @@ sp_status sp_set_base(sp_ctx* ctx, const double* U, void* stream);
  * boundary data (Sec. 2). Precision: cfg.prec. Needs sp_set_base. */
 sp_status sp_jvp(sp_ctx* ctx, const double* du, double* Jdu, int n_dir, void* stream);
 
+/* sp_jvp for directions in HOST memory: du and Jdu are host arrays of n_dir
+ * states (page-locked memory lets the copies overlap; pageable memory works
+ * but serialises them). The directions are processed in chunks of `chunk`
+ * (<= 0: n_dir/8 rounded up, at most cfg.max_batch): chunk i is copied in on
+ * an internal stream while chunk i-1 is computed on `stream` and chunk i-2 is
+ * copied out on another internal stream (two device slots held by the
+ * context). Asynchronous: Jdu is complete once `stream` has reached this point
+ * (for instance after cudaStreamSynchronize(stream)); du and Jdu must stay
+ * valid until then. Same results as sp_jvp. */
+sp_status sp_jvp_host(sp_ctx* ctx, const double* du, double* Jdu, int n_dir, int chunk, void* stream);
+
 /* JTr = G_U^* r for n_dir vectors: the adjoint of sp_jvp in the inner product
  * above (the transpose of every stage, in reverse). Precision: cfg.prec. */
 sp_status sp_vjp(sp_ctx* ctx, const double* r, double* JTr, int n_dir, void* stream);

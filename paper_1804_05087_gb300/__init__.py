@@ -89,6 +89,7 @@ def _load():
         "sp_trace_read": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), I], I),
         "sp_autotune": ([P, I, ctypes.POINTER(_TuneReport), V], I),
         "sp_step_n": ([P, P, P, I, V], I),
+        "sp_jvp_host": ([P, P, P, I, I, V], I),
         "sp_set_base_n": ([P, P, I, V], I),
         "sp_jvp_n": ([P, P, P, I, V], I),
         "sp_set_solve_shape": ([P, I, I], I),
@@ -121,7 +122,8 @@ EXPORTS = ("sp_create", "sp_destroy", "sp_last_error", "sp_state_len", "sp_dims"
            "sp_pipe_seed_state", "sp_group_create", "sp_group_destroy", "sp_group_last_error", "sp_group_size",
            "sp_group_state_len", "sp_group_offset", "sp_group_member", "sp_group_step", "sp_group_set_base",
            "sp_group_jvp", "sp_group_inner", "sp_group_newton_gmres", "sp_autotune",
-           "sp_set_solve_shape", "sp_step_n", "sp_set_base_n", "sp_jvp_n")
+           "sp_set_solve_shape", "sp_step_n", "sp_set_base_n", "sp_jvp_n",
+           "sp_jvp_host")
 STAGES = ("k_yinv", "k_xz", "k_solve", "step", "vector")
 
 
@@ -291,6 +293,19 @@ class Context:
         pd, n = self._ptr(du)
         po, _ = self._ptr(out, n)
         self._check(_lib.sp_jvp_n(self._h, pd, po, n, _stream(stream)))
+        return out
+
+    def sp_jvp_host(self, du, out, chunk=0, stream=None):
+        """sp_jvp on host tensors (pinned CPU complex128): copies overlap the computation.
+        Asynchronous on `stream`: synchronise it before reading `out`."""
+        for t in (du, out):
+            if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.complex128 or not t.is_contiguous():
+                raise TypeError("expected contiguous complex128 host tensors")
+        n = du.numel() * 2 // self.state_len
+        if du.numel() * 2 != n * self.state_len or out.numel() != du.numel():
+            raise ValueError("tensor sizes are not whole, equal numbers of states")
+        self._check(_lib.sp_jvp_host(self._h, ctypes.c_void_p(du.data_ptr()), ctypes.c_void_p(out.data_ptr()), n,
+                                     int(chunk), _stream(stream)))
         return out
 
     def sp_jvp_static(self, du, out, stream=None):

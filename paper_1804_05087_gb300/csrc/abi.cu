@@ -92,6 +92,12 @@ static void free_ctx(sp_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
+  if (c->hbuf) cudaFree(c->hbuf);
+  for (cudaEvent_t e : {c->hev_start, c->hev_in[0], c->hev_in[1], c->hev_comp[0], c->hev_comp[1], c->hev_out[0],
+                        c->hev_out[1]})
+    if (e) cudaEventDestroy(e);
+  if (c->hs_in) cudaStreamDestroy(c->hs_in);
+  if (c->hs_out) cudaStreamDestroy(c->hs_out);
   trace_reset(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
@@ -361,6 +367,79 @@ extern "C" sp_status sp_jvp(sp_ctx* c, const double* du, double* Jdu, int n_dir,
     if ((s = sp_cuda(c, traced(c, SP_STAGE_XZ, st, [&] { return launch_xz(c, f32, XZ_TANGENT, c->ws6, c->ws3, nb, st); }), "xz tangent")) != SP_OK) return s;
     if ((s = sp_cuda(c, traced(c, SP_STAGE_SOLVE, st, [&] { return launch_solve(c, f32, c->ws3, u, g, nb, st); }), "solve")) != SP_OK) return s;
   }
+  return SP_OK;
+}
+
+// ---------------------------------------------------------------- host buffers
+// Tangent of directions that live in host memory: chunk i is copied in on one
+// stream, computed on the caller's stream and copied out on another, with two
+// device slots, so the copies of neighbouring chunks overlap the computation.
+static sp_status host_pipeline_setup(sp_ctx* c, int chunk) {
+  if (!c->hs_in) {
+    bool ok = cudaStreamCreateWithFlags(&c->hs_in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&c->hs_out, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&c->hev_start, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; ++k)
+      ok = cudaEventCreateWithFlags(&c->hev_in[k], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->hev_comp[k], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->hev_out[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      return sp_fail(c, SP_ECUDA, "sp_jvp_host: stream/event creation");
+    }
+  }
+  if (c->hchunk < chunk) {
+    if (c->hbuf) cudaFree(c->hbuf);
+    c->hbuf = nullptr;
+    c->hchunk = 0;
+    if (cudaMalloc((void**)&c->hbuf, (size_t)4 * chunk * c->state_len * 8) != cudaSuccess) {
+      cudaGetLastError();
+      return sp_fail(c, SP_ENOMEM, "sp_jvp_host: device slots");
+    }
+    c->hchunk = chunk;
+  }
+  return SP_OK;
+}
+
+extern "C" sp_status sp_jvp_host(sp_ctx* c, const double* du, double* Jdu, int n_dir, int chunk, void* stream) {
+  if (!c || !du || !Jdu || n_dir < 0 || du == Jdu) return sp_fail(c, SP_EINVAL, "sp_jvp_host: bad arguments");
+  if (!c->has_base) return sp_fail(c, SP_EINVAL, "sp_jvp_host: call sp_set_base first");
+  if (n_dir == 0) return SP_OK;
+  if (chunk <= 0) chunk = std::max(1, std::min(c->cfg.max_batch, (n_dir + 7) / 8));
+  chunk = std::min(chunk, c->cfg.max_batch);
+  sp_status s = host_pipeline_setup(c, chunk);
+  if (s != SP_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t L = c->state_len;
+  double* din[2] = {c->hbuf, c->hbuf + (size_t)c->hchunk * L};
+  double* dout[2] = {c->hbuf + (size_t)2 * c->hchunk * L, c->hbuf + (size_t)3 * c->hchunk * L};
+  // the copies start after the caller's earlier work on `stream`
+  if ((s = sp_cuda(c, cudaEventRecord(c->hev_start, st), "event")) != SP_OK) return s;
+  if ((s = sp_cuda(c, cudaStreamWaitEvent(c->hs_in, c->hev_start, 0), "wait")) != SP_OK) return s;
+  if ((s = sp_cuda(c, cudaStreamWaitEvent(c->hs_out, c->hev_start, 0), "wait")) != SP_OK) return s;
+  const int nchunks = (n_dir + chunk - 1) / chunk;
+  for (int i = 0; i < nchunks; ++i) {
+    const int k = i & 1, d0 = i * chunk, nb = std::min(chunk, n_dir - d0);
+    const size_t bytes = (size_t)nb * L * 8;
+    // slot k is free for input once chunk i-2 was computed, for output once it was copied out
+    if (i >= 2 && (s = sp_cuda(c, cudaStreamWaitEvent(c->hs_in, c->hev_comp[k], 0), "wait")) != SP_OK) return s;
+    if ((s = sp_cuda(c, cudaMemcpyAsync(din[k], du + (size_t)d0 * L, bytes, cudaMemcpyHostToDevice, c->hs_in),
+                     "copy in")) != SP_OK)
+      return s;
+    if ((s = sp_cuda(c, cudaEventRecord(c->hev_in[k], c->hs_in), "event")) != SP_OK) return s;
+    if ((s = sp_cuda(c, cudaStreamWaitEvent(st, c->hev_in[k], 0), "wait")) != SP_OK) return s;
+    if (i >= 2 && (s = sp_cuda(c, cudaStreamWaitEvent(st, c->hev_out[k], 0), "wait")) != SP_OK) return s;
+    if ((s = sp_jvp(c, din[k], dout[k], nb, st)) != SP_OK) return s;
+    if ((s = sp_cuda(c, cudaEventRecord(c->hev_comp[k], st), "event")) != SP_OK) return s;
+    if ((s = sp_cuda(c, cudaStreamWaitEvent(c->hs_out, c->hev_comp[k], 0), "wait")) != SP_OK) return s;
+    if ((s = sp_cuda(c, cudaMemcpyAsync(Jdu + (size_t)d0 * L, dout[k], bytes, cudaMemcpyDeviceToHost, c->hs_out),
+                     "copy out")) != SP_OK)
+      return s;
+    if ((s = sp_cuda(c, cudaEventRecord(c->hev_out[k], c->hs_out), "event")) != SP_OK) return s;
+  }
+  // the caller's stream completes after the last copy out
+  for (int k = 0; k < std::min(2, nchunks); ++k)
+    if ((s = sp_cuda(c, cudaStreamWaitEvent(st, c->hev_out[k], 0), "wait")) != SP_OK) return s;
   return SP_OK;
 }
 

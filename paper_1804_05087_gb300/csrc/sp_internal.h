@@ -118,6 +118,11 @@ struct sp_ctx {
   int traj_cap = 0;
   int traj_n = 0;                // steps of the stored trajectory (0: none)
   double* nbuf = nullptr;        // [2] states: scratch of sp_step_n
+  // host-buffer tangent (sp_jvp_host): two copy streams, double-buffered device slots
+  cudaStream_t hs_in = nullptr, hs_out = nullptr;
+  cudaEvent_t hev_start = nullptr, hev_in[2] = {}, hev_comp[2] = {}, hev_out[2] = {};
+  double* hbuf = nullptr;        // [4][hchunk] states: in0, in1, out0, out1
+  int hchunk = 0;
 };
 
 // run `launch` (returning cudaError_t) bracketed by trace events when tracing
