@@ -214,8 +214,11 @@ def run_newton(args):
     import seeded_inputs as si
     nx, ny, nz = (int(t) for t in args.grid.split("x"))
     res = {}
-    for name, prec, fd in (("mixed_tangent", sp.SP_MIXED, False), ("fp64_tangent", sp.SP_FP64, False),
-                           ("fp64_fd", sp.SP_FP64, True)):
+    for name, prec, fd, kry, ell in (("mixed_tangent", sp.SP_MIXED, False, "gmres", 0),
+                                     ("fp64_tangent", sp.SP_FP64, False, "gmres", 0),
+                                     ("fp64_fd", sp.SP_FP64, True, "gmres", 0),
+                                     ("mixed_bicgstab2", sp.SP_MIXED, False, "bicgstab", 2),
+                                     ("mixed_bicgstab4", sp.SP_MIXED, False, "bicgstab", 4)):
         ctx = sp.Context(sp.Config(nx, ny, nz, lx=LX, lz=LZ, re=RE, dt=DT, prec=prec))
         ctx.sp_autotune(1)
         a, b, c = si.couette_random_coeffs(1000, nx, ny, nz)
@@ -223,7 +226,9 @@ def run_newton(args):
         ctx.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], 0.1, U)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rep = ctx.sp_newton_gmres(U, max_newton=30, max_krylov=args.krylov, tol=1e-10, eta=1e-3, use_fd=fd)
+        kmax = args.krylov if kry == "gmres" else 20 * args.krylov  # BiCGSTAB: actions per Newton step
+        rep = ctx.sp_newton_gmres(U, max_newton=30, max_krylov=kmax, tol=1e-10, eta=1e-3, use_fd=fd,
+                                  krylov=kry, ell=max(ell, 1))
         torch.cuda.synchronize()
         rep["wall_s"] = time.perf_counter() - t0
         res[name] = rep

@@ -293,6 +293,12 @@ typedef struct {
   int int_steps;      /* <= 1: G = G^Stokes = B_dt - I (one step, Eq. Gstokes);
                          n > 1: G = G^int = (B_dt)^n - I (n steps of cfg.dt,
                          Eq. Gint; plane Couette, use_gradient = 0)            */
+  int krylov;         /* 0: GMRES with hookstep (default); 1: BiCGSTAB(ell)
+                         (Sec. 3.6: no K^2 term), at most max_krylov actions per
+                         Newton step, trust region along the computed direction
+                         (one more action for its predicted residual); needs
+                         int_steps <= 1, use_gradient = 0                       */
+  int ell;            /* BiCGSTAB(ell): ell (1..8, <= 0: 2)                   */
 } sp_newton_opts;
 
 typedef struct {

@@ -676,11 +676,185 @@ double now_ms() {
 
 }  // namespace
 
+// ---------------------------------------------------------------- BiCGSTAB(l)
+// Newton with BiCGSTAB(l) (Sleijpen & Fokkema, 1993) for G_U du = G(U): no Krylov
+// basis is kept, so no part of the work grows like K^2 (Sec. 3.6). Each outer
+// iteration takes l BiCG steps (two actions each) and then minimises the residual
+// over the l new directions (modified Gram-Schmidt on the small space). Without a
+// Hessenberg matrix there is no hookstep: the trust region acts along the single
+// direction X (step s X, s = min(1, delta/|X|)), with the predicted residual
+// |G - s J X| from one more action and the hookstep's radius update.
+static sp_status newton_bicgstab(sp_ctx* c, double* U, const sp_newton_opts* o, sp_newton_report* rep,
+                                 cudaStream_t st) {
+  const int ell = std::max(1, std::min(8, o->ell > 0 ? o->ell : 2));
+  const int max_act = std::max(2, o->max_krylov);
+  const size_t L = c->state_len;
+  const int nvec = 2 * (ell + 1) + 4;
+  if (c->kry_cap < nvec) {
+    if (c->kry) cudaFree(c->kry);
+    c->kry = nullptr;
+    c->kry_cap = 0;
+    if (cudaMalloc((void**)&c->kry, (size_t)nvec * L * 8) != cudaSuccess) {
+      cudaGetLastError();
+      return sp_fail(c, SP_ENOMEM, "BiCGSTAB vectors");
+    }
+    c->kry_cap = nvec;
+  }
+  double* R = c->kry;                               // r_0 .. r_l
+  double* Uv = c->kry + (size_t)(ell + 1) * L;      // u_0 .. u_l
+  double* X = c->kry + (size_t)2 * (ell + 1) * L;   // the Newton correction
+  double* Rt = X + L;                               // shadow residual
+  double* F = Rt + L;                               // G(U)
+  double* Ut = F + L;                               // trial state
+  auto r = [&](int i) { return R + (size_t)i * L; };
+  auto u = [&](int i) { return Uv + (size_t)i * L; };
+  auto dot = [&](const double* a, const double* b, double* out) { return inner_many(c, a, 1, b, out, st); };
+  auto axpby = [&](double* out, double a, const double* x, double b, const double* y) {
+    return sp_cuda(c, launch_axpby(out, a, x, b, y, L, st), "axpby");
+  };
+  auto act = [&](const double* in, double* out) {
+    rep->total_jvps++;
+    return o->use_fd ? sp_jvp_fd(c, in, out, 1, st) : sp_jvp(c, in, out, 1, st);
+  };
+  const double t0 = now_ms();
+  sp_status s;
+  if ((s = step_batch(c, U, F, 1, st)) != SP_OK) return s;
+  rep->total_steps++;
+  double nF;
+  if ((s = dot(F, F, &nF)) != SP_OK) return s;
+  nF = std::sqrt(nF);
+  rep->norm_F0 = nF;
+  double nU;
+  if ((s = dot(U, U, &nU)) != SP_OK) return s;
+  double delta = o->delta0 > 0 ? o->delta0 : 0.1 * std::max(std::sqrt(nU), 1.0);
+  sp_status result = SP_ENOTCONV;
+  std::vector<double> tau((size_t)(ell + 1) * (ell + 1)), sigma(ell + 1), gp(ell + 1), g(ell + 1), gpp(ell + 1);
+  for (int it = 0; it <= o->max_newton; ++it) {
+    if (!std::isfinite(nF)) { result = SP_ENAN; break; }
+    if (nF < o->tol) { result = SP_OK; break; }
+    if (it == o->max_newton) break;
+    if ((s = sp_set_base(c, U, st)) != SP_OK) return s;
+    rep->total_steps++;
+    // solve J x = F from x = 0
+    if ((s = axpby(r(0), 1.0, F, 0.0, nullptr)) != SP_OK) return s;
+    if ((s = axpby(Rt, 1.0, F, 0.0, nullptr)) != SP_OK) return s;
+    if ((s = sp_cuda(c, cudaMemsetAsync(u(0), 0, L * 8, st), "zero")) != SP_OK) return s;
+    if ((s = sp_cuda(c, cudaMemsetAsync(X, 0, L * 8, st), "zero")) != SP_OK) return s;
+    double rho0 = 1.0, alpha = 0.0, omega = 1.0, rn = nF;
+    int acts = 0;
+    bool broke = false;
+    while (acts < max_act && rn > o->eta * nF && !broke) {
+      rho0 = -omega * rho0;
+      for (int j = 0; j < ell && !broke; ++j) {
+        double rho1;
+        if ((s = dot(Rt, r(j), &rho1)) != SP_OK) return s;
+        if (rho0 == 0.0 || !std::isfinite(rho1)) { broke = true; break; }
+        const double beta = alpha * rho1 / rho0;
+        rho0 = rho1;
+        for (int i = 0; i <= j; ++i)
+          if ((s = axpby(u(i), 1.0, r(i), -beta, u(i))) != SP_OK) return s;
+        if ((s = act(u(j), u(j + 1))) != SP_OK) return s;
+        double gam;
+        if ((s = dot(Rt, u(j + 1), &gam)) != SP_OK) return s;
+        if (gam == 0.0 || !std::isfinite(gam)) { broke = true; break; }
+        alpha = rho0 / gam;
+        for (int i = 0; i <= j; ++i)
+          if ((s = axpby(r(i), 1.0, r(i), -alpha, u(i + 1))) != SP_OK) return s;
+        if ((s = act(r(j), r(j + 1))) != SP_OK) return s;
+        if ((s = axpby(X, 1.0, X, alpha, u(0))) != SP_OK) return s;
+        acts += 2;
+      }
+      if (broke) break;
+      // minimal residual over r_1 .. r_l
+      for (int j = 1; j <= ell; ++j) {
+        for (int i = 1; i < j; ++i) {
+          double t;
+          if ((s = dot(r(j), r(i), &t)) != SP_OK) return s;
+          tau[(size_t)i * (ell + 1) + j] = t / sigma[i];
+          if ((s = axpby(r(j), 1.0, r(j), -tau[(size_t)i * (ell + 1) + j], r(i))) != SP_OK) return s;
+        }
+        if ((s = dot(r(j), r(j), &sigma[j])) != SP_OK) return s;
+        double t0r;
+        if ((s = dot(r(0), r(j), &t0r)) != SP_OK) return s;
+        if (!(sigma[j] > 0.0)) { broke = true; break; }
+        gp[j] = t0r / sigma[j];
+      }
+      if (broke) break;
+      g[ell] = gp[ell];
+      omega = g[ell];
+      for (int j = ell - 1; j >= 1; --j) {
+        double acc = gp[j];
+        for (int i = j + 1; i <= ell; ++i) acc -= tau[(size_t)j * (ell + 1) + i] * g[i];
+        g[j] = acc;
+      }
+      for (int j = 1; j < ell; ++j) {
+        double acc = g[j + 1];
+        for (int i = j + 1; i < ell; ++i) acc += tau[(size_t)j * (ell + 1) + i] * g[i + 1];
+        gpp[j] = acc;
+      }
+      if ((s = axpby(X, 1.0, X, g[1], r(0))) != SP_OK) return s;
+      if ((s = axpby(r(0), 1.0, r(0), -gp[ell], r(ell))) != SP_OK) return s;
+      if ((s = axpby(u(0), 1.0, u(0), -g[ell], u(ell))) != SP_OK) return s;
+      for (int j = 1; j < ell; ++j) {
+        if ((s = axpby(u(0), 1.0, u(0), -g[j], u(j))) != SP_OK) return s;
+        if ((s = axpby(X, 1.0, X, gpp[j], r(j))) != SP_OK) return s;
+        if ((s = axpby(r(0), 1.0, r(0), -gp[j], r(j))) != SP_OK) return s;
+      }
+      if ((s = dot(r(0), r(0), &rn)) != SP_OK) return s;
+      rn = std::sqrt(rn);
+      if (!std::isfinite(rn) || omega == 0.0) broke = true;
+    }
+    // trust region along X (the same radius update as the hookstep): the step s X with
+    // s = min(1, delta/|X|), its predicted residual |F - s J X| from one more action
+    double* JX = u(1);  // free after the solve
+    if ((s = act(X, JX)) != SP_OK) return s;
+    double xx, fj, jj;
+    if ((s = dot(X, X, &xx)) != SP_OK || (s = dot(F, JX, &fj)) != SP_OK || (s = dot(JX, JX, &jj)) != SP_OK) return s;
+    const double nX = std::sqrt(xx);
+    bool accepted = false;
+    double nT = nF;
+    for (int trial = 0; trial < 12 && nX > 0 && std::isfinite(nX); ++trial) {
+      const double sc = std::min(1.0, delta / nX);
+      const double pred = std::sqrt(std::max(0.0, nF * nF - 2.0 * sc * fj + sc * sc * jj));
+      if ((s = axpby(Ut, 1.0, U, -sc, X)) != SP_OK) return s;
+      if ((s = step_batch(c, Ut, F, 1, st)) != SP_OK) return s;
+      rep->total_steps++;
+      if ((s = dot(F, F, &nT)) != SP_OK) return s;
+      nT = std::sqrt(nT);
+      if (trust_update(nF, pred, nT, sc * nX, &delta)) {
+        accepted = true;
+        break;
+      }
+    }
+    if (!accepted) {
+      if ((s = step_batch(c, U, F, 1, st)) != SP_OK) return s;
+      break;
+    }
+    if ((s = sp_cuda(c, cudaMemcpyAsync(U, Ut, L * 8, cudaMemcpyDeviceToDevice, st), "accept")) != SP_OK) return s;
+    nF = nT;
+    rep->newton_iters++;
+  }
+  if ((s = sp_cuda(c, cudaStreamSynchronize(st), "newton sync")) != SP_OK) return s;
+  rep->norm_F = nF;
+  rep->t_total_ms = now_ms() - t0;
+  rep->t_action_ms = -1.0;  // not split for BiCGSTAB(l)
+  if (result == SP_ENOTCONV) c->err = "Newton did not reach the tolerance";
+  return result;
+}
+
 extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts* o, sp_newton_report* rep,
                                      void* stream) {
   if (!c || !U || !o) return sp_fail(c, SP_EINVAL, "sp_newton_gmres: bad arguments");
   if (o->use_gradient && c->geom != 0)
     return sp_fail(c, SP_EINVAL, "sp_newton_gmres: use_gradient needs the adjoint (plane Couette only)");
+  if (o->krylov == 1) {
+    if (o->use_gradient || o->int_steps > 1)
+      return sp_fail(c, SP_EINVAL, "sp_newton_gmres: BiCGSTAB(l) takes single-step actions without use_gradient");
+    sp_newton_report rr{};
+    sp_status s2 = newton_bicgstab(c, U, o, &rr, (cudaStream_t)stream);
+    if (rep) *rep = rr;
+    return s2;
+  }
   const int ns = o->int_steps > 1 ? o->int_steps : 1;  // 1: G^Stokes; > 1: G^int = B^ns - I
   if (ns > 1 && (c->geom != 0 || o->use_gradient))
     return sp_fail(c, SP_EINVAL, "sp_newton_gmres: int_steps > 1 needs a plane Couette context, no use_gradient");

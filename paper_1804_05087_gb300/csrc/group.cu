@@ -560,9 +560,9 @@ static sp_status group_arnoldi(sp_group* g, const GNewtonMem& m, int j, bool cap
 extern "C" sp_status sp_group_newton_gmres(sp_group* g, double* U, const sp_newton_opts* o, int use_graphs,
                                            sp_newton_report* reps, void* stream) {
   if (!g || !U || !o) return gfail(g, SP_EINVAL, "sp_group_newton_gmres: bad arguments");
-  if (o->use_fd || o->use_gradient || o->int_steps > 1)
+  if (o->use_fd || o->use_gradient || o->int_steps > 1 || o->krylov != 0)
     return gfail(g, SP_EINVAL, "sp_group_newton_gmres: single-step tangent actions only "
-                               "(use_fd = use_gradient = 0, int_steps <= 1)");
+                               "(use_fd = use_gradient = krylov = 0, int_steps <= 1)");
   const int K = o->max_krylov;
   if (K < 1 || K > 4096 || o->max_newton < 0) return gfail(g, SP_EINVAL, "sp_group_newton_gmres: bad options");
   const int n = g->n;
