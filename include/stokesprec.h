@@ -299,6 +299,11 @@ typedef struct {
                          (one more action for its predicted residual); needs
                          int_steps <= 1, use_gradient = 0                       */
   int ell;            /* BiCGSTAB(ell): ell (1..8, <= 0: 2)                   */
+  int use_graphs;     /* 1: each Arnoldi step (action + orthogonalisation) is
+                         captured once as a CUDA graph on a stream of the
+                         context and replayed (tangent actions with int_steps
+                         <= 1 and tracing off; otherwise plain launches). The
+                         graphs stay with the context.                         */
 } sp_newton_opts;
 
 typedef struct {

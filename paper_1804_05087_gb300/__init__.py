@@ -48,7 +48,7 @@ class _NewtonOpts(ctypes.Structure):
     _fields_ = [("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int), ("tol", ctypes.c_double),
                 ("eta", ctypes.c_double), ("delta0", ctypes.c_double), ("use_fd", ctypes.c_int),
                 ("use_gradient", ctypes.c_int), ("int_steps", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("ell", ctypes.c_int)]
+                ("ell", ctypes.c_int), ("use_graphs", ctypes.c_int)]
 
 
 class _TuneReport(ctypes.Structure):
@@ -366,9 +366,10 @@ class Context:
         return {STAGES[i]: (ms[i], cnt[i]) for i in range(n)}
 
     def sp_newton_gmres(self, U, max_newton=20, max_krylov=30, tol=1e-10, eta=1e-3, delta0=0.0,
-                        use_fd=False, use_gradient=False, int_steps=1, krylov="gmres", ell=2, stream=None):
+                        use_fd=False, use_gradient=False, int_steps=1, krylov="gmres", ell=2, use_graphs=True,
+                        stream=None):
         pu, _ = self._ptr(U, 1)
-        o = _opts(max_newton, max_krylov, tol, eta, delta0, use_fd, use_gradient, int_steps, krylov, ell)
+        o = _opts(max_newton, max_krylov, tol, eta, delta0, use_fd, use_gradient, int_steps, krylov, ell, use_graphs)
         r = _NewtonReport()
         st = _lib.sp_newton_gmres(self._h, pu, ctypes.byref(o), ctypes.byref(r), _stream(stream))
         rep = {k: getattr(r, k) for k, _ in _NewtonReport._fields_}
@@ -381,9 +382,10 @@ class Context:
 KRYLOV = {"gmres": 0, "bicgstab": 1}
 
 
-def _opts(max_newton, max_krylov, tol, eta, delta0, use_fd, use_gradient, int_steps=1, krylov="gmres", ell=2):
+def _opts(max_newton, max_krylov, tol, eta, delta0, use_fd, use_gradient, int_steps=1, krylov="gmres", ell=2,
+          use_graphs=False):
     return _NewtonOpts(max_newton, max_krylov, tol, eta, delta0, 1 if use_fd else 0, 1 if use_gradient else 0,
-                       int(int_steps), KRYLOV[krylov], int(ell))
+                       int(int_steps), KRYLOV[krylov], int(ell), 1 if use_graphs else 0)
 
 
 class Group:

@@ -84,6 +84,8 @@ static bool good_fft_len(int n) {
   return n == 1;
 }
 
+static void drop_newton_graphs(sp_ctx* c);
+
 static void free_ctx(sp_ctx* c) {
   void* ptrs[] = {c->Th, c->TDh, c->Cfh, c->yv, c->lam6, c->Th_f, c->TDh_f, c->Cfh_f, c->twx, c->twz, c->base32t,
                   c->twx_f, c->twz_f, c->ops, c->ws6, c->ws3, c->base64, c->base32, c->U0,
@@ -96,6 +98,11 @@ static void free_ctx(sp_ctx* c) {
   for (cudaEvent_t e : {c->hev_start, c->hev_in[0], c->hev_in[1], c->hev_comp[0], c->hev_comp[1], c->hev_out[0],
                         c->hev_out[1]})
     if (e) cudaEventDestroy(e);
+  drop_newton_graphs(c);
+  for (cudaEvent_t e : c->nev) cudaEventDestroy(e);
+  c->nev.clear();
+  if (c->nev_in) cudaEventDestroy(c->nev_in);
+  if (c->nstream) cudaStreamDestroy(c->nstream);
   if (c->hs_in) cudaStreamDestroy(c->hs_in);
   if (c->hs_out) cudaStreamDestroy(c->hs_out);
   trace_reset(c);
@@ -842,6 +849,11 @@ static sp_status newton_bicgstab(sp_ctx* c, double* U, const sp_newton_opts* o, 
   return result;
 }
 
+static void drop_newton_graphs(sp_ctx* c) {
+  for (auto& kv : c->ngraphs) cudaGraphExecDestroy(kv.second);
+  c->ngraphs.clear();
+}
+
 extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts* o, sp_newton_report* rep,
                                      void* stream) {
   if (!c || !U || !o) return sp_fail(c, SP_EINVAL, "sp_newton_gmres: bad arguments");
@@ -867,6 +879,7 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   // device scratch after the basis: partials, hA, hB, hn/inv
   const size_t extra = (size_t)(K + 2) * nb + 3 * (size_t)(K + 3) + 8;
   if (c->kry_cap < K + 5) {
+    drop_newton_graphs(c);  // they hold pointers into the old basis
     if (c->kry) cudaFree(c->kry);
     c->kry = nullptr;
     c->kry_cap = 0;
@@ -876,17 +889,38 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     }
     c->kry_cap = K + 5;
   }
-  double* V = c->kry;                           // K+2 basis vectors
-  double* F = c->kry + (size_t)(K + 2) * L;     // residual
-  double* Ut = c->kry + (size_t)(K + 3) * L;    // trial state
-  double* Zg = c->kry + (size_t)(K + 4) * L;    // gradient direction (use_gradient)
-  double* dpart = c->kry + (size_t)(K + 5) * L; // partial sums
-  double* dhA = dpart + (size_t)(K + 2) * nb;   // first Gram-Schmidt pass
-  double* dhB = dhA + (K + 3);                  // second pass
-  double* dhn = dhB + (K + 3);                  // [0] = |w|, [1] = 1/|w|, then y
-  double* hbuf = c->red_host;                   // pinned: hA | hB | hn
-  if ((size_t)2 * (K + 3) + 2 > (size_t)64 * c->red_blocks + 512)
+  // the layout follows the capacity, so captured graphs stay valid for smaller K
+  const int Kc = c->kry_cap - 5;
+  double* V = c->kry;                            // Kc+2 basis vectors
+  double* F = c->kry + (size_t)(Kc + 2) * L;     // residual
+  double* Ut = c->kry + (size_t)(Kc + 3) * L;    // trial state
+  double* Zg = c->kry + (size_t)(Kc + 4) * L;    // gradient direction (use_gradient)
+  double* dpart = c->kry + (size_t)(Kc + 5) * L; // partial sums
+  double* dhA = dpart + (size_t)(Kc + 2) * nb;   // first Gram-Schmidt pass
+  double* dhB = dhA + (Kc + 3);                  // second pass
+  double* dhn = dhB + (Kc + 3);                  // [0] = |w|, [1] = 1/|w|, then y
+  double* hbuf = c->red_host;                    // pinned: hA | hB | hn
+  if ((size_t)2 * (Kc + 3) + 2 > (size_t)64 * c->red_blocks + 512)
     return sp_fail(c, SP_EINVAL, "sp_newton_gmres: Krylov dimension too large for the pinned buffer");
+  // CUDA graphs of the Arnoldi steps: tangent actions only, on the context's own stream
+  bool graphs = o->use_graphs && !o->use_fd && ns == 1 && !c->trace;
+  if (graphs && !c->nstream) {
+    if (cudaStreamCreateWithFlags(&c->nstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->nev_in, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      graphs = false;
+    }
+  }
+  if (graphs) {  // the private stream starts after the caller's earlier work
+    cudaEventRecord(c->nev_in, st);
+    cudaStreamWaitEvent(c->nstream, c->nev_in, 0);
+    st = c->nstream;
+  }
+  while ((int)c->nev.size() < 3 * (Kc + 2)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return sp_fail(c, SP_ECUDA, "events");
+    c->nev.push_back(e);
+  }
   sp_newton_report r{};
   const double t0 = now_ms();
   sp_status s;
@@ -917,7 +951,8 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     int k = 0;
     // orthogonalise w = (action on column j) against V[0..j] (CGS2 on the device), normalise it
     // into V[j+1], and update column j of H, its Givens-rotated copy R and the residual g
-    auto orth_column = [&](int j, double* w, double* hn_out) -> sp_status {
+    // device part of one Arnoldi column (capturable): CGS2, normalisation, copies to the host
+    auto enqueue_orth = [&](int j, double* w) -> sp_status {
       sp_status q;
       if ((q = sp_cuda(c, launch_dev_dots(c, V, j + 1, w, dpart, nb, dhA, nullptr, st), "dots")) != SP_OK) return q;
       if ((q = sp_cuda(c, launch_multi_axpy(c, V, j + 1, dhA, w, st), "axpy")) != SP_OK) return q;
@@ -927,37 +962,81 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
       if ((q = sp_cuda(c, launch_scale_dev(c, w, dhn + 1, st), "scale")) != SP_OK) return q;
       if ((q = sp_cuda(c, cudaMemcpyAsync(hbuf, dhA, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, st), "h")) != SP_OK)
         return q;
-      if ((q = sp_cuda(c, cudaMemcpyAsync(hbuf + K + 3, dhB, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, st), "h")) !=
+      if ((q = sp_cuda(c, cudaMemcpyAsync(hbuf + Kc + 3, dhB, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, st), "h")) !=
           SP_OK)
         return q;
-      if ((q = sp_cuda(c, cudaMemcpyAsync(hbuf + 2 * (K + 3), dhn, 8, cudaMemcpyDeviceToHost, st), "h")) != SP_OK)
-        return q;
-      if ((q = sp_cuda(c, cudaStreamSynchronize(st), "orth sync")) != SP_OK) return q;
-      const double hn = hbuf[2 * (K + 3)];
+      return sp_cuda(c, cudaMemcpyAsync(hbuf + 2 * (Kc + 3), dhn, 8, cudaMemcpyDeviceToHost, st), "h");
+    };
+    // host part (after the stream is synchronised): column j of H, its Givens-rotated copy R, g
+    auto finish_orth = [&](int j) -> double {
+      const double hn = hbuf[2 * (Kc + 3)];
       double* Hc = H.data() + (size_t)j * LD;
       double* Rc = R.data() + (size_t)j * LD;
-      for (int i = 0; i <= j; ++i) Hc[i] = hbuf[i] + hbuf[K + 3 + i];
+      for (int i = 0; i <= j; ++i) Hc[i] = hbuf[i] + hbuf[Kc + 3 + i];
       Hc[j + 1] = hn;
       givens_column(Hc, Rc, j, cs.data(), sn.data(), g.data());
-      *hn_out = hn;
+      return hn;
+    };
+    auto orth_column = [&](int j, double* w, double* hn_out) -> sp_status {
+      sp_status q;
+      if ((q = enqueue_orth(j, w)) != SP_OK) return q;
+      if ((q = sp_cuda(c, cudaStreamSynchronize(st), "orth sync")) != SP_OK) return q;
+      *hn_out = finish_orth(j);
       return SP_OK;
     };
-    for (int j = 0; j < K; ++j) {
+    // one Arnoldi step on the device: the action on v_j, then its column; events bracket both
+    auto enqueue_step = [&](int j, bool capturing) -> sp_status {
       double* vj = V + (size_t)j * L;
       double* w = V + (size_t)(j + 1) * L;
-      double ta = now_ms();
-      if (o->use_fd) s = sp_jvp_fd(c, vj, w, 1, st);
-      else s = ns > 1 ? sp_jvp_n(c, vj, w, 1, st) : sp_jvp(c, vj, w, 1, st);
-      if (s != SP_OK) return s;
-      if (r.t_action_ms >= 0) {
-        if ((s = sp_cuda(c, cudaStreamSynchronize(st), "jvp sync")) != SP_OK) return s;
+      cudaEvent_t* ev = c->nev.data() + 3 * (size_t)j;
+      auto rec = [&](cudaEvent_t e) {
+        return capturing ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
+      };
+      sp_status q;
+      if ((q = sp_cuda(c, rec(ev[0]), "event")) != SP_OK) return q;
+      if (o->use_fd) q = sp_jvp_fd(c, vj, w, 1, st);
+      else q = ns > 1 ? sp_jvp_n(c, vj, w, 1, st) : sp_jvp(c, vj, w, 1, st);
+      if (q != SP_OK) return q;
+      if ((q = sp_cuda(c, rec(ev[1]), "event")) != SP_OK) return q;
+      if ((q = enqueue_orth(j, w)) != SP_OK) return q;
+      return sp_cuda(c, rec(ev[2]), "event");
+    };
+    for (int j = 0; j < K; ++j) {
+      bool launched = false;
+      if (graphs) {
+        auto itg = c->ngraphs.find(j);
+        if (itg == c->ngraphs.end()) {
+          cudaGraph_t graph = nullptr;
+          cudaGraphExec_t exec = nullptr;
+          bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+          const sp_status cs_ = ok ? enqueue_step(j, true) : SP_ECUDA;
+          const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+          ok = ok && cs_ == SP_OK && ce == cudaSuccess && graph &&
+               cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+          if (graph) cudaGraphDestroy(graph);
+          if (!ok) {  // not capturable here: continue with plain launches
+            cudaGetLastError();
+            if (exec) cudaGraphExecDestroy(exec);
+            graphs = false;
+          } else {
+            itg = c->ngraphs.emplace(j, exec).first;
+          }
+        }
+        if (graphs) {
+          if ((s = sp_cuda(c, cudaGraphLaunch(itg->second, st), "graph launch")) != SP_OK) return s;
+          launched = true;
+        }
       }
-      double tb = now_ms();
-      r.t_action_ms += tb - ta;
+      if (!launched && (s = enqueue_step(j, false)) != SP_OK) return s;
+      if ((s = sp_cuda(c, cudaStreamSynchronize(st), "arnoldi sync")) != SP_OK) return s;
+      const double hn = finish_orth(j);
+      float ta = 0, tb = 0;
+      cudaEvent_t* ev = c->nev.data() + 3 * (size_t)j;
+      if (cudaEventElapsedTime(&ta, ev[0], ev[1]) == cudaSuccess) r.t_action_ms += ta;
+      else cudaGetLastError();  // timing is best effort; keep the error state clean
+      if (cudaEventElapsedTime(&tb, ev[1], ev[2]) == cudaSuccess) r.t_orth_ms += tb;
+      else cudaGetLastError();
       r.total_jvps++;
-      double hn = 0;
-      if ((s = orth_column(j, w, &hn)) != SP_OK) return s;
-      r.t_orth_ms += now_ms() - tb;
       k = j + 1;
       if (!std::isfinite(hn)) return sp_fail(c, SP_ENAN, "non-finite Arnoldi vector");
       if (std::fabs(g[k]) <= o->eta * nF || hn == 0.0) break;

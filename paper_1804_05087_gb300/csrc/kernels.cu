@@ -1199,6 +1199,26 @@ __global__ void k_scale_dev(double* x, size_t n, const double* s) {
     x[i] *= f;
 }
 
+// w -= sum_i h_i V_i with the rows split over the 8 warps of a block: each block owns 32
+// consecutive elements (coalesced row reads), each warp a slice of the rows, then a
+// shared-memory sum; short dependent chains for small states with many rows
+__global__ void __launch_bounds__(256) k_multi_axpy_tiled(const double* __restrict__ V, int k, size_t n,
+                                                         const double* __restrict__ h, double* __restrict__ w) {
+  __shared__ double part[8][33];
+  const size_t e = (size_t)blockIdx.x * 32 + threadIdx.x;
+  double acc = 0.0;
+  if (e < n)
+    for (int r = threadIdx.y; r < k; r += 8) acc = fma(h[r], V[(size_t)r * n + e], acc);
+  part[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && e < n) {
+    double sum = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sum += part[q][threadIdx.x];
+    w[e] -= sum;
+  }
+}
+
 __global__ void k_multi_axpy(const double* V, int k, size_t n, const double* h, double* w) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     // eight independent partial sums keep eight loads in flight
@@ -1646,7 +1666,13 @@ cudaError_t launch_scale_dev(const sp_ctx* c, double* x, const double* s, cudaSt
 
 cudaError_t launch_multi_axpy(const sp_ctx* c, const double* V, int k, const double* h, double* w,
                               cudaStream_t st) {
-  k_multi_axpy<<<grid_for(c->state_len, 256, c->sm_count), 256, 0, st>>>(V, k, c->state_len, h, w);
+  if (k <= 0) return cudaSuccess;
+  if (k >= 16) {  // many rows: split them over warps
+    const unsigned blocks = (unsigned)((c->state_len + 31) / 32);
+    k_multi_axpy_tiled<<<blocks, dim3(32, 8), 0, st>>>(V, k, c->state_len, h, w);
+  } else {
+    k_multi_axpy<<<grid_for(c->state_len, 256, c->sm_count), 256, 0, st>>>(V, k, c->state_len, h, w);
+  }
   return cudaGetLastError();
 }
 

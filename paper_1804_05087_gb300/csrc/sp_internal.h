@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -123,6 +124,11 @@ struct sp_ctx {
   cudaEvent_t hev_start = nullptr, hev_in[2] = {}, hev_comp[2] = {}, hev_out[2] = {};
   double* hbuf = nullptr;        // [4][hchunk] states: in0, in1, out0, out1
   int hchunk = 0;
+  // Newton: captured Arnoldi steps (keyed by step index), their stream and timing events
+  std::map<int, cudaGraphExec_t> ngraphs;
+  cudaStream_t nstream = nullptr;
+  cudaEvent_t nev_in = nullptr;
+  std::vector<cudaEvent_t> nev;  // 3 per Arnoldi step
 };
 
 // run `launch` (returning cudaError_t) bracketed by trace events when tracing
