@@ -5,7 +5,8 @@
 // GMRES are one launch over all members' slices of a group vector (below).
 // Newton-GMRES-hookstep (Sec. 2, Sec. 3.2) runs on all members in lock step:
 // Arnoldi step j of every member that is still iterating is one sequence of
-// launches, optionally replayed as a captured CUDA graph. The arithmetic of a
+// launches (classical Gram-Schmidt with selective reorthogonalisation), optionally
+// replayed as a captured CUDA graph. The arithmetic of a
 // member is exactly that of its own context.
 #include <algorithm>
 #include <chrono>
@@ -128,6 +129,31 @@ __global__ void k_gnorm(const double* __restrict__ partials, const GVec* __restr
     hn[i] = s;
     inv[i] = s > 0.0 ? 1.0 / s : 0.0;
   }
+}
+
+// Selective reorthogonalisation (Daniel, Gragg, Kaufman & Stewart): after the first
+// Gram-Schmidt pass, |w'|^2 = |w|^2 - |h|^2 (V orthonormal); member i needs the second
+// pass only if |w'| < |w| / sqrt(2). flag[i] = 1 then; otherwise its second-pass
+// coefficients are zeroed. One warp per member.
+__global__ void k_greorth_decide(const double* __restrict__ h, int n, int k, const double* __restrict__ wn,
+                                 const int* __restrict__ active, int* __restrict__ flag, double* __restrict__ h2) {
+  const int i = blockIdx.x;
+  if (active && !active[i]) {
+    if (threadIdx.x == 0) flag[i] = 0;
+    return;
+  }
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < k; q += 32) {
+    const double v = h[(size_t)q * n + i];
+    acc = fma(v, v, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  acc = __shfl_sync(0xffffffffu, acc, 0);
+  const double w2 = wn[i] * wn[i];
+  const int f = (w2 - acc < 0.5 * w2) ? 1 : 0;
+  if (threadIdx.x == 0) flag[i] = f;
+  if (!f)
+    for (int q = threadIdx.x; q < k; q += 32) h2[(size_t)q * n + i] = 0.0;
 }
 
 // w_i -= sum_{row < k} h[row * n + i] V_row,i
@@ -475,6 +501,8 @@ struct GNewtonMem {
   double *part;               // partial sums [(K+2)][vblocks]
   double *hA, *hB, *y;        // [(K+3)][n] each (row-major over rows, member fastest)
   double *hn, *inv, *s;       // [n] each
+  double *wn, *wdummy;        // [n] each: |w| before the first pass
+  int* flag;                  // [n]: second Gram-Schmidt pass needed
   // pinned host mirrors
   double *hA_h, *hB_h, *hn_h, *y_h;
 };
@@ -484,7 +512,7 @@ struct GNewtonMem {
 static sp_status group_newton_mem(sp_group* g, int K, GNewtonMem* m) {
   const size_t L = g->len, n = (size_t)g->n;
   const size_t vec = (size_t)(K + 5) * L;
-  const size_t extra = (size_t)(K + 2) * g->vblocks + 3 * (size_t)(K + 3) * n + 3 * n + 8;
+  const size_t extra = (size_t)(K + 2) * g->vblocks + 3 * (size_t)(K + 3) * n + 6 * n + 8;
   if (g->kry_cap < K) {
     drop_graphs(g);  // graphs hold pointers into the old basis
     if (g->kry) cudaFree(g->kry);
@@ -522,6 +550,9 @@ static sp_status group_newton_mem(sp_group* g, int K, GNewtonMem* m) {
   m->hn = m->y + (size_t)(Kc + 3) * n;
   m->inv = m->hn + n;
   m->s = m->inv + n;
+  m->wn = m->s + n;
+  m->wdummy = m->wn + n;
+  m->flag = reinterpret_cast<int*>(m->wdummy + n);
   const size_t hl = (size_t)(Kc + 3) * n;
   m->hA_h = g->kry_host;
   m->hB_h = m->hA_h + hl;
@@ -530,8 +561,9 @@ static sp_status group_newton_mem(sp_group* g, int K, GNewtonMem* m) {
   return SP_OK;
 }
 
-// one lock-step Arnoldi step: w = J v_j for the active members, CGS2 against
-// v_0..v_j, normalisation into v_{j+1}; h columns and |w| copied to the host
+// one lock-step Arnoldi step: w = J v_j for the active members, Gram-Schmidt against
+// v_0..v_j (second pass where needed), normalisation into v_{j+1}; h columns and
+// |w| copied to the host
 static sp_status group_arnoldi(sp_group* g, const GNewtonMem& m, int j, bool capturing, cudaStream_t st) {
   const double* vj = m.V + (size_t)j * g->len;
   double* w = m.V + (size_t)(j + 1) * g->len;
@@ -544,10 +576,14 @@ static sp_status group_arnoldi(sp_group* g, const GNewtonMem& m, int j, bool cap
   if ((s = gcuda(g, rec(ev[0]), "event")) != SP_OK) return s;
   if ((s = group_jvp(g, vj, w, g->act, st)) != SP_OK) return s;
   if ((s = gcuda(g, rec(ev[1]), "event")) != SP_OK) return s;
+  // classical Gram-Schmidt, with the second pass only for the members that need it
   if ((s = gcuda(g, launch_ghdots(g, m.V, g->len, k, w, g->act, m.part, m.hA, st), "dots")) != SP_OK) return s;
+  if ((s = gcuda(g, launch_gnorm(g, w, g->act, m.part, m.wn, m.wdummy, st), "norm")) != SP_OK) return s;
+  k_greorth_decide<<<n, 32, 0, st>>>(m.hA, n, k, m.wn, g->act, m.flag, m.hB);
+  if ((s = gcuda(g, cudaGetLastError(), "decide")) != SP_OK) return s;
   if ((s = gcuda(g, launch_gaxpy(g, m.V, k, m.hA, w, g->act, st), "axpy")) != SP_OK) return s;
-  if ((s = gcuda(g, launch_ghdots(g, m.V, g->len, k, w, g->act, m.part, m.hB, st), "dots")) != SP_OK) return s;
-  if ((s = gcuda(g, launch_gaxpy(g, m.V, k, m.hB, w, g->act, st), "axpy")) != SP_OK) return s;
+  if ((s = gcuda(g, launch_ghdots(g, m.V, g->len, k, w, m.flag, m.part, m.hB, st), "dots")) != SP_OK) return s;
+  if ((s = gcuda(g, launch_gaxpy(g, m.V, k, m.hB, w, m.flag, st), "axpy")) != SP_OK) return s;
   if ((s = gcuda(g, launch_gnorm(g, w, g->act, m.part, m.hn, m.inv, st), "norm")) != SP_OK) return s;
   if ((s = gcuda(g, launch_gscale(g, w, w, m.inv, g->act, st), "scale")) != SP_OK) return s;
   const size_t hb = (size_t)k * n * 8;
