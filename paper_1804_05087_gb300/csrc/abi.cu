@@ -877,7 +877,7 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   // one partial sum per ~1024 complex values, at most red_blocks
   const int nb = (int)std::max<size_t>(1, std::min<size_t>(c->red_blocks, (c->cplx_per_state + 1023) / 1024));
   // device scratch after the basis: partials, hA, hB, hn/inv
-  const size_t extra = (size_t)(K + 2) * nb + 3 * (size_t)(K + 3) + 8;
+  const size_t extra = (size_t)(K + 2) * nb + 3 * (size_t)(K + 3) + 24;
   if (c->kry_cap < K + 5) {
     drop_newton_graphs(c);  // they hold pointers into the old basis
     if (c->kry) cudaFree(c->kry);
@@ -899,6 +899,8 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   double* dhA = dpart + (size_t)(Kc + 2) * nb;   // first Gram-Schmidt pass
   double* dhB = dhA + (Kc + 3);                  // second pass
   double* dhn = dhB + (Kc + 3);                  // [0] = |w|, [1] = 1/|w|, then y
+  double* dwn = dhn + (Kc + 6);                  // |w| before the first pass, scratch
+  int* dflag = reinterpret_cast<int*>(dwn + 4);  // second Gram-Schmidt pass needed
   double* hbuf = c->red_host;                    // pinned: hA | hB | hn
   if ((size_t)2 * (Kc + 3) + 2 > (size_t)64 * c->red_blocks + 512)
     return sp_fail(c, SP_EINVAL, "sp_newton_gmres: Krylov dimension too large for the pinned buffer");
@@ -951,13 +953,23 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     int k = 0;
     // orthogonalise w = (action on column j) against V[0..j] (CGS2 on the device), normalise it
     // into V[j+1], and update column j of H, its Givens-rotated copy R and the residual g
-    // device part of one Arnoldi column (capturable): CGS2, normalisation, copies to the host
+    // device part of one Arnoldi column (capturable): classical Gram-Schmidt twice, normalisation,
+    // copies to the host. For large states the second pass runs only when the first one lost
+    // too much (|w'| < |w|/sqrt(2), decided on the device): it halves the basis traffic; small
+    // states are latency-bound and keep the shorter launch sequence of the full second pass.
+    const bool selective = L >= 65536;
     auto enqueue_orth = [&](int j, double* w) -> sp_status {
       sp_status q;
+      const int* gate = selective ? dflag : nullptr;
       if ((q = sp_cuda(c, launch_dev_dots(c, V, j + 1, w, dpart, nb, dhA, nullptr, st), "dots")) != SP_OK) return q;
+      if (selective) {
+        if ((q = sp_cuda(c, launch_dev_norm(c, w, dpart, nb, dwn, dwn + 1, st), "norm")) != SP_OK) return q;
+        if ((q = sp_cuda(c, launch_reorth_decide(dhA, j + 1, dwn, dflag, dhB, st), "decide")) != SP_OK) return q;
+      }
       if ((q = sp_cuda(c, launch_multi_axpy(c, V, j + 1, dhA, w, st), "axpy")) != SP_OK) return q;
-      if ((q = sp_cuda(c, launch_dev_dots(c, V, j + 1, w, dpart, nb, dhB, nullptr, st), "dots")) != SP_OK) return q;
-      if ((q = sp_cuda(c, launch_multi_axpy(c, V, j + 1, dhB, w, st), "axpy")) != SP_OK) return q;
+      if ((q = sp_cuda(c, launch_dev_dots(c, V, j + 1, w, dpart, nb, dhB, nullptr, st, gate), "dots")) != SP_OK)
+        return q;
+      if ((q = sp_cuda(c, launch_multi_axpy(c, V, j + 1, dhB, w, st, gate), "axpy")) != SP_OK) return q;
       if ((q = sp_cuda(c, launch_dev_norm(c, w, dpart, nb, dhn, dhn + 1, st), "norm")) != SP_OK) return q;
       if ((q = sp_cuda(c, launch_scale_dev(c, w, dhn + 1, st), "scale")) != SP_OK) return q;
       if ((q = sp_cuda(c, cudaMemcpyAsync(hbuf, dhA, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, st), "h")) != SP_OK)

@@ -1127,7 +1127,8 @@ __global__ void k_multi_inner(const double2* V, int k, size_t ncplx, const doubl
 
 // partial weighted inner products of 8 rows of V with w per block row: grid (nb, ceil(k/8))
 __global__ void k_multi_inner8(const double2* V, int k, size_t ncplx, const double2* w, int NY, int MZ,
-                               double* partials) {
+                               double* partials, const int* gate) {
+  if (gate && !*gate) return;  // device-side switch (selective reorthogonalisation)
   const int i0 = blockIdx.y * 8;
   double acc[8];
 #pragma unroll
@@ -1173,7 +1174,8 @@ __global__ void k_multi_inner8(const double2* V, int k, size_t ncplx, const doub
 }
 
 // out[i] = sum_b partials[i][b] (+ add[i] if add != null); one block per i
-__global__ void k_reduce_rows(const double* partials, int nb, double* out, const double* add) {
+__global__ void k_reduce_rows(const double* partials, int nb, double* out, const double* add, const int* gate) {
+  if (gate && !*gate) return;
   const int i = blockIdx.x;
   double acc = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partials[(size_t)i * nb + b];
@@ -1199,11 +1201,29 @@ __global__ void k_scale_dev(double* x, size_t n, const double* s) {
     x[i] *= f;
 }
 
+// Selective reorthogonalisation (Daniel, Gragg, Kaufman & Stewart): after the first
+// Gram-Schmidt pass |w'|^2 = |w|^2 - |h|^2; the second pass runs only if
+// |w'| < |w| / sqrt(2) (flag = 1), otherwise its coefficients are zeroed. One warp.
+__global__ void k_reorth_decide(const double* __restrict__ h, int k, const double* __restrict__ wn,
+                                int* __restrict__ flag, double* __restrict__ h2) {
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < k; q += 32) acc = fma(h[q], h[q], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  acc = __shfl_sync(0xffffffffu, acc, 0);
+  const double w2 = wn[0] * wn[0];
+  const int f = (w2 - acc < 0.5 * w2) ? 1 : 0;
+  if (threadIdx.x == 0) *flag = f;
+  if (!f)
+    for (int q = threadIdx.x; q < k; q += 32) h2[q] = 0.0;
+}
+
 // w -= sum_i h_i V_i with the rows split over the 8 warps of a block: each block owns 32
 // consecutive elements (coalesced row reads), each warp a slice of the rows, then a
 // shared-memory sum; short dependent chains for small states with many rows
 __global__ void __launch_bounds__(256) k_multi_axpy_tiled(const double* __restrict__ V, int k, size_t n,
-                                                         const double* __restrict__ h, double* __restrict__ w) {
+                                                         const double* __restrict__ h, double* __restrict__ w,
+                                                         const int* __restrict__ gate) {
+  if (gate && !*gate) return;
   __shared__ double part[8][33];
   const size_t e = (size_t)blockIdx.x * 32 + threadIdx.x;
   double acc = 0.0;
@@ -1219,7 +1239,8 @@ __global__ void __launch_bounds__(256) k_multi_axpy_tiled(const double* __restri
   }
 }
 
-__global__ void k_multi_axpy(const double* V, int k, size_t n, const double* h, double* w) {
+__global__ void k_multi_axpy(const double* V, int k, size_t n, const double* h, double* w, const int* gate) {
+  if (gate && !*gate) return;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     // eight independent partial sums keep eight loads in flight
     double acc[8] = {w[e], 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -1641,12 +1662,17 @@ cudaError_t launch_inner_partials(const sp_ctx* c, const double* a, const double
 }
 
 // device-resident Arnoldi helpers (no host round trip)
+cudaError_t launch_reorth_decide(const double* h, int k, const double* wn, int* flag, double* h2, cudaStream_t st) {
+  k_reorth_decide<<<1, 32, 0, st>>>(h, k, wn, flag, h2);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dev_dots(const sp_ctx* c, const double* V, int k, const double* w, double* partials,
-                            int nblocks, double* out, const double* add, cudaStream_t st) {
+                            int nblocks, double* out, const double* add, cudaStream_t st, const int* gate) {
   dim3 grid(nblocks, (k + 7) / 8);
   k_multi_inner8<<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(V), k, c->cplx_per_state,
-                                       reinterpret_cast<const double2*>(w), c->NY, c->MZ, partials);
-  k_reduce_rows<<<k, 256, 0, st>>>(partials, nblocks, out, add);
+                                       reinterpret_cast<const double2*>(w), c->NY, c->MZ, partials, gate);
+  k_reduce_rows<<<k, 256, 0, st>>>(partials, nblocks, out, add, gate);
   return cudaGetLastError();
 }
 
@@ -1654,7 +1680,7 @@ cudaError_t launch_dev_norm(const sp_ctx* c, const double* w, double* partials, 
                             double* inv, cudaStream_t st) {
   dim3 grid(nblocks, 1);
   k_multi_inner8<<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(w), 1, c->cplx_per_state,
-                                       reinterpret_cast<const double2*>(w), c->NY, c->MZ, partials);
+                                       reinterpret_cast<const double2*>(w), c->NY, c->MZ, partials, nullptr);
   k_norm_finish<<<1, 256, 0, st>>>(partials, nblocks, h, inv);
   return cudaGetLastError();
 }
@@ -1665,13 +1691,13 @@ cudaError_t launch_scale_dev(const sp_ctx* c, double* x, const double* s, cudaSt
 }
 
 cudaError_t launch_multi_axpy(const sp_ctx* c, const double* V, int k, const double* h, double* w,
-                              cudaStream_t st) {
+                              cudaStream_t st, const int* gate) {
   if (k <= 0) return cudaSuccess;
   if (k >= 16) {  // many rows: split them over warps
     const unsigned blocks = (unsigned)((c->state_len + 31) / 32);
-    k_multi_axpy_tiled<<<blocks, dim3(32, 8), 0, st>>>(V, k, c->state_len, h, w);
+    k_multi_axpy_tiled<<<blocks, dim3(32, 8), 0, st>>>(V, k, c->state_len, h, w, gate);
   } else {
-    k_multi_axpy<<<grid_for(c->state_len, 256, c->sm_count), 256, 0, st>>>(V, k, c->state_len, h, w);
+    k_multi_axpy<<<grid_for(c->state_len, 256, c->sm_count), 256, 0, st>>>(V, k, c->state_len, h, w, gate);
   }
   return cudaGetLastError();
 }

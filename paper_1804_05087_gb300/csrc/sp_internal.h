@@ -230,11 +230,15 @@ cudaError_t launch_inner_partials(const sp_ctx* c, const double* a, const double
 cudaError_t launch_multi_inner(const sp_ctx* c, const double* V, int k, const double* w,
                                double* partials, int nblocks, cudaStream_t st);
 // device-resident Arnoldi: out[i] = <V_i, w> (+ add[i]); h = |w|, inv = 1/|w|; x *= *s
+// gate: device int; when it holds 0 the launches return at once (null: always run)
 cudaError_t launch_dev_dots(const sp_ctx* c, const double* V, int k, const double* w, double* partials,
-                            int nblocks, double* out, const double* add, cudaStream_t st);
+                            int nblocks, double* out, const double* add, cudaStream_t st,
+                            const int* gate = nullptr);
 cudaError_t launch_dev_norm(const sp_ctx* c, const double* w, double* partials, int nblocks, double* h,
                             double* inv, cudaStream_t st);
 cudaError_t launch_scale_dev(const sp_ctx* c, double* x, const double* s, cudaStream_t st);
 // w -= sum_i h_i V_i (h on device)
 cudaError_t launch_multi_axpy(const sp_ctx* c, const double* V, int k, const double* h,
-                              double* w, cudaStream_t st);
+                              double* w, cudaStream_t st, const int* gate = nullptr);
+// second Gram-Schmidt pass needed? *flag = (|w|^2 - |h|^2 < |w|^2 / 2); if not, h2 = 0 (k entries)
+cudaError_t launch_reorth_decide(const double* h, int k, const double* wn, int* flag, double* h2, cudaStream_t st);
