@@ -33,6 +33,15 @@ subspace (``sym``), which is what a real field requires.
 Inner product (used for norms, GMRES and the adjoint):
     <a, b> = sum over stored coefficients of w(iz) Re(conj(a) b),
     w(0) = 1, w(iz > 0) = 2.
+
+Laminar advection in L (``lam_adv=True``; Sec. 3.6, the closing proposal, and
+Eq. modelgen): the linearisation of the advection about laminar flow,
+    M u = (U_lam . grad) u + (u . grad) U_lam = y du/dx + v e_x,
+moves from N to L: L' = L - M, N' = N + M, so that the step is
+    (1/dt - nu lap + M) u_new + grad p = u/dt + N(u) + M u.
+Per mode M is i kx Y (Y: multiplication by y in Chebyshev coefficients) on
+every component plus v in the x-momentum rows; the fixed points of B' are
+those of B (both steps leave u_new = u where L u + N(u) = 0).
 """
 from __future__ import annotations
 
@@ -46,8 +55,9 @@ class Couette:
     """Grid, operators and per-mode factorisations for one configuration."""
 
     def __init__(self, nx, ny, nz, lx=2 * math.pi / 1.14, lz=2 * math.pi / 2.5,
-                 re=400.0, dt=100.0):
+                 re=400.0, dt=100.0, lam_adv=False):
         self.nx, self.ny, self.nz = nx, ny, nz
+        self.lam_adv = bool(lam_adv)
         self.lx, self.lz, self.re, self.dt = float(lx), float(lz), float(re), float(dt)
         self.nu = 1.0 / self.re
         self.N = ny - 1
@@ -81,6 +91,16 @@ class Couette:
                     D[n, p] = 2.0 * p / c[n]
         self.D = D
         self.D2 = D @ D
+        # multiplication by y: y T_0 = T_1, y T_m = (T_(m+1) + T_(m-1))/2 (degree N+1 dropped)
+        Y = np.zeros((N + 1, N + 1))
+        for m in range(N + 1):
+            if m == 0:
+                Y[1, 0] = 1.0
+                continue
+            Y[m - 1, m] += 0.5
+            if m + 1 <= N:
+                Y[m + 1, m] += 0.5
+        self.Y = Y
         # Fourier: physical points and the explicit exponentials
         xg = np.arange(nx) * self.lx / nx
         zg = np.arange(nz) * self.lz / nz
@@ -175,6 +195,13 @@ class Couette:
         n = self.cross(base_fields[0:3], g[3:6]) + self.cross(g[0:3], base_fields[3:6])
         return self.cheb_coeffs(self.to_spectral(n))
 
+    def laminar_advection(self, c):
+        """M u = y du/dx + v e_x per mode (Sec. 3.6): i kx Y on every component, + v in x."""
+        ikx = 1j * self.kx[:, None, None]
+        m = ikx * (c @ self.Y.T)
+        m[0] = m[0] + c[1]
+        return m
+
     # -------------------------------------------------------- per-mode Stokes
     def assemble_mode(self, kx, kz, lam):
         """Dense coupled Chebyshev-tau matrix for one mode (kx,kz) != (0,0).
@@ -183,6 +210,8 @@ class Couette:
         momentum for n = 0..N-2; no-slip at y = +1 and y = -1 for u, v, w;
         continuity i kx u + Dv + i kz w = 0 for n = 0..N. ``lam`` multiplies
         the identity in the momentum rows (lam = 1/dt + nu (kx^2 + kz^2)).
+        With laminar advection in L the momentum rows also carry i kx Y on
+        every component and v in the x-momentum rows.
         """
         N = self.N
         n1 = N + 1
@@ -194,6 +223,10 @@ class Couette:
         for comp in range(3):
             for n in range(N - 1):
                 A[r, comp * n1:(comp + 1) * n1] = H[n]
+                if self.lam_adv:
+                    A[r, comp * n1:(comp + 1) * n1] += 1j * kx * self.Y[n]
+                    if comp == 0:
+                        A[r, n1 + n] += 1.0
                 if comp == 0:
                     A[r, 3 * n1 + n] = 1j * kx
                 elif comp == 1:
@@ -285,16 +318,22 @@ class Couette:
         return out
 
     # ---------------------------------------------------------------- the maps
+    def _rhs(self, cs, n):
+        """u/dt + N(u) (+ M u with laminar advection in L) from the nonlinear part n."""
+        f = cs / self.dt + n
+        if self.lam_adv:
+            f = f + self.laminar_advection(cs)
+        return f
+
     def step(self, c):
         """G(u) = B_dt(u) - u (Eqs. befe, Gstokes) for the spectral state c."""
         cs = self.sym(c)
-        f = cs / self.dt + self.nonlinear(cs)
-        return self.sym(self.solve(f) - cs)
+        return self.sym(self.solve(self._rhs(cs, self.nonlinear(cs))) - cs)
 
     def befe(self, c):
         """B_dt(u) itself (Eq. befe)."""
         cs = self.sym(c)
-        return self.sym(self.solve(cs / self.dt + self.nonlinear(cs)))
+        return self.sym(self.solve(self._rhs(cs, self.nonlinear(cs))))
 
     def base(self, c):
         """Total fields U_tot, Omega_tot on the grid: the linearisation point."""
@@ -303,7 +342,7 @@ class Couette:
     def jvp(self, base_fields, dc):
         """Tangent G_U du: N -> N_U with homogeneous boundary data (Sec. 2)."""
         ds = self.sym(dc)
-        f = ds / self.dt + self.nonlinear_tangent(base_fields, ds)
+        f = self._rhs(ds, self.nonlinear_tangent(base_fields, ds))
         return self.sym(self.solve(f) - ds)
 
     def jvp_fd(self, c, dc, eps=None, g0=None):
@@ -338,6 +377,8 @@ class Couette:
 
     def vjp(self, base_fields, r):
         """Adjoint G_U^* r with respect to the weighted inner product <.,.>."""
+        if self.lam_adv:
+            raise NotImplementedError("the adjoint is defined for the Stokes step only")
         W = self.wz[None, None, :, None]
         rw = self.sym(r * W)
         # J = sym o S o (sym/dt + M o sym) - sym, M = to_spec o prod o to_phys
