@@ -59,6 +59,9 @@ def parse():
                    help="pipe flow, Re 2500, Nr 64, m<=24, |k|<=24: tangent throughput and traveling-wave Newton")
     p.add_argument("--config4", action="store_true",
                    help="96x97x96, Re 1000, doubled box: adjoint gradient check and Newton-hookstep with J^T F")
+    p.add_argument("--lamadv", action="store_true",
+                   help="laminar advection folded into L vs the Stokes step: Krylov actions, Newton time, "
+                        "tangent throughput")
     return p.parse_args()
 
 
@@ -619,6 +622,93 @@ def run_config3(args):
     print(json.dumps(out))
 
 
+def run_lamadv(args):
+    """Laminar advection folded into L (Sec. 3.6, the closing proposal) against the Stokes
+    step: Krylov actions of one linear solve at fixed states, Newton-GMRES-hookstep to
+    |F| < 1e-10 from perturbed-laminar guesses, and the tangent throughput at 48x65x48."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1804_05087_gb300 as sp
+    import seeded_inputs as si
+
+    def context(grid, re, lam_adv, max_batch=1):
+        nx, ny, nz = grid
+        ctx = sp.Context(sp.Config(nx, ny, nz, lx=LX, lz=LZ, re=re, dt=DT, prec=sp.SP_MIXED,
+                                   max_batch=max_batch, lam_adv=lam_adv))
+        return ctx
+
+    def seeded(ctx, grid, seed, amp):
+        a, b, c = si.couette_random_coeffs(seed, *grid)
+        U = ctx.zeros()
+        return ctx.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], amp, U)
+
+    first_solve, newton = [], []
+    for grid, re in (((16, 33, 16), 400.0), ((48, 35, 48), 380.0), ((32, 33, 32), 1000.0)):
+        g = "x".join(map(str, grid))
+        for lam_adv in (0, 1):
+            ctx = context(grid, re, lam_adv)
+            ctx.sp_autotune(1)
+            # one Newton step: the Krylov dimension GMRES needs for eta = 1e-3 at the guess
+            for amp in (0.1, 0.3):
+                U = seeded(ctx, grid, 1000, amp)
+                rep = ctx.sp_newton_gmres(U, max_newton=1, max_krylov=args.krylov, tol=1e-30)
+                first_solve.append({"grid": g, "re": re, "amplitude": amp, "lam_adv": lam_adv,
+                                    "actions": rep["total_jvps"]})
+            U = seeded(ctx, grid, 1000, 0.1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = ctx.sp_newton_gmres(U, max_newton=30, max_krylov=args.krylov, tol=1e-10)
+            torch.cuda.synchronize()
+            newton.append({"grid": g, "re": re, "lam_adv": lam_adv, "converged": rep["converged"],
+                           "newton_iters": rep["newton_iters"], "actions": rep["total_jvps"],
+                           "norm_F": rep["norm_F"], "wall_s": time.perf_counter() - t0})
+            ctx.close()
+
+    # tangent throughput with the complex per-mode operators (48x65x48, 256 directions)
+    grid, nd = (NX, NY, NZ), args.ndir
+    thr = {}
+    for lam_adv in (0, 1):
+        ctx = context(grid, RE, lam_adv, max_batch=nd)
+        U = seeded(ctx, grid, BASE_SEED, 0.1)
+        D = ctx.zeros(nd)
+        for i in range(nd):
+            D[i].copy_(seeded(ctx, grid, DIR_SEED0 + i, 1.0))
+        OUT = ctx.zeros(nd)
+        tune = ctx.sp_autotune(nd)
+        for _ in range(max(args.warmup, 3)):
+            ctx.sp_set_base(U)
+            ctx.sp_jvp(D, OUT)
+        torch.cuda.synchronize()
+        ctx.sp_trace_enable(True)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            ctx.sp_set_base(U)
+            ctx.sp_jvp(D, OUT)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        tr = ctx.sp_trace_read()
+        ctx.sp_trace_enable(False)
+        solve_ms = tr["k_solve"][0] / tr["k_solve"][1]
+        n = NY - 1
+        ent = 2 * (n - 1) * NY if lam_adv else op_entries() // 2
+        flops = nd * n_unique() * (ent * 8 + (n - 1) * 8 + NY * 16)
+        thr["lam_adv" if lam_adv else "stokes"] = {
+            "jvp_per_s": nd * args.steps / (ms * 1e-3), "k_solve_ms": solve_ms,
+            "k_solve_tflops": flops / (solve_ms * 1e-3) / 1e12, "tile": tune["tangent"],
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in tr.items()}}
+        ctx.close()
+    out = {"metric": "Krylov actions and time to |F|<1e-10: laminar advection in L vs the Stokes step",
+           "unit": "actions", "higher_is_better": False,
+           "config": {"workload": "plane Couette, dt=100, seed 1000 perturbed-laminar guesses; tangent "
+                                  f"throughput {NX}x{NY}x{NZ} Re {RE} {nd} directions, mixed",
+                      "max_krylov": args.krylov, "eta": 1e-3},
+           "first_solve": first_solve, "newton": newton, "throughput": thr}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -635,6 +725,8 @@ def main():
         return run_spectra(args)
     if args.config4:
         return run_config4(args)
+    if args.lamadv:
+        return run_lamadv(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:

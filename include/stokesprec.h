@@ -71,6 +71,14 @@ typedef struct {
   int prec;         /* sp_prec: precision of the tangent (sp_jvp, sp_vjp)    */
   int max_batch;    /* largest n_dir a single internal pass handles (>= 1);
                        larger batches are processed in passes of this size   */
+  int lam_adv;      /* 0: the Stokes step (Eq. befe). 1: laminar advection in L
+                       (Sec. 3.6, the closing proposal): M u = y du/dx + v e_x
+                       moves from N into the implicit operator, so one step solves
+                       (1/dt - nu lap + M) u' + grad p = u/dt + N(u) + M u.
+                       Same fixed points; per mode the solve becomes complex and
+                       couples both Chebyshev parities. With 1, sp_vjp,
+                       sp_vjp_euclid, the gradient hookstep and groups return
+                       SP_EINVAL (they are defined for the Stokes step). */
 } sp_config;
 
 /* ---- lifetime ----------------------------------------------------------- */

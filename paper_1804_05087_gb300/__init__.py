@@ -35,7 +35,8 @@ class SpError(RuntimeError):
 class _Config(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("lx", ctypes.c_double), ("lz", ctypes.c_double), ("re", ctypes.c_double),
-                ("dt", ctypes.c_double), ("prec", ctypes.c_int), ("max_batch", ctypes.c_int)]
+                ("dt", ctypes.c_double), ("prec", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("lam_adv", ctypes.c_int)]
 
 
 class _PipeConfig(ctypes.Structure):
@@ -139,6 +140,7 @@ class Config:
     dt: float = 100.0
     prec: int = SP_FP64
     max_batch: int = 1
+    lam_adv: int = 0
 
 
 @dataclass
@@ -181,7 +183,8 @@ class Context:
                             cfg.prec, cfg.max_batch)
             st = _lib.sp_pipe_create(ctypes.byref(c), ctypes.byref(h))
         else:
-            c = _Config(cfg.nx, cfg.ny, cfg.nz, cfg.lx, cfg.lz, cfg.re, cfg.dt, cfg.prec, cfg.max_batch)
+            c = _Config(cfg.nx, cfg.ny, cfg.nz, cfg.lx, cfg.lz, cfg.re, cfg.dt, cfg.prec, cfg.max_batch,
+                        int(cfg.lam_adv))
             st = _lib.sp_create(ctypes.byref(c), ctypes.byref(h))
         if st != 0:
             raise SpError(st, _lib.sp_last_error(None).decode())
@@ -396,7 +399,8 @@ class Group:
 
     def __init__(self, cfgs):
         cfgs = list(cfgs)
-        arr = (_Config * len(cfgs))(*[_Config(c.nx, c.ny, c.nz, c.lx, c.lz, c.re, c.dt, c.prec, 1) for c in cfgs])
+        arr = (_Config * len(cfgs))(*[_Config(c.nx, c.ny, c.nz, c.lx, c.lz, c.re, c.dt, c.prec, 1, int(c.lam_adv))
+                                       for c in cfgs])
         h = ctypes.c_void_p()
         st = _lib.sp_group_create(arr, len(cfgs), ctypes.byref(h))
         if st != 0:

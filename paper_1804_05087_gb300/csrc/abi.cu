@@ -130,6 +130,7 @@ extern "C" sp_status sp_create(const sp_config* cfg, sp_ctx** out) {
   if (!(cfg->lx > 0) || !(cfg->lz > 0) || !(cfg->re > 0) || !(cfg->dt > 0)) return bail(SP_EINVAL, "params");
   if (cfg->prec != SP_FP64 && cfg->prec != SP_MIXED) return bail(SP_EINVAL, "prec");
   if (cfg->max_batch < 1) return bail(SP_EINVAL, "max_batch");
+  if (cfg->lam_adv != 0 && cfg->lam_adv != 1) return bail(SP_EINVAL, "lam_adv");
   c->nx = cfg->nx; c->ny = cfg->ny; c->nz = cfg->nz;
   c->N = cfg->ny - 1;
   c->NH = c->N / 2 + 1;
@@ -454,6 +455,7 @@ static sp_status vjp_impl(sp_ctx* c, const double* r, double* JTr, int n_dir, bo
                           const char* who) {
   if (!c || !r || !JTr || n_dir < 0 || r == JTr) return sp_fail(c, SP_EINVAL, std::string(who) + ": bad arguments");
   if (c->geom != 0) return sp_fail(c, SP_EINVAL, std::string(who) + ": the adjoint is built for plane Couette only");
+  if (c->cfg.lam_adv) return sp_fail(c, SP_EINVAL, std::string(who) + ": the adjoint is built for the Stokes step only");
   if (!c->has_base) return sp_fail(c, SP_EINVAL, std::string(who) + ": call sp_set_base first");
   const bool f32 = c->cfg.prec == SP_MIXED;
   for (int d0 = 0; d0 < n_dir; d0 += c->cfg.max_batch) {
@@ -859,6 +861,8 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   if (!c || !U || !o) return sp_fail(c, SP_EINVAL, "sp_newton_gmres: bad arguments");
   if (o->use_gradient && c->geom != 0)
     return sp_fail(c, SP_EINVAL, "sp_newton_gmres: use_gradient needs the adjoint (plane Couette only)");
+  if (o->use_gradient && c->cfg.lam_adv)
+    return sp_fail(c, SP_EINVAL, "sp_newton_gmres: use_gradient needs the adjoint of the Stokes step (lam_adv = 0)");
   if (o->krylov == 1) {
     if (o->use_gradient || o->int_steps > 1)
       return sp_fail(c, SP_EINVAL, "sp_newton_gmres: BiCGSTAB(l) takes single-step actions without use_gradient");

@@ -13,6 +13,9 @@
 //   k_solve: per Fourier mode, values -> Chebyshev coefficients, the
 //            right-hand side u/dt + N, the Chebyshev-tau Stokes solve through
 //            the precomputed per-mode operators, and G = u_new - u.
+//            With laminar advection in L (Sec. 3.6) the right-hand side gains
+//            M u = y du/dx + v e_x and the operators are the complex ones of
+//            that system (template flag LA).
 // T is the real type of the transforms and the product (double or float);
 // the solve and everything after it are double.
 #include <algorithm>
@@ -434,6 +437,7 @@ struct SolveArgs {
   const float* Cfh_f;
   int n_unique, Mm, MX, MZ, Kx, NY, N, NH;
   int cv, rb0, rb1, off_v0, off_v1, off_h0, off_h1, op_stride;
+  int off_vc, off_hc;  // complex operators of the laminar-advection variant
   double alpha, beta, inv_dt;
 };
 
@@ -453,7 +457,8 @@ __device__ __forceinline__ void unique_to_mode(int u, int Kx, int MZ, int* pos, 
 // du : [dir][3][Mm][NY] complex double; out: same layout (G = u_new - u)
 // (bx, by): tile of solved modes, direction
 // TM: solved modes per block (any block size works; every mode's arithmetic is the same)
-template <typename T, int TM>
+// LA: laminar advection in L (right-hand side + M du, complex operators)
+template <typename T, int TM, bool LA>
 __device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const double2* __restrict__ du,
                                            double2* __restrict__ out, const SolveArgs& a, int bx, int by) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -553,6 +558,22 @@ __device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const 
     }
     const double2 d = sdu[(c * TM + t) * NY + n];
     double2 f = make_double2((double)acc.x + d.x * a.inv_dt, (double)acc.y + d.y * a.inv_dt);
+    if constexpr (LA) {
+      // + M du on the momentum rows: i kx (Y du)_n, and dv_n in the x-momentum rows
+      const double2* dc = sdu + (c * TM + t) * NY;
+      double2 yv;
+      if (n == 0) yv = make_double2(0.5 * dc[1].x, 0.5 * dc[1].y);
+      else if (n == 1) yv = make_double2(dc[0].x + 0.5 * dc[2].x, dc[0].y + 0.5 * dc[2].y);
+      else yv = make_double2(0.5 * (dc[n - 1].x + dc[n + 1].x), 0.5 * (dc[n - 1].y + dc[n + 1].y));
+      const double kx = s_kx[t];
+      f.x = fma(-kx, yv.y, f.x);
+      f.y = fma(kx, yv.x, f.y);
+      if (c == 0) {
+        const double2 dv = sdu[(TM + t) * NY + n];
+        f.x += dv.x;
+        f.y += dv.y;
+      }
+    }
     if (s_pos[t] == 0 && s_iz[t] == 0) f.y = 0.0;
     sf[(c * TM + t) * NR + n] = f;
   }
@@ -606,6 +627,46 @@ __device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const 
   // column-major operator (coalesced). The mean-mode test is hoisted out of the
   // loops so that no predicated-off double FMA occupies the FP64 pipe.
   const int nv0 = N / 2 + 1;  // even unknowns
+  if constexpr (LA) {
+    // D1: v = V' g, one complex row per thread (consecutive rows: coalesced columns)
+    for (int idx = threadIdx.x; idx < TM * NY; idx += blockDim.x) {
+      const int t = idx / NY, n = idx - t * NY;
+      if (s_u[t] >= a.n_unique || (s_pos[t] == 0 && s_iz[t] == 0)) continue;
+      const double2* V = reinterpret_cast<const double2*>(a.ops + (size_t)s_u[t] * a.op_stride + a.off_vc) + n;
+      sv[t * NY + n] = cdot4(V, NY, srv + t * 2 * a.cv, NR);
+    }
+    __syncthreads();
+    // D1b: right-hand side of b, f_b + (kz/k) v on the momentum rows
+    for (int idx = threadIdx.x; idx < TM * NR; idx += blockDim.x) {
+      const int t = idx / NR, n = idx - t * NR;
+      if (s_u[t] >= a.n_unique || (s_pos[t] == 0 && s_iz[t] == 0)) continue;
+      const double s = s_kz[t] * s_ik[t];
+      const double2 v = sv[t * NY + n];
+      double2 fb = sfb[t * NR + n];
+      fb.x = fma(s, v.x, fb.x);
+      fb.y = fma(s, v.y, fb.y);
+      sfb[t * NR + n] = fb;
+    }
+    __syncthreads();
+    // D2: b = H' (f_b + (kz/k) v); the mean mode uses the real Helmholtz operators
+    for (int idx = threadIdx.x; idx < TM * NY; idx += blockDim.x) {
+      const int t = idx / NY, k = idx - t * NY;
+      if (s_u[t] >= a.n_unique) continue;
+      const double* op = a.ops + (size_t)s_u[t] * a.op_stride;
+      if (s_pos[t] == 0 && s_iz[t] == 0) {
+        const int Q = k < nv0 ? 0 : 1, row = Q == 0 ? k : k - nv0, n = 2 * row + Q;
+        const int nrow = Q == 0 ? nv0 : NY - nv0;
+        const int rb = Q == 0 ? a.rb0 : a.rb1;
+        const double* H = op + (Q == 0 ? a.off_h0 : a.off_h1) + row;
+        sb[t * NY + n] = dot4(H, nrow, sfb + t * NR + Q, 2, rb);
+        sv[t * NY + n] = dot4(H, nrow, sfw + t * NR + Q, 2, rb);
+        continue;
+      }
+      const double2* H = reinterpret_cast<const double2*>(op + a.off_hc) + k;
+      sb[t * NY + k] = cdot4(H, NY, sfb + t * NR, NR);
+    }
+    __syncthreads();
+  } else {
   for (int idx = threadIdx.x; idx < TM * NY; idx += blockDim.x) {
     const int t = idx / NY, k = idx - t * NY;
     if (s_u[t] >= a.n_unique) continue;
@@ -627,6 +688,7 @@ __device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const 
     sv[t * NY + n] = dot4(V, nrow, srv + (t * 2 + Q) * a.cv, 1, rb);
   }
   __syncthreads();
+  }
   // (D v)_n = (2/c_n) sum_{p > n, p + n odd} p v_p: one suffix sum per (mode, parity),
   // kept in sfb (free after phase D) as S_n = sum_{p >= n, p = n mod 2} p v_p
   double2* ssum = sfb;
@@ -681,10 +743,10 @@ __device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const 
   }
 }
 
-template <typename T, int TM, int THREADS>
+template <typename T, int TM, int THREADS, bool LA>
 __global__ void __launch_bounds__(THREADS) k_solve(const C2<T>* __restrict__ in3, const double2* __restrict__ du,
                                                    double2* __restrict__ out, SolveArgs a) {
-  solve_body<T, TM>(in3, du, out, a, blockIdx.x, blockIdx.y);
+  solve_body<T, TM, LA>(in3, du, out, a, blockIdx.x, blockIdx.y);
 }
 
 
@@ -1327,7 +1389,7 @@ __global__ void __launch_bounds__(kThreadsSolveGrp) k_solve_grp(const double* __
   __shared__ GSolve r;
   if (threadIdx.x == 0) r = recs[i];
   __syncthreads();
-  solve_body<T, kTileSolve>(reinterpret_cast<const C2<T>*>(r.in3), reinterpret_cast<const double2*>(du_base + r.off),
+  solve_body<T, kTileSolve, false>(reinterpret_cast<const C2<T>*>(r.in3), reinterpret_cast<const double2*>(du_base + r.off),
                 reinterpret_cast<double2*>(out_base + r.off), r.a, blockIdx.x - first[i], 0);
 }
 
@@ -1498,6 +1560,7 @@ static SolveArgs solve_args(const sp_ctx* c) {
   a.cv = c->cv; a.rb0 = c->rb0; a.rb1 = c->rb1;
   a.off_v0 = c->off_v0; a.off_v1 = c->off_v1; a.off_h0 = c->off_h0; a.off_h1 = c->off_h1;
   a.op_stride = c->op_stride;
+  a.off_vc = c->off_vc; a.off_hc = c->off_hc;
   a.alpha = c->alpha; a.beta = c->beta; a.inv_dt = 1.0 / c->dt;
   return a;
 }
@@ -1521,12 +1584,12 @@ static cudaError_t launch_solve_t(const sp_ctx* c, const SolveArgs& a, const voi
                                   int n_dir, int threads, cudaStream_t st) {
   const size_t sm = solve_smem(c, (int)sizeof(T), TM);
   if (sm + 40 * TM + 64 > (size_t)232448 || threads > MAXT) return cudaErrorInvalidConfiguration;  // does not fit
-  cudaError_t e = cudaFuncSetAttribute(k_solve<T, TM, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  auto kern = c->cfg.lam_adv ? k_solve<T, TM, MAXT, true> : k_solve<T, TM, MAXT, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 grid((c->n_unique + TM - 1) / TM, n_dir);
-  k_solve<T, TM, MAXT><<<grid, threads, sm, st>>>(reinterpret_cast<const C2<T>*>(in3),
-                                                  reinterpret_cast<const double2*>(du),
-                                                  reinterpret_cast<double2*>(out), a);
+  kern<<<grid, threads, sm, st>>>(reinterpret_cast<const C2<T>*>(in3), reinterpret_cast<const double2*>(du),
+                                  reinterpret_cast<double2*>(out), a);
   return cudaGetLastError();
 }
 

@@ -26,7 +26,22 @@
 // form g with one O(N) suffix sum.
 // b uses the restricted inverse H_Q of the Dirichlet Helmholtz tau problem.
 // The mean mode (0,0) uses H_Q with k = 0 for u and w.
+//
+// Laminar advection in L (Sec. 3.6, the closing proposal): M u = y du/dx + v e_x
+// adds i kx Y (Y: multiplication by y on Chebyshev coefficients) to every
+// momentum row and v to the x-momentum rows. In the rotated components
+//   (lam - nu D^2 + i kx Y) a~ - i (kx/k) v + k p = f~_a
+//   (lam - nu D^2 + i kx Y) v + D p            = f_v
+//   (lam - nu D^2 + i kx Y) b = f_b + (kz/k) v
+// Y couples the two parities and makes the system complex, but the elimination
+// above goes through unchanged (the new terms are operator terms, not
+// right-hand sides): v = V' g with the same reduced right-hand side g, now one
+// complex operator over both parities, and b = H' (f_b + (kz/k) v) with the
+// complex Helmholtz operator H'. The mean mode keeps the real H_Q (kx = 0 and
+// v = 0 there).
+#include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <thread>
 
@@ -54,43 +69,48 @@ bool make_fft_plan(int n, FftPlan* p) {
   return m == 1 && p->nst <= 12;
 }
 
-// LU with partial pivoting, in place, row-major n x n. Returns false if singular.
-bool lu_factor(std::vector<double>& A, int n, std::vector<int>& piv) {
+using cplx = std::complex<double>;
+
+// LU with partial pivoting, in place, row-major n x n (S = double or complex).
+// Returns false if singular.
+template <typename S>
+bool lu_factor(std::vector<S>& A, int n, std::vector<int>& piv) {
   piv.resize(n);
   for (int k = 0; k < n; ++k) {
     int p = k;
-    double best = std::fabs(A[(size_t)k * n + k]);
+    double best = std::abs(A[(size_t)k * n + k]);
     for (int i = k + 1; i < n; ++i) {
-      double v = std::fabs(A[(size_t)i * n + k]);
+      double v = std::abs(A[(size_t)i * n + k]);
       if (v > best) { best = v; p = i; }
     }
     if (best == 0.0) return false;
     piv[k] = p;
     if (p != k)
       for (int j = 0; j < n; ++j) std::swap(A[(size_t)k * n + j], A[(size_t)p * n + j]);
-    double inv = 1.0 / A[(size_t)k * n + k];
+    S inv = S(1.0) / A[(size_t)k * n + k];
     for (int i = k + 1; i < n; ++i) {
-      double l = A[(size_t)i * n + k] * inv;
+      S l = A[(size_t)i * n + k] * inv;
       A[(size_t)i * n + k] = l;
-      if (l != 0.0)
+      if (l != S(0.0))
         for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
     }
   }
   return true;
 }
 
-void lu_solve(const std::vector<double>& LU, int n, const std::vector<int>& piv, double* b) {
+template <typename S>
+void lu_solve(const std::vector<S>& LU, int n, const std::vector<int>& piv, S* b) {
   for (int k = 0; k < n; ++k) {
     int p = piv[k];
     if (p != k) std::swap(b[k], b[p]);
   }
   for (int i = 0; i < n; ++i) {
-    double s = b[i];
+    S s = b[i];
     for (int j = 0; j < i; ++j) s -= LU[(size_t)i * n + j] * b[j];
     b[i] = s;
   }
   for (int i = n - 1; i >= 0; --i) {
-    double s = b[i];
+    S s = b[i];
     for (int j = i + 1; j < n; ++j) s -= LU[(size_t)i * n + j] * b[j];
     b[i] = s / LU[(size_t)i * n + i];
   }
@@ -99,8 +119,15 @@ void lu_solve(const std::vector<double>& LU, int n, const std::vector<int>& piv,
 struct ChebOps {
   int N;
   std::vector<double> D, D2;  // (N+1)^2 row-major: (Du)_n = sum_m D[n][m] u_m
+  std::vector<double> Y;      // multiplication by y: y T_0 = T_1, y T_m = (T_(m+1) + T_(m-1))/2
   explicit ChebOps(int N_) : N(N_) {
     int n1 = N + 1;
+    Y.assign((size_t)n1 * n1, 0.0);
+    Y[(size_t)1 * n1 + 0] = 1.0;
+    for (int m = 1; m < n1; ++m) {
+      Y[(size_t)(m - 1) * n1 + m] += 0.5;
+      if (m + 1 < n1) Y[(size_t)(m + 1) * n1 + m] += 0.5;
+    }
     D.assign((size_t)n1 * n1, 0.0);
     for (int n = 0; n < n1; ++n)
       for (int p = n + 1; p < n1; ++p)
@@ -205,6 +232,92 @@ bool build_hop(const ChebOps& C, int Q, double lam, double nu, double* out) {
   return true;
 }
 
+// V': the v unknowns n = 0..N (rows) against the reduced right-hand side g in the
+// parity order of the kernel (column j < N/2: row 2j; j >= N/2: row 2(j - N/2) + 1),
+// complex, column-major, (re, im) pairs. Laminar advection in L (see the top).
+bool build_vop_la(const ChebOps& C, double kx, double k, double lam, double nu, double* out) {
+  const int N = C.N, n1 = N + 1, nt = 3 * n1;
+  const cplx ikx(0.0, kx);
+  auto col_v = [&](int n) { return n; };
+  auto col_a = [&](int n) { return n1 + n; };
+  auto col_p = [&](int n) { return 2 * n1 + n; };
+  std::vector<cplx> A((size_t)nt * nt, cplx(0.0));
+  std::vector<int> vrow(n1, -1);
+  int r = 0;
+  auto op = [&](int n, int m) {
+    return cplx((n == m ? lam : 0.0) - nu * C.D2[(size_t)n * n1 + m]) + ikx * C.Y[(size_t)n * n1 + m];
+  };
+  for (int n = 0; n <= N - 2; ++n) {  // v-momentum
+    for (int m = 0; m < n1; ++m) {
+      A[(size_t)r * nt + col_v(m)] = op(n, m);
+      A[(size_t)r * nt + col_p(m)] = C.D[(size_t)n * n1 + m];
+    }
+    vrow[n] = r++;
+  }
+  for (int n = 0; n <= N - 2; ++n) {  // a~-momentum
+    for (int m = 0; m < n1; ++m) A[(size_t)r * nt + col_a(m)] = op(n, m);
+    A[(size_t)r * nt + col_v(n)] += cplx(0.0, -kx / k);
+    A[(size_t)r * nt + col_p(n)] += k;
+    ++r;
+  }
+  for (int n = 0; n <= N; ++n) {  // continuity: -k a~_n + (D v)_n = 0
+    A[(size_t)r * nt + col_a(n)] = -k;
+    for (int m = 0; m < n1; ++m) A[(size_t)r * nt + col_v(m)] = C.D[(size_t)n * n1 + m];
+    ++r;
+  }
+  for (int m = 0; m < n1; ++m) {  // v(+1) = v(-1) = a(+1) = a(-1) = 0
+    const double sg = (m & 1) ? -1.0 : 1.0;
+    A[(size_t)r * nt + col_v(m)] = 1.0;
+    A[(size_t)(r + 1) * nt + col_v(m)] = sg;
+    A[(size_t)(r + 2) * nt + col_a(m)] = 1.0;
+    A[(size_t)(r + 3) * nt + col_a(m)] = sg;
+  }
+  r += 4;
+  if (r != nt) return false;
+  std::vector<int> piv;
+  if (!lu_factor(A, nt, piv)) return false;
+  const int cv = N / 2;
+  std::vector<cplx> b(nt);
+  for (int j = 0; j < N - 1; ++j) {
+    const int n = j < cv ? 2 * j : 2 * (j - cv) + 1;
+    std::fill(b.begin(), b.end(), cplx(0.0));
+    b[vrow[n]] = 1.0;
+    lu_solve(A, nt, piv, b.data());
+    for (int i = 0; i < n1; ++i) {
+      out[((size_t)j * n1 + i) * 2 + 0] = b[col_v(i)].real();
+      out[((size_t)j * n1 + i) * 2 + 1] = b[col_v(i)].imag();
+    }
+  }
+  return true;
+}
+
+// H': the Dirichlet problem (lam - nu D^2 + i kx Y) b = r on rows 0..N-2, b(+-1) = 0;
+// rows = unknowns n = 0..N, columns = momentum rows 0..N-2, complex, column-major.
+bool build_hop_la(const ChebOps& C, double kx, double lam, double nu, double* out) {
+  const int N = C.N, n1 = N + 1;
+  std::vector<cplx> A((size_t)n1 * n1, cplx(0.0));
+  for (int n = 0; n <= N - 2; ++n)
+    for (int m = 0; m < n1; ++m)
+      A[(size_t)n * n1 + m] = cplx((n == m ? lam : 0.0) - nu * C.D2[(size_t)n * n1 + m], kx * C.Y[(size_t)n * n1 + m]);
+  for (int m = 0; m < n1; ++m) {
+    A[(size_t)(N - 1) * n1 + m] = 1.0;
+    A[(size_t)N * n1 + m] = (m & 1) ? -1.0 : 1.0;
+  }
+  std::vector<int> piv;
+  if (!lu_factor(A, n1, piv)) return false;
+  std::vector<cplx> b(n1);
+  for (int j = 0; j <= N - 2; ++j) {
+    std::fill(b.begin(), b.end(), cplx(0.0));
+    b[j] = 1.0;
+    lu_solve(A, n1, piv, b.data());
+    for (int i = 0; i < n1; ++i) {
+      out[((size_t)j * n1 + i) * 2 + 0] = b[i].real();
+      out[((size_t)j * n1 + i) * 2 + 1] = b[i].imag();
+    }
+  }
+  return true;
+}
+
 }  // namespace
 
 // unique mode u -> (pos, iz): positions 0..Kx keep every iz, negative ix skip iz = 0
@@ -260,6 +373,14 @@ sp_status sp_build_plan(sp_ctx* c) {
   c->off_h0 = c->off_v1 + c->nv1 * c->rb1;
   c->off_h1 = c->off_h0 + c->nv0 * c->rb0;
   c->op_stride = c->off_h1 + c->nv1 * c->rb1;
+  const bool la = c->cfg.lam_adv != 0;
+  if (la) {
+    // complex V' and H', (N - 1) columns of N + 1 rows each; the mean mode keeps H_Q
+    c->off_vc = 0;
+    c->off_hc = 2 * (N - 1) * n1;
+    c->op_stride = std::max(c->op_stride, 4 * (N - 1) * n1);
+    c->op_stride += c->op_stride & 1;  // 16-byte aligned complex columns
+  }
   std::vector<double> ops((size_t)c->n_unique * c->op_stride, 0.0);
   ChebOps C(N);
   int nthreads = (int)std::thread::hardware_concurrency();
@@ -276,12 +397,17 @@ sp_status sp_build_plan(sp_ctx* c) {
       double lam = 1.0 / c->dt + c->nu * k2;
       double* o = ops.data() + (size_t)u * c->op_stride;
       bool ok = true;
-      if (u != 0) {
-        ok = ok && build_vop(C, 0, k, lam, c->nu, o + c->off_v0);
-        ok = ok && build_vop(C, 1, k, lam, c->nu, o + c->off_v1);
+      if (la && u != 0) {
+        ok = ok && build_vop_la(C, kx, k, lam, c->nu, o + c->off_vc);
+        ok = ok && build_hop_la(C, kx, lam, c->nu, o + c->off_hc);
+      } else {
+        if (u != 0) {
+          ok = ok && build_vop(C, 0, k, lam, c->nu, o + c->off_v0);
+          ok = ok && build_vop(C, 1, k, lam, c->nu, o + c->off_v1);
+        }
+        ok = ok && build_hop(C, 0, lam, c->nu, o + c->off_h0);
+        ok = ok && build_hop(C, 1, lam, c->nu, o + c->off_h1);
       }
-      ok = ok && build_hop(C, 0, lam, c->nu, o + c->off_h0);
-      ok = ok && build_hop(C, 1, lam, c->nu, o + c->off_h1);
       if (!ok) bad[tid] = 1;
     }
   };

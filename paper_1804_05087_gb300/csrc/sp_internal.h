@@ -69,6 +69,9 @@ struct sp_ctx {
   int nv0 = 0, nv1 = 0, cv = 0;  // rows of V0 / V1 (and H0 / H1); cv = N/2: RHS stride
   int rb0 = 0, rb1 = 0;          // columns of V0, H0 / V1, H1: momentum rows of each parity
   int off_v0 = 0, off_v1 = 0, off_h0 = 0, off_h1 = 0, op_stride = 0;
+  // laminar advection in L (cfg.lam_adv): complex V' and H' per mode, (N - 1) columns of
+  // N + 1 complex rows, column-major (the mean mode keeps H0 / H1)
+  int off_vc = 0, off_hc = 0;
 
   // device tables
   double *Th = nullptr, *TDh = nullptr, *Cfh = nullptr;

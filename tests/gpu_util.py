@@ -10,7 +10,7 @@ def make(nx, ny, nz, prec=0, max_batch=1, **kw):
     import paper_1804_05087_gb300 as sp
     cfg = sp.Config(nx, ny, nz, prec=prec, max_batch=max_batch, **kw)
     ctx = sp.Context(cfg)
-    orc = Couette(nx, ny, nz, lx=cfg.lx, lz=cfg.lz, re=cfg.re, dt=cfg.dt)
+    orc = Couette(nx, ny, nz, lx=cfg.lx, lz=cfg.lz, re=cfg.re, dt=cfg.dt, lam_adv=bool(cfg.lam_adv))
     return ctx, orc
 
 
