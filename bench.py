@@ -32,6 +32,7 @@ NX, NY, NZ = 48, 65, 48
 RE, DT = 400.0, 100.0
 LX, LZ = 2 * math.pi / 1.14, 2 * math.pi / 2.5
 BASE_SEED, DIR_SEED0 = 1001, 2000
+LAM_ADV = False  # the throughput run with laminar advection in L (--lam-adv)
 METRIC = "JVPs/s (BEFE step+tangent) at 48x65x48"
 
 
@@ -59,6 +60,8 @@ def parse():
                    help="pipe flow, Re 2500, Nr 64, m<=24, |k|<=24: tangent throughput and traveling-wave Newton")
     p.add_argument("--config4", action="store_true",
                    help="96x97x96, Re 1000, doubled box: adjoint gradient check and Newton-hookstep with J^T F")
+    p.add_argument("--lam-adv", action="store_true",
+                   help="the default throughput run with laminar advection folded into L")
     p.add_argument("--lamadv", action="store_true",
                    help="laminar advection folded into L vs the Stokes step: Krylov actions, Newton time, "
                         "tangent throughput")
@@ -91,7 +94,8 @@ def kernel_bytes(stage, n_dir, esz):
     if stage == "k_xz":
         return n_dir * 9 * ny * mm * esz + 6 * ny * NX * NZ * esz // 2
     if stage == "k_solve":
-        return n_dir * (3 * ny * mm * esz + 2 * state) + n_unique() * op_entries() * 8
+        ops = n_unique() * (la_op_entries() * 16 if LAM_ADV else op_entries() * 8)
+        return n_dir * (3 * ny * mm * esz + 2 * state) + ops
     return 0
 
 
@@ -100,6 +104,13 @@ def op_entries():
     n = NY - 1
     nv0, nv1, rb0, rb1 = n // 2 + 1, n // 2, n // 2, n // 2 - 1
     return 2 * (nv0 * rb0 + nv1 * rb1)
+
+
+def la_op_entries():
+    """Complex entries of the per-mode operators V' and H' with laminar advection in L
+    ((N - 1) columns of N + 1 rows each)."""
+    n = NY - 1
+    return 2 * (n - 1) * NY
 
 
 def kernel_flops(stage, n_dir):
@@ -119,7 +130,11 @@ def kernel_flops(stage, n_dir):
         # 4 flops per entry), the reduced right-hand side g (one complex FMA and one complex
         # update per momentum row) and the continuity/rotation epilogue (16 per point); the
         # Chebyshev transform (float in mixed mode) is excluded
+        # With laminar advection in L: complex operators on complex right-hand sides (8 flops
+        # per entry), plus the M du right-hand-side term and the v -> b coupling (10 per row).
         n = ny - 1
+        if LAM_ADV:
+            return n_dir * n_unique() * (la_op_entries() * 8 + (n - 1) * 18 + ny * 16)
         return n_dir * n_unique() * (op_entries() * 4 + (n - 1) * 8 + ny * 16)
     return 0
 
@@ -549,6 +564,28 @@ def run_spectra(args):
                    "stokes_100_max_imag": float(np.abs(st100.imag).max()),
                    "stokes_100_frac_real_within_0.2_of_-1": float(np.mean(np.abs(st100.real + 1) < 0.2)),
                    "int_r95": r95}
+    # laminar advection folded into L (Sec. 3.6): spectra of G^Stokes_100 and G'^Stokes_100 at
+    # laminar flow and at a seeded perturbed state (amplitude 0.1), on the same subspace S
+    import seeded_inputs as si
+    for re in (500.0, 1750.0):
+        la = {}
+        for lam_adv in (0, 1):
+            for amp in (0.0, 0.1):
+                ctx = sp.Context(sp.Config(nx, ny, nz, lx=LX, lz=LZ, re=re, dt=100.0, prec=sp.SP_FP64,
+                                           max_batch=256, lam_adv=lam_adv))
+                U = ctx.zeros()
+                if amp > 0:
+                    a_, b_, c_ = si.couette_random_coeffs(1000, nx, ny, nz)
+                    ctx.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a_, b_, c_)], amp, U)
+                ctx.sp_set_base(U)
+                J = dense_jacobian(ctx, 1)
+                ev = np.linalg.eigvals(Q.T @ J @ Q) * (1 + 100.0) / 100.0
+                dist = np.sort(np.abs(ev + 1.0))
+                la[f"{'lam_adv' if lam_adv else 'stokes'}_amp{amp}"] = {
+                    "max_imag": float(np.abs(ev.imag).max()), "max_dist_from_-1": float(dist[-1]),
+                    "r95_around_-1": float(dist[int(np.ceil(0.95 * len(dist))) - 1])}
+                ctx.close()
+        res[re]["laminar_advection_in_L"] = la
     a, b = res[500.0], res[1750.0]
     out = {"metric": "Jacobian spectra: model scalings (Sec. 3.3)", "config": {
         "workload": "laminar plane Couette flow, 12x17x12, box 2pi/1.14 x 2 x 2pi/2.5, FP64; G^Stokes_T for "
@@ -651,7 +688,7 @@ def run_lamadv(args):
             # one Newton step: the Krylov dimension GMRES needs for eta = 1e-3 at the guess
             for amp in (0.1, 0.3):
                 U = seeded(ctx, grid, 1000, amp)
-                rep = ctx.sp_newton_gmres(U, max_newton=1, max_krylov=args.krylov, tol=1e-30)
+                rep = ctx.sp_newton_gmres(U, max_newton=1, max_krylov=max(args.krylov, 1200), tol=1e-30)
                 first_solve.append({"grid": g, "re": re, "amplitude": amp, "lam_adv": lam_adv,
                                     "actions": rep["total_jvps"]})
             U = seeded(ctx, grid, 1000, 0.1)
@@ -693,8 +730,8 @@ def run_lamadv(args):
         ctx.sp_trace_enable(False)
         solve_ms = tr["k_solve"][0] / tr["k_solve"][1]
         n = NY - 1
-        ent = 2 * (n - 1) * NY if lam_adv else op_entries() // 2
-        flops = nd * n_unique() * (ent * 8 + (n - 1) * 8 + NY * 16)
+        flops = (nd * n_unique() * (la_op_entries() * 8 + (n - 1) * 18 + NY * 16) if lam_adv
+                 else nd * n_unique() * (op_entries() * 4 + (n - 1) * 8 + NY * 16))
         thr["lam_adv" if lam_adv else "stokes"] = {
             "jvp_per_s": nd * args.steps / (ms * 1e-3), "k_solve_ms": solve_ms,
             "k_solve_tflops": flops / (solve_ms * 1e-3) / 1e12, "tile": tune["tangent"],
@@ -740,8 +777,11 @@ def main():
 
     prec = sp.SP_MIXED if args.prec == "mixed" else sp.SP_FP64
     esz = 8 if args.prec == "mixed" else 16
+    global LAM_ADV
+    LAM_ADV = bool(args.lam_adv)
     nd = args.ndir
-    ctx = sp.Context(sp.Config(NX, NY, NZ, lx=LX, lz=LZ, re=RE, dt=DT, prec=prec, max_batch=nd))
+    ctx = sp.Context(sp.Config(NX, NY, NZ, lx=LX, lz=LZ, re=RE, dt=DT, prec=prec, max_batch=nd,
+                               lam_adv=1 if args.lam_adv else 0))
     # seeded inputs, built on the device by the library
     def seeded(seed, amp):
         a, b, c = si.couette_random_coeffs(seed, NX, NY, NZ)
@@ -855,6 +895,7 @@ def main():
                "config": {"workload": "plane Couette 48x65x48, Re=400, dt=100, box 2pi/1.14 x 2 x 2pi/2.5; "
                                       "per step: set_base + tangent on 256 seeded unit directions",
                           "grid": [NX, NY, NZ], "ndir_per_gpu": nd, "precision": args.prec,
+                          "laminar_advection_in_L": bool(args.lam_adv),
                           "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                           "solve_tile": {"tangent": list(tune["tangent"]), "step": list(tune["step"])}},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
