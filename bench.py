@@ -60,6 +60,8 @@ def parse():
                    help="pipe flow, Re 2500, Nr 64, m<=24, |k|<=24: tangent throughput and traveling-wave Newton")
     p.add_argument("--config4", action="store_true",
                    help="96x97x96, Re 1000, doubled box: adjoint gradient check and Newton-hookstep with J^T F")
+    p.add_argument("--eq", action="store_true",
+                   help="continuation from a nontrivial equilibrium (48x35x48, Re 400 -> 380): G^Stokes_T vs G^int_T")
     p.add_argument("--lam-adv", action="store_true",
                    help="the default throughput run with laminar advection folded into L")
     p.add_argument("--lamadv", action="store_true",
@@ -415,6 +417,30 @@ def run_config2(args):
     conv = summary(reps, time.perf_counter() - t0)
     conv["max_newton"], conv["max_krylov"] = 20, args.krylov
     out["to_convergence"] = conv
+    grp.close()
+    # laminar advection folded into L (Sec. 3.6): the same members and initial guesses
+    gla = sp.Group([sp.Config(*g, lx=LX, lz=LZ, re=re, dt=DT, prec=sp.SP_MIXED, lam_adv=1) for g, re in members])
+    U0 = gla.zeros()
+    for i, m in enumerate(gla.members):
+        seed_into(m, i, gla.member_view(U0, i))
+    for rep_i in range(2):
+        U = U0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ok, reps = gla.sp_group_newton_gmres(U, use_graphs=True, **budget)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    out["runs"]["group_graphs_lam_adv"] = summary(reps, wall)
+    U = U0.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ok, reps = gla.sp_group_newton_gmres(U, max_newton=20, max_krylov=args.krylov, tol=1e-10, eta=1e-3,
+                                         use_graphs=True)
+    torch.cuda.synchronize()
+    conv = summary(reps, time.perf_counter() - t0)
+    conv["max_newton"], conv["max_krylov"] = 20, args.krylov
+    out["to_convergence_lam_adv"] = conv
+    gla.close()
     print(json.dumps(out))
 
 
@@ -746,6 +772,77 @@ def run_lamadv(args):
     print(json.dumps(out))
 
 
+def find_equilibrium(sp, si, torch, grid=(48, 35, 48), re=400.0, seed=7123, amp=0.3):
+    """A nontrivial plane Couette equilibrium: Newton-GMRES-hookstep with laminar advection in
+    L from a seeded perturbed-laminar guess (modes |ix|, |iz| <= 1). From seed 7123 it reaches
+    a state with a spanwise-fundamental streak pair and a mean-flow correction (weighted norm
+    0.2243, energy input 1.43 times the laminar one) at 48 x 35 x 48, Re 400."""
+    ctx = sp.Context(sp.Config(*grid, lx=LX, lz=LZ, re=re, dt=DT, prec=sp.SP_MIXED, lam_adv=1))
+    a, b, c = si.couette_random_coeffs(seed, *grid, mmax=1)
+    U = ctx.zeros()
+    ctx.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], amp, U)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep = ctx.sp_newton_gmres(U, max_newton=40, max_krylov=300, tol=1e-10)
+    torch.cuda.synchronize()
+    rep["wall_s"] = time.perf_counter() - t0
+    rep["norm_U"] = math.sqrt(ctx.sp_inner(U, U)[0])
+    ctx.close()
+    return U, rep
+
+
+def run_eq(args):
+    """The Newton-performance experiment of Sec. 3.3 (figures on G^Stokes_T and G^int_T) from a
+    nontrivial equilibrium instead of laminar flow: the equilibrium at Re 400 (48 x 35 x 48, the
+    paper's box) is the initial guess at Re 380. G^Stokes_T = B_T - I for T = 1, 10, 100 (and
+    with laminar advection in L); G^int_T = (B_dt)^(T/dt) - I with the same BEFE step at
+    dt = 1/32 (the paper's dt; the explicit advection of this first-order step is unstable there
+    for the largest kx, so only short T converge) and at dt = 1/256 (stable). Timesteps =
+    residual steps + (actions x T/dt)."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1804_05087_gb300 as sp
+    import seeded_inputs as si
+    grid = (48, 35, 48)
+    U400, rep0 = find_equilibrium(sp, si, torch)
+    eq = {k: rep0[k] for k in ("converged", "newton_iters", "total_jvps", "norm_F", "wall_s", "norm_U")}
+    runs = []
+    cases = [("stokes", 100.0, None, 0, 30, 300), ("stokes", 10.0, None, 0, 30, 300), ("stokes", 1.0, None, 0, 30, 300),
+             ("stokes", 100.0, None, 1, 30, 300), ("int", 0.25, 1 / 32, 0, 30, 300),
+             ("int", 0.25, 1 / 256, 0, 12, 150), ("int", 1.0, 1 / 256, 0, 12, 150), ("int", 4.0, 1 / 256, 0, 8, 100)]
+    for kind, T, dti, la, max_newton, max_krylov in cases:
+        dt = T if kind == "stokes" else dti
+        ns = 1 if kind == "stokes" else int(round(T / dti))
+        ctx = sp.Context(sp.Config(*grid, lx=LX, lz=LZ, re=380.0, dt=dt, prec=sp.SP_MIXED, lam_adv=la))
+        U = U400.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = ctx.sp_newton_gmres(U, max_newton=max_newton, max_krylov=max_krylov, tol=1e-10, int_steps=ns)
+        torch.cuda.synchronize()
+        it = max(rep["newton_iters"], 1)
+        runs.append({"operator": "G^Stokes_T" if kind == "stokes" else "G^int_T", "T": T, "dt": dt,
+                     "laminar_advection_in_L": bool(la), "converged": rep["converged"],
+                     "newton_iters": rep["newton_iters"], "actions": rep["total_jvps"],
+                     "K_per_newton_step": rep["total_jvps"] / it,
+                     "timesteps": rep["total_steps"] + rep["total_jvps"] * ns,
+                     "wall_s": time.perf_counter() - t0, "norm_F": rep["norm_F"],
+                     "norm_U": math.sqrt(ctx.sp_inner(U, U)[0]), "caps": [max_newton, max_krylov]})
+        ctx.close()
+    out = {"metric": "timesteps and time to |F|<1e-10, continuation from an equilibrium (Re 400 -> 380)",
+           "unit": "timesteps", "higher_is_better": False,
+           "config": {"workload": "plane Couette 48x35x48, box 2pi/1.14 x 2 x 2pi/2.5, mixed tangent; initial "
+                                  "guess: the equilibrium at Re 400 found from seed 7123; target Re 380", "eta": 1e-3},
+           "equilibrium_search": eq, "runs": runs}
+    st = [r for r in runs if r["operator"] == "G^Stokes_T" and r["T"] == 100.0 and not r["laminar_advection_in_L"]][0]
+    conv_int = [r for r in runs if r["operator"] == "G^int_T" and r["converged"]]
+    if conv_int and st["converged"]:
+        fastest = min(conv_int, key=lambda r: r["timesteps"])
+        out["ratio_timesteps_int_over_stokes"] = fastest["timesteps"] / st["timesteps"]
+        out["ratio_time_int_over_stokes"] = fastest["wall_s"] / st["wall_s"]
+        out["fastest_int"] = {"T": fastest["T"], "dt": fastest["dt"]}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -764,6 +861,8 @@ def main():
         return run_config4(args)
     if args.lamadv:
         return run_lamadv(args)
+    if args.eq:
+        return run_eq(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:

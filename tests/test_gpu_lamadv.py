@@ -168,7 +168,7 @@ def test_static_entry_point():
     assert np.array_equal(host(a), host(b))
 
 
-def test_adjoint_and_groups_rejected():
+def test_adjoint_and_mixed_groups_rejected():
     import paper_1804_05087_gb300 as sp
     ctx, orc = la(8, 17, 8)
     ctx.sp_set_base(ctx.zeros())
@@ -177,7 +177,7 @@ def test_adjoint_and_groups_rejected():
     with pytest.raises(sp.SpError):
         ctx.sp_newton_gmres(ctx.zeros(), use_gradient=True)
     with pytest.raises(sp.SpError):
-        sp.Group([sp.Config(8, 17, 8, lam_adv=1)])
+        sp.Group([sp.Config(8, 17, 8, lam_adv=1), sp.Config(8, 17, 8, lam_adv=0)])
 
 
 def test_newton_converges_with_fewer_actions():

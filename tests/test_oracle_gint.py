@@ -65,3 +65,32 @@ def test_single_step_and_laminar():
     u = orc.seed_state(*si.couette_random_coeffs(14, 8, 17, 8), 0.1)
     assert np.max(np.abs(step_n(orc, u, 1) - orc.step(u))) == 0.0
     assert np.max(np.abs(step_n(orc, orc.zeros(), 7))) < 1e-14
+
+
+def test_befe_loop_unstable_at_large_kx():
+    """One BEFE step treats the advection explicitly (forward Euler), so at laminar flow a mode
+    with streamwise wavenumber kx near walls moving at |U| = 1 is amplified by up to
+    sqrt(1 + (dt kx)^2) / (1 + dt nu k^2) per step. At dt = 1/32 and kx = 15 x 1.14 that
+    exceeds one: B_dt^n grows with n and G^int_T = B^n - I becomes ill conditioned for
+    T >= 1. At dt = 1/256 the same mode decays. (Power iteration on B_U = G_U + I restricted
+    to the ix = Kx modes, which B_U leaves invariant at laminar flow.)"""
+    rad = {}
+    for dt in (1 / 32, 1 / 256):
+        o = Couette(48, 17, 4, re=380.0, dt=dt)
+        base = o.base(o.zeros())
+        rng = np.random.default_rng(0)
+        d = o.zeros()
+        d[:, o.Kx, 0, :] = rng.standard_normal((3, o.NY)) + 1j * rng.standard_normal((3, o.NY))
+        d = o.befe(o.sym(d)) - o.befe(o.zeros())
+        lam = 0.0
+        for _ in range(80):
+            d = d / o.norm(d)
+            e = o.jvp(base, d) + d
+            lam = o.norm(e)
+            d = e
+        rad[dt] = lam
+        kx = o.kx[o.Kx]
+        bound = math.sqrt(1 + (dt * kx) ** 2)
+        assert lam < bound
+    assert rad[1 / 32] > 1.02
+    assert rad[1 / 256] < 1.0
