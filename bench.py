@@ -238,7 +238,9 @@ def run_newton(args):
                                      ("fp64_tangent", sp.SP_FP64, False, "gmres", 0),
                                      ("fp64_fd", sp.SP_FP64, True, "gmres", 0),
                                      ("mixed_bicgstab2", sp.SP_MIXED, False, "bicgstab", 2),
-                                     ("mixed_bicgstab4", sp.SP_MIXED, False, "bicgstab", 4)):
+                                     ("mixed_bicgstab4", sp.SP_MIXED, False, "bicgstab", 4),
+                                     ("mixed_idr4", sp.SP_MIXED, False, "idr", 4),
+                                     ("mixed_idr8", sp.SP_MIXED, False, "idr", 8)):
         ctx = sp.Context(sp.Config(nx, ny, nz, lx=LX, lz=LZ, re=RE, dt=DT, prec=prec))
         ctx.sp_autotune(1)
         a, b, c = si.couette_random_coeffs(1000, nx, ny, nz)
@@ -727,6 +729,22 @@ def run_lamadv(args):
                            "norm_F": rep["norm_F"], "wall_s": time.perf_counter() - t0})
             ctx.close()
 
+    # the short-recurrence solvers of Sec. 3.6 with and without laminar advection in L
+    short = []
+    grid = (16, 33, 16)
+    for krylov, ell in (("bicgstab", 4), ("idr", 8)):
+        for lam_adv in (0, 1):
+            ctx = context(grid, 400.0, lam_adv)
+            U = seeded(ctx, grid, 1000, 0.1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = ctx.sp_newton_gmres(U, max_newton=20, max_krylov=4000, tol=1e-10, krylov=krylov, ell=ell)
+            torch.cuda.synchronize()
+            short.append({"solver": f"{krylov}({ell})", "lam_adv": lam_adv, "converged": rep["converged"],
+                          "newton_iters": rep["newton_iters"], "actions": rep["total_jvps"],
+                          "norm_F": rep["norm_F"], "wall_s": time.perf_counter() - t0})
+            ctx.close()
+
     # tangent throughput with the complex per-mode operators (48x65x48, 256 directions)
     grid, nd = (NX, NY, NZ), args.ndir
     thr = {}
@@ -768,7 +786,8 @@ def run_lamadv(args):
            "config": {"workload": "plane Couette, dt=100, seed 1000 perturbed-laminar guesses; tangent "
                                   f"throughput {NX}x{NY}x{NZ} Re {RE} {nd} directions, mixed",
                       "max_krylov": args.krylov, "eta": 1e-3},
-           "first_solve": first_solve, "newton": newton, "throughput": thr}
+           "first_solve": first_solve, "newton": newton, "short_recurrence_16x33x16_re400": short,
+           "throughput": thr}
     print(json.dumps(out))
 
 

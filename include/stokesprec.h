@@ -77,8 +77,9 @@ typedef struct {
                        (1/dt - nu lap + M) u' + grad p = u/dt + N(u) + M u.
                        Same fixed points; per mode the solve becomes complex and
                        couples both Chebyshev parities. With 1, sp_vjp,
-                       sp_vjp_euclid, the gradient hookstep and groups return
-                       SP_EINVAL (they are defined for the Stokes step). */
+                       sp_vjp_euclid and the gradient hookstep return SP_EINVAL
+                       (they are defined for the Stokes step); the members of a
+                       group must all have the same value. */
 } sp_config;
 
 /* ---- lifetime ----------------------------------------------------------- */
@@ -301,12 +302,15 @@ typedef struct {
   int int_steps;      /* <= 1: G = G^Stokes = B_dt - I (one step, Eq. Gstokes);
                          n > 1: G = G^int = (B_dt)^n - I (n steps of cfg.dt,
                          Eq. Gint; plane Couette, use_gradient = 0)            */
-  int krylov;         /* 0: GMRES with hookstep (default); 1: BiCGSTAB(ell)
-                         (Sec. 3.6: no K^2 term), at most max_krylov actions per
-                         Newton step, trust region along the computed direction
-                         (one more action for its predicted residual); needs
-                         int_steps <= 1, use_gradient = 0                       */
-  int ell;            /* BiCGSTAB(ell): ell (1..8, <= 0: 2)                   */
+  int krylov;         /* 0: GMRES with hookstep (default); 1: BiCGSTAB(ell);
+                         2: IDR(s) with biorthogonalised bases (Sec. 3.6: no
+                         K^2 term; s seeded shadow vectors). 1 and 2: at most
+                         max_krylov actions per Newton step, trust region along
+                         the computed direction (one more action for its
+                         predicted residual); need int_steps <= 1,
+                         use_gradient = 0. Other values: SP_EINVAL.            */
+  int ell;            /* BiCGSTAB(ell): ell (1..8, <= 0: 2); IDR(s): s (1..8,
+                         <= 0: 4)                                              */
   int use_graphs;     /* 1: each Arnoldi step (action + orthogonalisation) is
                          captured once as a CUDA graph on a stream of the
                          context and replayed (tangent actions with int_steps

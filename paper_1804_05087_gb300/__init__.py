@@ -382,7 +382,7 @@ class Context:
         return rep
 
 
-KRYLOV = {"gmres": 0, "bicgstab": 1}
+KRYLOV = {"gmres": 0, "bicgstab": 1, "idr": 2}
 
 
 def _opts(max_newton, max_krylov, tol, eta, delta0, use_fd, use_gradient, int_steps=1, krylov="gmres", ell=2,

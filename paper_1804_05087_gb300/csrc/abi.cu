@@ -1,6 +1,7 @@
 // The C ABI (include/stokesprec.h): context lifetime, the BEFE step, its
 // tangent and finite-difference actions, inner products and seeding.
 #include <chrono>
+#include <cstdint>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -693,142 +694,309 @@ double now_ms() {
 // Hessenberg matrix there is no hookstep: the trust region acts along the single
 // direction X (step s X, s = min(1, delta/|X|)), with the predicted residual
 // |G - s J X| from one more action and the hookstep's radius update.
-static sp_status newton_bicgstab(sp_ctx* c, double* U, const sp_newton_opts* o, sp_newton_report* rep,
-                                 cudaStream_t st) {
-  const int ell = std::max(1, std::min(8, o->ell > 0 ? o->ell : 2));
-  const int max_act = std::max(2, o->max_krylov);
+// Short-recurrence Krylov solvers for the Newton system J x = F (Sec. 3.6: no K^2 term).
+// Work vectors are states of the context; scalars live on the host.
+struct ShortKrylov {
+  sp_ctx* c;
+  const sp_newton_opts* o;
+  sp_newton_report* rep;
+  cudaStream_t st;
+  size_t L;
+  sp_status dot(const double* a, const double* b, double* out) const { return inner_many(c, a, 1, b, out, st); }
+  sp_status dots(const double* V, int k, const double* w, double* out) const { return inner_many(c, V, k, w, out, st); }
+  sp_status axpby(double* out, double a, const double* x, double b, const double* y) const {
+    return sp_cuda(c, launch_axpby(out, a, x, b, y, L, st), "axpby");
+  }
+  sp_status copy(double* out, const double* x) const {
+    return sp_cuda(c, cudaMemcpyAsync(out, x, L * 8, cudaMemcpyDeviceToDevice, st), "copy");
+  }
+  sp_status zero(double* x) const { return sp_cuda(c, cudaMemsetAsync(x, 0, L * 8, st), "zero"); }
+  sp_status act(const double* in, double* out) const {
+    rep->total_jvps++;
+    return o->use_fd ? sp_jvp_fd(c, in, out, 1, st) : sp_jvp(c, in, out, 1, st);
+  }
+};
+
+static int bicgstab_ell(const sp_newton_opts* o) { return std::max(1, std::min(8, o->ell > 0 ? o->ell : 2)); }
+static int idr_s(const sp_newton_opts* o) { return std::max(1, std::min(8, o->ell > 0 ? o->ell : 4)); }
+
+// BiCGSTAB(ell) (Sleijpen and Fokkema): ell BiCG steps, then a minimal-residual polynomial of
+// degree ell. W: 2 (ell + 1) + 1 vectors. Solves J X = F from X = 0 to |r| <= eta |F|.
+static sp_status bicgstab_solve(const ShortKrylov& k, double* W, const double* F, double nF, double* X, double* Xb) {
+  const int ell = bicgstab_ell(k.o);
+  const size_t L = k.L;
+  double* R = W;                                   // r_0 .. r_l
+  double* Uv = W + (size_t)(ell + 1) * L;          // u_0 .. u_l
+  double* Rt = W + (size_t)2 * (ell + 1) * L;      // shadow residual
+  auto r = [&](int i) { return R + (size_t)i * L; };
+  auto u = [&](int i) { return Uv + (size_t)i * L; };
+  const int max_act = std::max(2, k.o->max_krylov);
+  sp_status s;
+  std::vector<double> tau((size_t)(ell + 1) * (ell + 1)), sigma(ell + 1), gp(ell + 1), g(ell + 1), gpp(ell + 1);
+  if ((s = k.copy(r(0), F)) != SP_OK || (s = k.copy(Rt, F)) != SP_OK || (s = k.zero(u(0))) != SP_OK ||
+      (s = k.zero(X)) != SP_OK)
+    return s;
+  double rho0 = 1.0, alpha = 0.0, omega = 1.0, rn = nF, best = nF;
+  if ((s = k.zero(Xb)) != SP_OK) return s;
+  int acts = 0;
+  bool broke = false;
+  while (acts < max_act && rn > k.o->eta * nF && !broke) {
+    rho0 = -omega * rho0;
+    for (int j = 0; j < ell && !broke; ++j) {
+      double rho1;
+      if ((s = k.dot(Rt, r(j), &rho1)) != SP_OK) return s;
+      if (rho0 == 0.0 || !std::isfinite(rho1)) { broke = true; break; }
+      const double beta = alpha * rho1 / rho0;
+      rho0 = rho1;
+      for (int i = 0; i <= j; ++i)
+        if ((s = k.axpby(u(i), 1.0, r(i), -beta, u(i))) != SP_OK) return s;
+      if ((s = k.act(u(j), u(j + 1))) != SP_OK) return s;
+      double gam;
+      if ((s = k.dot(Rt, u(j + 1), &gam)) != SP_OK) return s;
+      if (gam == 0.0 || !std::isfinite(gam)) { broke = true; break; }
+      alpha = rho0 / gam;
+      for (int i = 0; i <= j; ++i)
+        if ((s = k.axpby(r(i), 1.0, r(i), -alpha, u(i + 1))) != SP_OK) return s;
+      if ((s = k.act(r(j), r(j + 1))) != SP_OK) return s;
+      if ((s = k.axpby(X, 1.0, X, alpha, u(0))) != SP_OK) return s;
+      acts += 2;
+    }
+    if (broke) break;
+    // minimal residual over r_1 .. r_l
+    for (int j = 1; j <= ell; ++j) {
+      for (int i = 1; i < j; ++i) {
+        double t;
+        if ((s = k.dot(r(j), r(i), &t)) != SP_OK) return s;
+        tau[(size_t)i * (ell + 1) + j] = t / sigma[i];
+        if ((s = k.axpby(r(j), 1.0, r(j), -tau[(size_t)i * (ell + 1) + j], r(i))) != SP_OK) return s;
+      }
+      if ((s = k.dot(r(j), r(j), &sigma[j])) != SP_OK) return s;
+      double t0r;
+      if ((s = k.dot(r(0), r(j), &t0r)) != SP_OK) return s;
+      if (!(sigma[j] > 0.0)) { broke = true; break; }
+      gp[j] = t0r / sigma[j];
+    }
+    if (broke) break;
+    g[ell] = gp[ell];
+    omega = g[ell];
+    for (int j = ell - 1; j >= 1; --j) {
+      double acc = gp[j];
+      for (int i = j + 1; i <= ell; ++i) acc -= tau[(size_t)j * (ell + 1) + i] * g[i];
+      g[j] = acc;
+    }
+    for (int j = 1; j < ell; ++j) {
+      double acc = g[j + 1];
+      for (int i = j + 1; i < ell; ++i) acc += tau[(size_t)j * (ell + 1) + i] * g[i + 1];
+      gpp[j] = acc;
+    }
+    if ((s = k.axpby(X, 1.0, X, g[1], r(0))) != SP_OK) return s;
+    if ((s = k.axpby(r(0), 1.0, r(0), -gp[ell], r(ell))) != SP_OK) return s;
+    if ((s = k.axpby(u(0), 1.0, u(0), -g[ell], u(ell))) != SP_OK) return s;
+    for (int j = 1; j < ell; ++j) {
+      if ((s = k.axpby(u(0), 1.0, u(0), -g[j], u(j))) != SP_OK) return s;
+      if ((s = k.axpby(X, 1.0, X, gpp[j], r(j))) != SP_OK) return s;
+      if ((s = k.axpby(r(0), 1.0, r(0), -gp[j], r(j))) != SP_OK) return s;
+    }
+    if ((s = k.dot(r(0), r(0), &rn)) != SP_OK) return s;
+    rn = std::sqrt(rn);
+    if (!std::isfinite(rn) || omega == 0.0) broke = true;
+    if (std::isfinite(rn) && rn < best) {
+      best = rn;
+      if ((s = k.copy(Xb, X)) != SP_OK) return s;
+    }
+  }
+  // a broken, stagnating or diverging recurrence hands back its best iterate
+  if ((broke || !(std::isfinite(rn) && rn <= best)) && best < nF) return k.copy(X, Xb);
+  return SP_OK;
+}
+
+// IDR(s) with biorthogonalised bases (van Gijzen and Sonneveld's variant): each cycle
+// builds s directions U_k (G_k = J U_k) whose residual updates keep r orthogonal to the
+// shadow space P, then one minimal-residual step (omega, with the 0.7 safeguard).
+// W: 3 s + 3 vectors; P (s orthonormal seeded vectors) is built once per solve.
+static sp_status idr_solve(const ShortKrylov& k, double* W, const double* F, double nF, double* X, double* Xb) {
+  const int sdim = idr_s(k.o);
+  const size_t L = k.L;
+  double* P = W;
+  double* G = W + (size_t)sdim * L;
+  double* Us = W + (size_t)2 * sdim * L;
+  double* r = W + (size_t)3 * sdim * L;
+  double* v = r + L;
+  double* t = v + L;
+  auto pv = [&](int i) { return P + (size_t)i * L; };
+  auto gv = [&](int i) { return G + (size_t)i * L; };
+  auto uv = [&](int i) { return Us + (size_t)i * L; };
+  const int max_act = std::max(2, k.o->max_krylov);
+  sp_status s;
+  // shadow space: seeded normal vectors, orthonormalised (modified Gram-Schmidt)
+  {
+    std::vector<double> h((size_t)sdim * L);
+    uint64_t z = 0x9E3779B97F4A7C15ull;
+    for (size_t i = 0; i < h.size(); ++i) {  // splitmix64 + Box-Muller
+      auto next = [&]() {
+        z += 0x9E3779B97F4A7C15ull;
+        uint64_t x = z;
+        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+        x ^= x >> 31;
+        return ((x >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+      };
+      const double u1 = next(), u2 = next();
+      h[i] = std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2);
+    }
+    if ((s = sp_cuda(k.c, cudaMemcpyAsync(P, h.data(), h.size() * 8, cudaMemcpyHostToDevice, k.st), "P")) != SP_OK)
+      return s;
+    if ((s = sp_cuda(k.c, cudaStreamSynchronize(k.st), "P sync")) != SP_OK) return s;
+    for (int i = 0; i < sdim; ++i) {
+      for (int j = 0; j < i; ++j) {
+        double d;
+        if ((s = k.dot(pv(j), pv(i), &d)) != SP_OK || (s = k.axpby(pv(i), 1.0, pv(i), -d, pv(j))) != SP_OK)
+          return s;
+      }
+      double n2;
+      if ((s = k.dot(pv(i), pv(i), &n2)) != SP_OK) return s;
+      if (!(n2 > 0.0)) return sp_fail(k.c, SP_ENAN, "IDR: degenerate shadow space");
+      if ((s = k.axpby(pv(i), 1.0 / std::sqrt(n2), pv(i), 0.0, nullptr)) != SP_OK) return s;
+    }
+  }
+  if ((s = k.copy(r, F)) != SP_OK || (s = k.zero(X)) != SP_OK) return s;
+  for (int i = 0; i < sdim; ++i)
+    if ((s = k.zero(gv(i))) != SP_OK || (s = k.zero(uv(i))) != SP_OK) return s;
+  std::vector<double> M((size_t)sdim * sdim, 0.0), f(sdim), cc(sdim), col(sdim);
+  for (int i = 0; i < sdim; ++i) M[(size_t)i * sdim + i] = 1.0;
+  double om = 1.0, rn = nF, best = nF;
+  if ((s = k.zero(Xb)) != SP_OK) return s;
+  auto keep_best = [&]() -> sp_status {
+    if (std::isfinite(rn) && rn < best) {
+      best = rn;
+      return k.copy(Xb, X);
+    }
+    return SP_OK;
+  };
+  int acts = 0;
+  bool broke = false;
+  while (acts < max_act && rn > k.o->eta * nF && !broke) {
+    if ((s = k.dots(P, sdim, r, f.data())) != SP_OK) return s;
+    for (int kk = 0; kk < sdim && !broke; ++kk) {
+      // M(kk:s, kk:s) c = f(kk:s), lower triangular
+      for (int i = kk; i < sdim; ++i) {
+        double acc = f[i];
+        for (int j = kk; j < i; ++j) acc -= M[(size_t)i * sdim + j] * cc[j];
+        cc[i] = acc / M[(size_t)i * sdim + i];
+      }
+      // v = r - G(:, kk:s) c;  U_kk = om v + U(:, kk:s) c
+      if ((s = k.copy(v, r)) != SP_OK) return s;
+      for (int i = kk; i < sdim; ++i)
+        if ((s = k.axpby(v, 1.0, v, -cc[i], gv(i))) != SP_OK) return s;
+      if ((s = k.axpby(t, om, v, cc[kk], uv(kk))) != SP_OK) return s;
+      for (int i = kk + 1; i < sdim; ++i)
+        if ((s = k.axpby(t, 1.0, t, cc[i], uv(i))) != SP_OK) return s;
+      if ((s = k.copy(uv(kk), t)) != SP_OK) return s;
+      if ((s = k.act(uv(kk), gv(kk))) != SP_OK) return s;
+      ++acts;
+      // biorthogonalise: P_i . G_kk = 0 for i < kk
+      for (int i = 0; i < kk; ++i) {
+        double d;
+        if ((s = k.dot(pv(i), gv(kk), &d)) != SP_OK) return s;
+        const double alpha = d / M[(size_t)i * sdim + i];
+        if ((s = k.axpby(gv(kk), 1.0, gv(kk), -alpha, gv(i))) != SP_OK) return s;
+        if ((s = k.axpby(uv(kk), 1.0, uv(kk), -alpha, uv(i))) != SP_OK) return s;
+      }
+      if ((s = k.dots(pv(kk), sdim - kk, gv(kk), col.data())) != SP_OK) return s;
+      for (int i = kk; i < sdim; ++i) M[(size_t)i * sdim + kk] = col[i - kk];
+      const double mkk = M[(size_t)kk * sdim + kk];
+      if (mkk == 0.0 || !std::isfinite(mkk)) { broke = true; break; }
+      const double beta = f[kk] / mkk;
+      if ((s = k.axpby(r, 1.0, r, -beta, gv(kk))) != SP_OK) return s;
+      if ((s = k.axpby(X, 1.0, X, beta, uv(kk))) != SP_OK) return s;
+      if ((s = k.dot(r, r, &rn)) != SP_OK) return s;
+      rn = std::sqrt(rn);
+      if (!std::isfinite(rn)) { broke = true; break; }
+      if ((s = keep_best()) != SP_OK) return s;
+      if (rn <= k.o->eta * nF || acts >= max_act) break;
+      for (int i = kk + 1; i < sdim; ++i) f[i] -= beta * M[(size_t)i * sdim + kk];
+    }
+    if (broke || rn <= k.o->eta * nF || acts >= max_act) break;
+    // dimension reduction: t = J r, om minimises |r - om t| (kept away from 0)
+    if ((s = k.act(r, t)) != SP_OK) return s;
+    ++acts;
+    double tt, tr;
+    if ((s = k.dot(t, t, &tt)) != SP_OK || (s = k.dot(t, r, &tr)) != SP_OK) return s;
+    if (!(tt > 0.0) || !std::isfinite(tr)) break;
+    om = tr / tt;
+    const double rho = std::fabs(tr) / (std::sqrt(tt) * rn);
+    if (rho < 0.7) om *= 0.7 / rho;
+    if (om == 0.0 || !std::isfinite(om)) break;
+    if ((s = k.axpby(X, 1.0, X, om, r)) != SP_OK) return s;
+    if ((s = k.axpby(r, 1.0, r, -om, t)) != SP_OK) return s;
+    if ((s = k.dot(r, r, &rn)) != SP_OK) return s;
+    rn = std::sqrt(rn);
+    if (!std::isfinite(rn)) break;
+    if ((s = keep_best()) != SP_OK) return s;
+  }
+  // a broken, stagnating or diverging recurrence hands back its best iterate
+  if ((broke || !(std::isfinite(rn) && rn <= best)) && best < nF) return k.copy(X, Xb);
+  return SP_OK;
+}
+
+// Newton with a short-recurrence linear solver (krylov = 1: BiCGSTAB(ell), 2: IDR(s)) and a
+// trust region along the computed direction X (the hookstep's radius update): the step
+// s X with s = min(1, delta/|X|), its predicted residual |F - s J X| from one more action.
+static sp_status newton_short(sp_ctx* c, double* U, const sp_newton_opts* o, sp_newton_report* rep, cudaStream_t st) {
   const size_t L = c->state_len;
-  const int nvec = 2 * (ell + 1) + 4;
+  const int nsolve = o->krylov == 2 ? 3 * idr_s(o) + 3 : 2 * (bicgstab_ell(o) + 1) + 1;
+  const int nvec = nsolve + 5;
   if (c->kry_cap < nvec) {
     if (c->kry) cudaFree(c->kry);
     c->kry = nullptr;
     c->kry_cap = 0;
     if (cudaMalloc((void**)&c->kry, (size_t)nvec * L * 8) != cudaSuccess) {
       cudaGetLastError();
-      return sp_fail(c, SP_ENOMEM, "BiCGSTAB vectors");
+      return sp_fail(c, SP_ENOMEM, "short-recurrence Krylov vectors");
     }
     c->kry_cap = nvec;
   }
-  double* R = c->kry;                               // r_0 .. r_l
-  double* Uv = c->kry + (size_t)(ell + 1) * L;      // u_0 .. u_l
-  double* X = c->kry + (size_t)2 * (ell + 1) * L;   // the Newton correction
-  double* Rt = X + L;                               // shadow residual
-  double* F = Rt + L;                               // G(U)
-  double* Ut = F + L;                               // trial state
-  auto r = [&](int i) { return R + (size_t)i * L; };
-  auto u = [&](int i) { return Uv + (size_t)i * L; };
-  auto dot = [&](const double* a, const double* b, double* out) { return inner_many(c, a, 1, b, out, st); };
-  auto axpby = [&](double* out, double a, const double* x, double b, const double* y) {
-    return sp_cuda(c, launch_axpby(out, a, x, b, y, L, st), "axpby");
-  };
-  auto act = [&](const double* in, double* out) {
-    rep->total_jvps++;
-    return o->use_fd ? sp_jvp_fd(c, in, out, 1, st) : sp_jvp(c, in, out, 1, st);
-  };
+  double* W = c->kry;
+  double* X = c->kry + (size_t)nsolve * L;  // the Newton correction
+  double* F = X + L;                        // G(U)
+  double* Ut = F + L;                       // trial state
+  double* JX = Ut + L;                      // J X
+  double* Xb = JX + L;                      // best iterate of the linear solve
+  const ShortKrylov k{c, o, rep, st, L};
   const double t0 = now_ms();
   sp_status s;
   if ((s = step_batch(c, U, F, 1, st)) != SP_OK) return s;
   rep->total_steps++;
   double nF;
-  if ((s = dot(F, F, &nF)) != SP_OK) return s;
+  if ((s = k.dot(F, F, &nF)) != SP_OK) return s;
   nF = std::sqrt(nF);
   rep->norm_F0 = nF;
   double nU;
-  if ((s = dot(U, U, &nU)) != SP_OK) return s;
+  if ((s = k.dot(U, U, &nU)) != SP_OK) return s;
   double delta = o->delta0 > 0 ? o->delta0 : 0.1 * std::max(std::sqrt(nU), 1.0);
   sp_status result = SP_ENOTCONV;
-  std::vector<double> tau((size_t)(ell + 1) * (ell + 1)), sigma(ell + 1), gp(ell + 1), g(ell + 1), gpp(ell + 1);
   for (int it = 0; it <= o->max_newton; ++it) {
     if (!std::isfinite(nF)) { result = SP_ENAN; break; }
     if (nF < o->tol) { result = SP_OK; break; }
     if (it == o->max_newton) break;
     if ((s = sp_set_base(c, U, st)) != SP_OK) return s;
     rep->total_steps++;
-    // solve J x = F from x = 0
-    if ((s = axpby(r(0), 1.0, F, 0.0, nullptr)) != SP_OK) return s;
-    if ((s = axpby(Rt, 1.0, F, 0.0, nullptr)) != SP_OK) return s;
-    if ((s = sp_cuda(c, cudaMemsetAsync(u(0), 0, L * 8, st), "zero")) != SP_OK) return s;
-    if ((s = sp_cuda(c, cudaMemsetAsync(X, 0, L * 8, st), "zero")) != SP_OK) return s;
-    double rho0 = 1.0, alpha = 0.0, omega = 1.0, rn = nF;
-    int acts = 0;
-    bool broke = false;
-    while (acts < max_act && rn > o->eta * nF && !broke) {
-      rho0 = -omega * rho0;
-      for (int j = 0; j < ell && !broke; ++j) {
-        double rho1;
-        if ((s = dot(Rt, r(j), &rho1)) != SP_OK) return s;
-        if (rho0 == 0.0 || !std::isfinite(rho1)) { broke = true; break; }
-        const double beta = alpha * rho1 / rho0;
-        rho0 = rho1;
-        for (int i = 0; i <= j; ++i)
-          if ((s = axpby(u(i), 1.0, r(i), -beta, u(i))) != SP_OK) return s;
-        if ((s = act(u(j), u(j + 1))) != SP_OK) return s;
-        double gam;
-        if ((s = dot(Rt, u(j + 1), &gam)) != SP_OK) return s;
-        if (gam == 0.0 || !std::isfinite(gam)) { broke = true; break; }
-        alpha = rho0 / gam;
-        for (int i = 0; i <= j; ++i)
-          if ((s = axpby(r(i), 1.0, r(i), -alpha, u(i + 1))) != SP_OK) return s;
-        if ((s = act(r(j), r(j + 1))) != SP_OK) return s;
-        if ((s = axpby(X, 1.0, X, alpha, u(0))) != SP_OK) return s;
-        acts += 2;
-      }
-      if (broke) break;
-      // minimal residual over r_1 .. r_l
-      for (int j = 1; j <= ell; ++j) {
-        for (int i = 1; i < j; ++i) {
-          double t;
-          if ((s = dot(r(j), r(i), &t)) != SP_OK) return s;
-          tau[(size_t)i * (ell + 1) + j] = t / sigma[i];
-          if ((s = axpby(r(j), 1.0, r(j), -tau[(size_t)i * (ell + 1) + j], r(i))) != SP_OK) return s;
-        }
-        if ((s = dot(r(j), r(j), &sigma[j])) != SP_OK) return s;
-        double t0r;
-        if ((s = dot(r(0), r(j), &t0r)) != SP_OK) return s;
-        if (!(sigma[j] > 0.0)) { broke = true; break; }
-        gp[j] = t0r / sigma[j];
-      }
-      if (broke) break;
-      g[ell] = gp[ell];
-      omega = g[ell];
-      for (int j = ell - 1; j >= 1; --j) {
-        double acc = gp[j];
-        for (int i = j + 1; i <= ell; ++i) acc -= tau[(size_t)j * (ell + 1) + i] * g[i];
-        g[j] = acc;
-      }
-      for (int j = 1; j < ell; ++j) {
-        double acc = g[j + 1];
-        for (int i = j + 1; i < ell; ++i) acc += tau[(size_t)j * (ell + 1) + i] * g[i + 1];
-        gpp[j] = acc;
-      }
-      if ((s = axpby(X, 1.0, X, g[1], r(0))) != SP_OK) return s;
-      if ((s = axpby(r(0), 1.0, r(0), -gp[ell], r(ell))) != SP_OK) return s;
-      if ((s = axpby(u(0), 1.0, u(0), -g[ell], u(ell))) != SP_OK) return s;
-      for (int j = 1; j < ell; ++j) {
-        if ((s = axpby(u(0), 1.0, u(0), -g[j], u(j))) != SP_OK) return s;
-        if ((s = axpby(X, 1.0, X, gpp[j], r(j))) != SP_OK) return s;
-        if ((s = axpby(r(0), 1.0, r(0), -gp[j], r(j))) != SP_OK) return s;
-      }
-      if ((s = dot(r(0), r(0), &rn)) != SP_OK) return s;
-      rn = std::sqrt(rn);
-      if (!std::isfinite(rn) || omega == 0.0) broke = true;
-    }
-    // trust region along X (the same radius update as the hookstep): the step s X with
-    // s = min(1, delta/|X|), its predicted residual |F - s J X| from one more action
-    double* JX = u(1);  // free after the solve
-    if ((s = act(X, JX)) != SP_OK) return s;
+    s = o->krylov == 2 ? idr_solve(k, W, F, nF, X, Xb) : bicgstab_solve(k, W, F, nF, X, Xb);
+    if (s != SP_OK) return s;
+    if ((s = k.act(X, JX)) != SP_OK) return s;
     double xx, fj, jj;
-    if ((s = dot(X, X, &xx)) != SP_OK || (s = dot(F, JX, &fj)) != SP_OK || (s = dot(JX, JX, &jj)) != SP_OK) return s;
+    if ((s = k.dot(X, X, &xx)) != SP_OK || (s = k.dot(F, JX, &fj)) != SP_OK || (s = k.dot(JX, JX, &jj)) != SP_OK)
+      return s;
     const double nX = std::sqrt(xx);
     bool accepted = false;
     double nT = nF;
     for (int trial = 0; trial < 12 && nX > 0 && std::isfinite(nX); ++trial) {
       const double sc = std::min(1.0, delta / nX);
       const double pred = std::sqrt(std::max(0.0, nF * nF - 2.0 * sc * fj + sc * sc * jj));
-      if ((s = axpby(Ut, 1.0, U, -sc, X)) != SP_OK) return s;
+      if ((s = k.axpby(Ut, 1.0, U, -sc, X)) != SP_OK) return s;
       if ((s = step_batch(c, Ut, F, 1, st)) != SP_OK) return s;
       rep->total_steps++;
-      if ((s = dot(F, F, &nT)) != SP_OK) return s;
+      if ((s = k.dot(F, F, &nT)) != SP_OK) return s;
       nT = std::sqrt(nT);
       if (trust_update(nF, pred, nT, sc * nX, &delta)) {
         accepted = true;
@@ -839,14 +1007,14 @@ static sp_status newton_bicgstab(sp_ctx* c, double* U, const sp_newton_opts* o, 
       if ((s = step_batch(c, U, F, 1, st)) != SP_OK) return s;
       break;
     }
-    if ((s = sp_cuda(c, cudaMemcpyAsync(U, Ut, L * 8, cudaMemcpyDeviceToDevice, st), "accept")) != SP_OK) return s;
+    if ((s = k.copy(U, Ut)) != SP_OK) return s;
     nF = nT;
     rep->newton_iters++;
   }
   if ((s = sp_cuda(c, cudaStreamSynchronize(st), "newton sync")) != SP_OK) return s;
   rep->norm_F = nF;
   rep->t_total_ms = now_ms() - t0;
-  rep->t_action_ms = -1.0;  // not split for BiCGSTAB(l)
+  rep->t_action_ms = -1.0;  // not split for the short-recurrence solvers
   if (result == SP_ENOTCONV) c->err = "Newton did not reach the tolerance";
   return result;
 }
@@ -863,11 +1031,12 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     return sp_fail(c, SP_EINVAL, "sp_newton_gmres: use_gradient needs the adjoint (plane Couette only)");
   if (o->use_gradient && c->cfg.lam_adv)
     return sp_fail(c, SP_EINVAL, "sp_newton_gmres: use_gradient needs the adjoint of the Stokes step (lam_adv = 0)");
-  if (o->krylov == 1) {
+  if (o->krylov < 0 || o->krylov > 2) return sp_fail(c, SP_EINVAL, "sp_newton_gmres: krylov must be 0, 1 or 2");
+  if (o->krylov != 0) {
     if (o->use_gradient || o->int_steps > 1)
-      return sp_fail(c, SP_EINVAL, "sp_newton_gmres: BiCGSTAB(l) takes single-step actions without use_gradient");
+      return sp_fail(c, SP_EINVAL, "sp_newton_gmres: BiCGSTAB(l) and IDR(s) take single-step actions without use_gradient");
     sp_newton_report rr{};
-    sp_status s2 = newton_bicgstab(c, U, o, &rr, (cudaStream_t)stream);
+    sp_status s2 = newton_short(c, U, o, &rr, (cudaStream_t)stream);
     if (rep) *rep = rr;
     return s2;
   }

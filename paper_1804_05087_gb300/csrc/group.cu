@@ -291,7 +291,7 @@ extern "C" sp_status sp_group_create(const sp_config* cfgs, int n, sp_group** ou
   size_t pos = 0;
   for (int i = 0; i < n; ++i) {
     if (cfgs[i].prec != g->prec) return bail(SP_EINVAL, "members differ in precision");
-    if (cfgs[i].lam_adv) return bail(SP_EINVAL, "groups take the Stokes step only (lam_adv = 0)");
+    if (cfgs[i].lam_adv != cfgs[0].lam_adv) return bail(SP_EINVAL, "members differ in lam_adv");
     sp_config c = cfgs[i];
     c.max_batch = 1;
     sp_status s = sp_create(&c, &g->mem[i]);

@@ -1377,7 +1377,7 @@ struct GSolve {
   SolveArgs a;
 };
 
-template <typename T>
+template <typename T, bool LA>
 __global__ void __launch_bounds__(kThreadsSolveGrp) k_solve_grp(const double* __restrict__ du_base,
                                                             double* __restrict__ out_base,
                                                             const GSolve* __restrict__ recs,
@@ -1389,7 +1389,7 @@ __global__ void __launch_bounds__(kThreadsSolveGrp) k_solve_grp(const double* __
   __shared__ GSolve r;
   if (threadIdx.x == 0) r = recs[i];
   __syncthreads();
-  solve_body<T, kTileSolve, false>(reinterpret_cast<const C2<T>*>(r.in3), reinterpret_cast<const double2*>(du_base + r.off),
+  solve_body<T, kTileSolve, LA>(reinterpret_cast<const C2<T>*>(r.in3), reinterpret_cast<const double2*>(du_base + r.off),
                 reinterpret_cast<double2*>(out_base + r.off), r.a, blockIdx.x - first[i], 0);
 }
 
@@ -1877,15 +1877,17 @@ static cudaError_t grp_build_solve(GrpKernel* k, sp_ctx* const* mem, int n, cons
     nblk[m] = (c->n_unique + kTileSolve - 1) / kTileSolve;
     smem = std::max(smem, solve_smem(c, esize));
   }
-  cudaError_t e = esize == 8
-                      ? cudaFuncSetAttribute(k_solve_grp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                      : cudaFuncSetAttribute(k_solve_grp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const bool la = mem[0]->cfg.lam_adv != 0;
+  const void* kern = esize == 8 ? (la ? (const void*)k_solve_grp<double, true> : (const void*)k_solve_grp<double, false>)
+                                : (la ? (const void*)k_solve_grp<float, true> : (const void*)k_solve_grp<float, false>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return grp_make(k, recs, nblk, order, n, smem);
 }
 
 cudaError_t grp_plan_build(GrpPlan* p, sp_ctx* const* mem, int n, const size_t* offs, const int* order) {
   p->n = n;
+  p->lam_adv = mem[0]->cfg.lam_adv != 0;
   // split the Gauss-Lobatto points of k_yinv only when the whole group has too few mode tiles
   int tiles = 0, nh_min = 1 << 30;
   for (int m = 0; m < n; ++m) {
@@ -1950,9 +1952,11 @@ cudaError_t grp_launch_solve(const GrpPlan& p, bool fp32, const double* du_base,
   const GrpKernel& k = fp32 ? p.solve32 : p.solve64;
   if (k.blocks == 0) return cudaSuccess;
   const GSolve* r = static_cast<const GSolve*>(k.recs);
+  auto kern = p.lam_adv ? k_solve_grp<float, true> : k_solve_grp<float, false>;
+  auto kern64 = p.lam_adv ? k_solve_grp<double, true> : k_solve_grp<double, false>;
   if (fp32)
-    k_solve_grp<float><<<k.blocks, kThreadsSolveGrp, k.smem, st>>>(du_base, out_base, r, k.inst, k.first, active);
+    kern<<<k.blocks, kThreadsSolveGrp, k.smem, st>>>(du_base, out_base, r, k.inst, k.first, active);
   else
-    k_solve_grp<double><<<k.blocks, kThreadsSolveGrp, k.smem, st>>>(du_base, out_base, r, k.inst, k.first, active);
+    kern64<<<k.blocks, kThreadsSolveGrp, k.smem, st>>>(du_base, out_base, r, k.inst, k.first, active);
   return cudaGetLastError();
 }

@@ -177,6 +177,7 @@ struct GrpKernel {
 constexpr int kGrpRegClasses = 5;  // register-FFT plane kernels: grids 16, 24, 32, 48, 64
 struct GrpPlan {
   int n = 0;
+  int lam_adv = 0;                // every member has laminar advection in L (else none has)
   GrpKernel yinv64, yinv32, xz64, solve64, solve32;
   GrpKernel xz32;                 // float plane stage of the members without a register-FFT kernel
   GrpKernel xzr[kGrpRegClasses];  // float plane stage of the others, per grid size class (xz_reg.cu)

@@ -1,4 +1,4 @@
-"""Newton with BiCGSTAB(l) as the linear solver (Sec. 3.6).
+"""Newton with BiCGSTAB(l) or IDR(s) as the linear solver (Sec. 3.6).
 
 The G^Stokes Jacobian has eigenvalues spread along the imaginary axis, with an
 extent that grows like Re (about +-27i at Re 400 on 8x17x8): BiCGSTAB(l) needs
@@ -7,6 +7,9 @@ several times more actions than GMRES there (the oracle's dense 8x17x8 Jacobian:
 and at Re 400 the later Newton steps do not reach eta within thousands of actions,
 as the paper reports for BiCGSTAB. At Re 100 the spectrum is compact and Newton
 with BiCGSTAB(l) must reach the same root as GMRES (laminar flow) to |G| < 1e-10.
+IDR(s) (the other method the paper names) is held to the same checks. With laminar
+advection folded into L the imaginary extent shrinks (Sec. 3.6), and both
+short-recurrence solvers converge at Re 400 as well.
 """
 import pytest
 import torch
@@ -40,3 +43,24 @@ def test_bicgstab_rejects_unsupported_options():
     U = dev(seeded(orc, 1000, 0.05))
     with pytest.raises(Exception):
         ctx.sp_newton_gmres(U, krylov="bicgstab", int_steps=4)
+
+
+@pytest.mark.parametrize("sdim", [4, 8])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_idr_newton_reaches_laminar_at_low_re(sdim, prec):
+    ctx, orc = make(16, 33, 16, prec=prec, re=100.0)
+    U = dev(seeded(orc, 1000, 0.05))
+    rep = ctx.sp_newton_gmres(U, max_newton=30, max_krylov=4000, tol=1e-10, eta=1e-3, krylov="idr", ell=sdim)
+    assert rep["converged"], rep
+    assert float(torch.linalg.vector_norm(U)) < 1e-8
+
+
+def test_unknown_krylov_rejected():
+    import paper_1804_05087_gb300 as sp
+    ctx, orc = make(8, 17, 8)
+    o = sp._opts(5, 10, 1e-10, 1e-3, 0.0, False, False)
+    o.krylov = 3
+    r = sp._NewtonReport()
+    U = dev(seeded(orc, 1000, 0.05))
+    st = sp._lib.sp_newton_gmres(ctx._h, ctx._ptr(U, 1)[0], sp.ctypes.byref(o), sp.ctypes.byref(r), None)
+    assert st == 1  # SP_EINVAL
