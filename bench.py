@@ -62,6 +62,9 @@ def parse():
                    help="96x97x96, Re 1000, doubled box: adjoint gradient check and Newton-hookstep with J^T F")
     p.add_argument("--eq", action="store_true",
                    help="continuation from a nontrivial equilibrium (48x35x48, Re 400 -> 380): G^Stokes_T vs G^int_T")
+    p.add_argument("--eq-spectra", action="store_true",
+                   help="spectra of G^Stokes_T and G^int_T at a nontrivial equilibrium (Re 500) and its leading "
+                        "eigenvalue")
     p.add_argument("--lam-adv", action="store_true",
                    help="the default throughput run with laminar advection folded into L")
     p.add_argument("--lamadv", action="store_true",
@@ -862,6 +865,101 @@ def run_eq(args):
     print(json.dumps(out))
 
 
+def truncate_state(ctx_to, U, Kx_from):
+    """Copy the retained modes of a plane Couette state onto a coarser grid (Fourier modes
+    |ix| <= Kx, iz <= Kz of the target, Chebyshev degrees < NY of the target)."""
+    out = ctx_to.zeros()
+    MXf = 2 * Kx_from + 1
+    for ix in range(-ctx_to.Kx, ctx_to.Kx + 1):
+        out[:, ix % ctx_to.MX, :, :] = U[:, ix % MXf, :ctx_to.MZ, :ctx_to.NY]
+    return out
+
+
+def continue_in_re(sp, torch, grid, U, res, lam_adv=1):
+    """Newton continuation of an equilibrium through the Reynolds numbers ``res``."""
+    reps = []
+    for re in res:
+        ctx = sp.Context(sp.Config(*grid, lx=LX, lz=LZ, re=re, dt=DT, prec=sp.SP_MIXED, lam_adv=lam_adv))
+        rep = ctx.sp_newton_gmres(U, max_newton=30, max_krylov=300, tol=1e-11)
+        reps.append({"re": re, "converged": rep["converged"], "newton_iters": rep["newton_iters"],
+                     "norm_F": rep["norm_F"], "norm_U": math.sqrt(ctx.sp_inner(U, U)[0])})
+        ctx.close()
+    return reps
+
+
+def run_eq_spectra(args):
+    """Spectra of the Jacobians at a nontrivial equilibrium (Sec. 3.5, the spectra figures at
+    EQ1, Re 500): the equilibrium of --eq is continued from Re 400 to 500 at 48 x 35 x 48; its
+    leading eigenvalue (the paper quotes 0.06 for EQ1 at Re 500) comes from power iteration on
+    the tangent of the propagator B_dt^n (dt = 1/256, T = n dt = 5: mu = exp(lambda T)). The
+    same equilibrium, truncated to 12 x 25 x 12 and re-converged, gives dense Jacobians of
+    G^Stokes_T (T = 1e-4, 0.1, 100; rescaled by (1 + T)/T) and G^int_10 (dt = 1/256),
+    restricted to the physical subspace; eigenvalues on the host."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1804_05087_gb300 as sp
+    import seeded_inputs as si
+    big = (48, 35, 48)
+    U, rep0 = find_equilibrium(sp, si, torch)
+    cont = continue_in_re(sp, torch, big, U, (450.0, 500.0))
+    # leading eigenvalue at 48 x 35 x 48, Re 500: power iteration on (B^n)_U
+    dt, n = 1.0 / 256, 1280
+    ctx = sp.Context(sp.Config(*big, lx=LX, lz=LZ, re=500.0, dt=dt, prec=sp.SP_MIXED))
+    ctx.sp_set_base_n(U, n)
+    v = ctx.zeros()
+    a, b, c = si.couette_random_coeffs(4242, *big)
+    ctx.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], 1.0, v)
+    w = ctx.zeros()
+    mus = []
+    for _ in range(40):
+        ctx.sp_jvp_n(v, w)
+        w += v                                    # (B^n)_U v = G^int_U v + v
+        mu = math.sqrt(ctx.sp_inner(w, w)[0] / ctx.sp_inner(v, v)[0])
+        mus.append(mu)
+        v = w / math.sqrt(ctx.sp_inner(w, w)[0])
+    lead = {"mu": mus[-1], "lambda": math.log(mus[-1]) / (n * dt), "T": n * dt, "dt": dt,
+            "mu_change_last": abs(mus[-1] - mus[-2]) / mus[-1]}
+    ctx.close()
+    # dense spectra on 12 x 25 x 12
+    small = (12, 25, 12)
+    cs = sp.Context(sp.Config(*small, lx=LX, lz=LZ, re=500.0, dt=DT, prec=sp.SP_MIXED, lam_adv=1))
+    Us = truncate_state(cs, U, 15)
+    cs.close()
+    cont_small = continue_in_re(sp, torch, small, Us, (500.0,))
+    specs = {}
+    Q = None
+    for kind, T in (("stokes", 1e-4), ("stokes", 0.1), ("stokes", 100.0), ("int", 10.0)):
+        dts = T if kind == "stokes" else 1.0 / 256
+        ns = 1 if kind == "stokes" else int(round(T / dts))
+        ctx = sp.Context(sp.Config(*small, lx=LX, lz=LZ, re=500.0, dt=dts, prec=sp.SP_FP64, max_batch=256))
+        ctx.sp_set_base_n(Us, ns)
+        J = dense_jacobian(ctx, ns)
+        if Q is None:
+            u_, sv, _ = np.linalg.svd(J + hermitian_projection(ctx))
+            d = int(np.sum(sv > 1e-10 * sv[0]))
+            Q = u_[:, :d]
+        ev = np.linalg.eigvals(Q.T @ J @ Q)
+        if kind == "stokes":
+            ev = ev * (1 + T) / T
+        dist = np.sort(np.abs(ev + 1.0))
+        specs[f"{kind}_{T:g}"] = {
+            "most_negative_real": float(ev.real.min()), "max_real": float(ev.real.max()),
+            "max_imag": float(np.abs(ev.imag).max()),
+            "frac_real_within_0.2_of_-1": float(np.mean(np.abs(ev.real + 1) < 0.2)),
+            "r95_around_-1": float(dist[int(np.ceil(0.95 * len(dist))) - 1]),
+            "largest_real_parts": [float(x) for x in np.sort(ev.real)[::-1][:3]]}
+        ctx.close()
+    out = {"metric": "Jacobian spectra at a nontrivial equilibrium (Re 500)", "config": {
+        "workload": "equilibrium of --eq continued to Re 500 (48x35x48; leading eigenvalue by power iteration "
+                    "on the propagator, dt = 1/256, T = 5); dense spectra on 12x25x12 (re-converged there), "
+                    "FP64 tangent, restricted to the physical subspace"},
+        "equilibrium_search": {k: rep0[k] for k in ("converged", "newton_iters", "norm_F", "norm_U")},
+        "continuation_48x35x48": cont, "leading_eigenvalue_48x35x48": lead,
+        "continuation_12x25x12": cont_small, "subspace_dim": int(Q.shape[1]), "spectra_12x25x12": specs}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -882,6 +980,8 @@ def main():
         return run_lamadv(args)
     if args.eq:
         return run_eq(args)
+    if args.eq_spectra:
+        return run_eq_spectra(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:
