@@ -868,7 +868,6 @@ __global__ void __launch_bounds__(kThreadsSolve) k_solve_adj(const double2* __re
     const int t = idx / NR, n = idx - t * NR;  // momentum row n
     if (s_u[t] >= a.n_unique) continue;
     const int Q = n & 1, col = n >> 1;
-    const int rb = Q == 0 ? a.rb0 : a.rb1;
     const int nrow = Q == 0 ? N / 2 + 1 : N / 2;
     const double* H = a.ops + (size_t)s_u[t] * a.op_stride + (Q == 0 ? a.off_h0 : a.off_h1);
     const bool mean = s_pos[t] == 0 && s_iz[t] == 0;
