@@ -144,6 +144,19 @@ def kernel_flops(stage, n_dir):
     return 0
 
 
+# DRAM bytes of one mixed-precision k_solve tangent launch at 48x65x48 with 64 directions, from
+# one ncu capture of that launch (dram__bytes_read.sum, dram__bytes_write.sum). The
+# reads are 64 x (values + state) plus the per-mode operators once; both scale with the
+# directions except the operators.
+K_SOLVE_DRAM_64 = (164491520, 72370944)
+
+
+def solve_traffic(n_dir):
+    ops = n_unique() * op_entries() * 8
+    rd, wr = K_SOLVE_DRAM_64
+    return (rd - ops) * n_dir / 64 + ops + wr * n_dir / 64
+
+
 # ----------------------------------------------------------------- clocks
 class Clocks:
     def __init__(self, index):
@@ -153,7 +166,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", "20"], stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
 
@@ -1096,7 +1109,9 @@ def main():
         roof = {"bound": "alu", "achieved": tfs, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfs / alu_peak,
                 "peak_source": "nominal FP64 1.25 TFLOP/s" if alu_peak == fp64_peak
                 else "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
-    roof.update({"kernel": dom, "traffic": None, "avg_launch_ms": dom_ms / dom_n,
+    roof.update({"kernel": dom, "traffic": solve_traffic(nd) if (dom == "k_solve" and args.prec == "mixed"
+                                                                  and not args.lam_adv) else None,
+                 "avg_launch_ms": dom_ms / dom_n,
                  "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
                  "kernel_ms_per_step": {k: v[0] / args.steps for k, v in trace.items()}})
 

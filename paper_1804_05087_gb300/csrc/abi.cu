@@ -324,7 +324,17 @@ extern "C" sp_status sp_set_base(sp_ctx* c, const double* U, void* stream) {
                      "pvals")) != SP_OK)
       return s;
     if ((s = sp_cuda(c, launch_pipe_dz(c, c->U0, c->dzU, st), "dz")) != SP_OK) return s;
-  } else if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_yinv(c, false, c->U0, c->ws6, 1, st); }), "yinv")) != SP_OK) return s;
+  } else {
+    // one pass of curl, values and inverse transforms serves both the base fields and the
+    // step's product G(U) (the same arithmetic as sp_step)
+    if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_yinv(c, false, c->U0, c->ws6, 1, st); }), "yinv")) != SP_OK) return s;
+    if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_xz(c, false, XZ_STEP_BASE, c->ws6, c->ws3, 1, st); }), "xz step+base")) != SP_OK) return s;
+    if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_base_to_f32(c, st); }), "base f32")) != SP_OK) return s;
+    if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_solve(c, false, c->ws3, c->U0, c->G0, 1, st, c->solve_shape_step); }), "solve")) != SP_OK) return s;
+    c->has_base = 1;
+    c->traj_n = 1;
+    return SP_OK;
+  }
   if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_xz(c, false, XZ_BASE, c->ws6, nullptr, 1, st); }), "xz base")) != SP_OK) return s;
   if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_base_to_f32(c, st); }), "base f32")) != SP_OK) return s;
   if ((s = step_batch(c, c->U0, c->G0, 1, st)) != SP_OK) return s;

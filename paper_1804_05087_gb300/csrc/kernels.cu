@@ -343,9 +343,14 @@ __device__ __forceinline__ void xz_body(const XzArgs<T>& a, int bx, int by) {
           if constexpr (MODE == XZ_BASE) {
 #pragma unroll
             for (int f = 0; f < 6; ++f) a.base[(size_t)f * a.NY * nxz + gidx] = F[f] + lam[f];
-          } else if constexpr (MODE == XZ_STEP) {
+          } else if constexpr (MODE == XZ_STEP || MODE == XZ_STEP_BASE) {
             const T U0 = F[0] + lam[0], U1 = F[1] + lam[1], U2 = F[2] + lam[2];
             const T O0 = F[3] + lam[3], O1 = F[4] + lam[4], O2 = F[5] + lam[5];
+            if constexpr (MODE == XZ_STEP_BASE) {
+              const T tot[6] = {U0, U1, U2, O0, O1, O2};
+#pragma unroll
+              for (int f = 0; f < 6; ++f) a.base[(size_t)f * a.NY * nxz + gidx] = tot[f];
+            }
             res[r][0] = U1 * O2 - U2 * O1;
             res[r][1] = U2 * O0 - U0 * O2;
             res[r][2] = U0 * O1 - U1 * O0;
@@ -1529,6 +1534,10 @@ cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, voi
     case XZ_STEP:
       return launch_xz_t<double, XZ_STEP>(c, in6, out3, nullptr, tx, tz, c->xz_rp64, c->xz_cx64,
                                           c->smem_xz64, n_dir, st);
+    case XZ_STEP_BASE:
+      if (n_dir != 1) return cudaErrorInvalidValue;  // one base state
+      return launch_xz_t<double, XZ_STEP_BASE>(c, in6, out3, c->base64, tx, tz, c->xz_rp64, c->xz_cx64,
+                                               c->smem_xz64, n_dir, st);
     case XZ_TANGENT:
       return launch_xz_t<double, XZ_TANGENT>(c, in6, out3, c->base64, tx, tz, c->xz_rp64, c->xz_cx64,
                                              c->smem_xz64, n_dir, st);

@@ -201,7 +201,8 @@ cudaError_t grp_upload(void** dst, const void* src, size_t bytes);
 void grp_kernel_free(GrpKernel* k);
 
 // kernel launchers (kernels.cu); all asynchronous on `st`
-enum XzMode { XZ_STEP = 0, XZ_TANGENT = 1, XZ_BASE = 2, XZ_ADJOINT = 3 };
+// XZ_STEP_BASE: the step's product and, from the same inverse transforms, the base fields
+enum XzMode { XZ_STEP = 0, XZ_TANGENT = 1, XZ_BASE = 2, XZ_ADJOINT = 3, XZ_STEP_BASE = 4 };
 cudaError_t launch_yinv(const sp_ctx* c, bool fp32, const double* in, void* out6, int n_dir,
                         cudaStream_t st);
 cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, void* out3,
