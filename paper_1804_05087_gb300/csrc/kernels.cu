@@ -606,23 +606,42 @@ __device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const 
   }
   __syncthreads();
   // phase C2: reduced right-hand side g_n = f_v,n - (2 / (c_n k)) sum_{m > n, m + n odd,
-  // m <= N-2} m f~_a,m for each parity P (one suffix sum per mode and parity)
-  if (threadIdx.x < 2 * TM) {
-    const int t = threadIdx.x >> 1, P = threadIdx.x & 1;
-    if (s_u[t] < a.n_unique && !(s_pos[t] == 0 && s_iz[t] == 0)) {
+  // m <= N-2} m f~_a,m for each parity P. With x_n = (n+1) f~_a,n+1 the sum is the inclusive
+  // suffix sum of x over the rows of parity P: one warp per (mode, parity), a shuffle scan over
+  // chunks of 32 rows from the top, carrying the total of the chunks above.
+  {
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int pair = threadIdx.x >> 5; pair < 2 * TM; pair += nwarps) {
+      const int t = pair >> 1, P = pair & 1;
+      if (s_u[t] >= a.n_unique || (s_pos[t] == 0 && s_iz[t] == 0)) continue;  // whole warp
       const double ik = s_ik[t];
       double2* g = srv + (t * 2 + P) * a.cv;
-      double2 S = make_double2(0.0, 0.0);
-      for (int n = (P == 0 ? N - 2 : N - 3); n >= 0; n -= 2) {
-        const int m = n + 1;
-        if (m <= N - 2) {
-          const double2 x = sfa[t * NR + m];
-          S.x = fma((double)m, x.x, S.x);
-          S.y = fma((double)m, x.y, S.y);
+      const int cnt = P == 0 ? a.rb0 : a.rb1;  // rows n = 2i + P <= N-2
+      double2 carry = make_double2(0.0, 0.0);
+      for (int c0 = ((cnt - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
+        const int i = c0 + lane, n = 2 * i + P;
+        double2 x = make_double2(0.0, 0.0);
+        if (i < cnt && n + 1 <= N - 2) {
+          const double2 fa = sfa[t * NR + n + 1];
+          x = make_double2((double)(n + 1) * fa.x, (double)(n + 1) * fa.y);
         }
-        const double f = (n == 0 ? 1.0 : 2.0) * ik;
-        const double2 v = g[n / 2];
-        g[n / 2] = make_double2(v.x - f * S.x, v.y - f * S.y);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const double yx = __shfl_down_sync(0xffffffffu, x.x, o);
+          const double yy = __shfl_down_sync(0xffffffffu, x.y, o);
+          if (lane + o < 32) {
+            x.x += yx;
+            x.y += yy;
+          }
+        }
+        x.x += carry.x;
+        x.y += carry.y;
+        if (i < cnt) {
+          const double f = (n == 0 ? 1.0 : 2.0) * ik;
+          const double2 v = g[i];
+          g[i] = make_double2(v.x - f * x.x, v.y - f * x.y);
+        }
+        carry = make_double2(__shfl_sync(0xffffffffu, x.x, 0), __shfl_sync(0xffffffffu, x.y, 0));
       }
     }
   }
