@@ -807,22 +807,38 @@ def run_lamadv(args):
     print(json.dumps(out))
 
 
-def find_equilibrium(sp, si, torch, grid=(48, 35, 48), re=400.0, seed=7123, amp=0.3):
+# seeded guesses (seed, amplitude, perturbed modes |ix|, |iz| <= mmax) from which Newton with
+# laminar advection in L reached the spanwise-fundamental equilibrium at 48 x 35 x 48, Re 400
+EQ_SEEDS = ((7123, 0.3, 1), (7143, 0.3, 1), (7159, 0.3, 1), (7156, 0.05, 1), (7207, 0.3, 2), (7220, 0.05, 2))
+
+
+def find_equilibrium(sp, si, torch, grid=(48, 35, 48), re=400.0):
     """A nontrivial plane Couette equilibrium: Newton-GMRES-hookstep with laminar advection in
-    L from a seeded perturbed-laminar guess (modes |ix|, |iz| <= 1). From seed 7123 it reaches
-    a state with a spanwise-fundamental streak pair and a mean-flow correction (weighted norm
-    0.2243, energy input 1.43 times the laminar one) at 48 x 35 x 48, Re 400."""
+    L from seeded perturbed-laminar guesses, keeping the first root with weighted norm above
+    0.2: the state with the box's fundamental spanwise streak pair and a mean-flow correction
+    (norm 0.2243, energy input 1.43 times the laminar one at 48 x 35 x 48, Re 400). The other
+    roots these guesses reach have norms 0.11 to 0.15. Which root a guess reaches depends on
+    rounding along the Newton path, hence the list."""
     ctx = sp.Context(sp.Config(*grid, lx=LX, lz=LZ, re=re, dt=DT, prec=sp.SP_MIXED, lam_adv=1))
-    a, b, c = si.couette_random_coeffs(seed, *grid, mmax=1)
-    U = ctx.zeros()
-    ctx.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], amp, U)
+    tried = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rep = ctx.sp_newton_gmres(U, max_newton=40, max_krylov=300, tol=1e-10)
+    for seed, amp, mmax in EQ_SEEDS:
+        a, b, c = si.couette_random_coeffs(seed, *grid, mmax=mmax)
+        U = ctx.zeros()
+        ctx.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], amp, U)
+        rep = ctx.sp_newton_gmres(U, max_newton=40, max_krylov=300, tol=1e-10)
+        rep["norm_U"] = math.sqrt(ctx.sp_inner(U, U)[0])
+        tried.append({"seed": seed, "amplitude": amp, "mmax": mmax, "converged": rep["converged"],
+                      "norm_U": rep["norm_U"]})
+        if rep["converged"] and rep["norm_U"] > 0.2:
+            break
     torch.cuda.synchronize()
     rep["wall_s"] = time.perf_counter() - t0
-    rep["norm_U"] = math.sqrt(ctx.sp_inner(U, U)[0])
+    rep["tried"] = tried
     ctx.close()
+    if not (rep["converged"] and rep["norm_U"] > 0.2):
+        raise RuntimeError(f"no seeded guess reached the equilibrium: {tried}")
     return U, rep
 
 
@@ -840,7 +856,7 @@ def run_eq(args):
     import seeded_inputs as si
     grid = (48, 35, 48)
     U400, rep0 = find_equilibrium(sp, si, torch)
-    eq = {k: rep0[k] for k in ("converged", "newton_iters", "total_jvps", "norm_F", "wall_s", "norm_U")}
+    eq = {k: rep0[k] for k in ("converged", "newton_iters", "total_jvps", "norm_F", "wall_s", "norm_U", "tried")}
     runs = []
     cases = [("stokes", 100.0, None, 0, 30, 300), ("stokes", 10.0, None, 0, 30, 300), ("stokes", 1.0, None, 0, 30, 300),
              ("stokes", 100.0, None, 1, 30, 300), ("int", 0.25, 1 / 32, 0, 30, 300),
@@ -866,7 +882,7 @@ def run_eq(args):
     out = {"metric": "timesteps and time to |F|<1e-10, continuation from an equilibrium (Re 400 -> 380)",
            "unit": "timesteps", "higher_is_better": False,
            "config": {"workload": "plane Couette 48x35x48, box 2pi/1.14 x 2 x 2pi/2.5, mixed tangent; initial "
-                                  "guess: the equilibrium at Re 400 found from seed 7123; target Re 380", "eta": 1e-3},
+                                  "guess: the equilibrium at Re 400 found from the seeded guesses of EQ_SEEDS; target Re 380", "eta": 1e-3},
            "equilibrium_search": eq, "runs": runs}
     st = [r for r in runs if r["operator"] == "G^Stokes_T" and r["T"] == 100.0 and not r["laminar_advection_in_L"]][0]
     conv_int = [r for r in runs if r["operator"] == "G^int_T" and r["converged"]]
@@ -967,7 +983,7 @@ def run_eq_spectra(args):
         "workload": "equilibrium of --eq continued to Re 500 (48x35x48; leading eigenvalue by power iteration "
                     "on the propagator, dt = 1/256, T = 5); dense spectra on 12x25x12 (re-converged there), "
                     "FP64 tangent, restricted to the physical subspace"},
-        "equilibrium_search": {k: rep0[k] for k in ("converged", "newton_iters", "norm_F", "norm_U")},
+        "equilibrium_search": {k: rep0[k] for k in ("converged", "newton_iters", "norm_F", "norm_U", "tried")},
         "continuation_48x35x48": cont, "leading_eigenvalue_48x35x48": lead,
         "continuation_12x25x12": cont_small, "subspace_dim": int(Q.shape[1]), "spectra_12x25x12": specs}
     print(json.dumps(out))

@@ -91,7 +91,7 @@ static void free_ctx(sp_ctx* c) {
   void* ptrs[] = {c->Th, c->TDh, c->Cfh, c->yv, c->lam6, c->Th_f, c->TDh_f, c->Cfh_f, c->twx, c->twz, c->base32t,
                   c->twx_f, c->twz_f, c->ops, c->ws6, c->ws3, c->base64, c->base32, c->U0,
                   c->G0, c->tmp, c->red, c->kry, c->wsG, c->pops, c->fd_w1, c->fd_c1, c->dzU,
-                  c->traj, c->nbuf};
+                  c->traj, c->nbuf, c->traj_base};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -560,6 +560,28 @@ extern "C" sp_status sp_step_n(sp_ctx* c, const double* U, double* G, int n, voi
   return step_n(c, U, G, n, (cudaStream_t)stream);
 }
 
+// bytes of one trajectory step's base fields in the precision of the tangent
+static size_t base_slot_bytes(const sp_ctx* c) {
+  const size_t grid = (size_t)6 * c->NY * c->nx * c->nz;
+  return c->cfg.prec == SP_MIXED ? 2 * grid * 4 : grid * 8;
+}
+
+// copy the base fields of the tangent's precision to (save = true) or from trajectory slot k
+static sp_status base_slot(sp_ctx* c, int k, bool save, cudaStream_t st) {
+  const size_t grid = (size_t)6 * c->NY * c->nx * c->nz;
+  unsigned char* slot = c->traj_base + (size_t)k * base_slot_bytes(c);
+  auto cp = [&](void* live, unsigned char* p, size_t bytes) {
+    return save ? cudaMemcpyAsync(p, live, bytes, cudaMemcpyDeviceToDevice, st)
+                : cudaMemcpyAsync(live, p, bytes, cudaMemcpyDeviceToDevice, st);
+  };
+  if (c->cfg.prec == SP_MIXED) {
+    cudaError_t e = cp(c->base32, slot, grid * 4);
+    if (e == cudaSuccess) e = cp(c->base32t, slot + grid * 4, grid * 4);
+    return sp_cuda(c, e, "trajectory base fields");
+  }
+  return sp_cuda(c, cp(c->base64, slot, grid * 8), "trajectory base fields");
+}
+
 extern "C" sp_status sp_set_base_n(sp_ctx* c, const double* U, int n, void* stream) {
   if (!c || !U || n < 1) return sp_fail(c, SP_EINVAL, "sp_set_base_n: bad arguments");
   cudaStream_t st = (cudaStream_t)stream;
@@ -568,21 +590,47 @@ extern "C" sp_status sp_set_base_n(sp_ctx* c, const double* U, int n, void* stre
   if (c->geom != 0) return sp_fail(c, SP_EINVAL, "sp_set_base_n: n > 1 needs a plane Couette context");
   if ((s = ensure_buf(c, &c->traj, &c->traj_cap, n, "trajectory allocation")) != SP_OK) return s;
   const size_t L = c->state_len;
+  // base fields of every step, if they fit in a quarter of the free memory
+  c->traj_base_n = 0;
+  const size_t need = base_slot_bytes(c) * (size_t)n;
+  if (c->traj_base_bytes < need) {
+    size_t freeb = 0, totb = 0;
+    if (cudaMemGetInfo(&freeb, &totb) == cudaSuccess && need <= freeb / 4) {
+      if (c->traj_base) cudaFree(c->traj_base);
+      c->traj_base = nullptr;
+      c->traj_base_bytes = 0;
+      if (cudaMalloc((void**)&c->traj_base, need) == cudaSuccess) c->traj_base_bytes = need;
+      else cudaGetLastError();
+    }
+  }
+  const bool keep = c->traj_base_bytes >= need;
   if ((s = sp_cuda(c, cudaMemcpyAsync(c->traj, U, L * 8, cudaMemcpyDeviceToDevice, st), "copy")) != SP_OK) return s;
   if ((s = sp_cuda(c, cudaMemcpyAsync(c->U0, U, L * 8, cudaMemcpyDeviceToDevice, st), "copy")) != SP_OK) return s;
   double* D = c->G0;  // step increments, then G^int(U) for the finite-difference action
-  for (int k = 0; k + 1 < n; ++k) {
+  for (int k = 0; k < n; ++k) {
     const double* Xk = c->traj + (size_t)k * L;
-    if ((s = step_batch(c, Xk, D, 1, st)) != SP_OK) return s;
-    if ((s = sp_cuda(c, launch_axpby(c->traj + (size_t)(k + 1) * L, 1.0, Xk, 1.0, D, L, st), "axpby")) != SP_OK)
+    if (keep) {
+      // one pass gives the step's product and the base fields of U_k (as in sp_set_base)
+      if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_yinv(c, false, Xk, c->ws6, 1, st); }), "yinv")) != SP_OK) return s;
+      if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_xz(c, false, XZ_STEP_BASE, c->ws6, c->ws3, 1, st); }), "xz step+base")) != SP_OK) return s;
+      if (c->cfg.prec == SP_MIXED &&
+          (s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_base_to_f32(c, st); }), "base f32")) != SP_OK)
+        return s;
+      if ((s = base_slot(c, k, true, st)) != SP_OK) return s;
+      if ((s = sp_cuda(c, traced(c, SP_STAGE_STEP, st, [&] { return launch_solve(c, false, c->ws3, Xk, D, 1, st, c->solve_shape_step); }), "solve")) != SP_OK) return s;
+    } else if ((s = step_batch(c, Xk, D, 1, st)) != SP_OK) {
+      return s;
+    }
+    if (k + 1 < n &&
+        (s = sp_cuda(c, launch_axpby(c->traj + (size_t)(k + 1) * L, 1.0, Xk, 1.0, D, L, st), "axpby")) != SP_OK)
       return s;
   }
+  // D = U_n - U_{n-1}; G0 = U_n - U_0 = (U_{n-1} - U_0) + D
   const double* Xl = c->traj + (size_t)(n - 1) * L;
-  if ((s = step_batch(c, Xl, D, 1, st)) != SP_OK) return s;  // D = U_n - U_{n-1}
-  // G0 = U_n - U_0 = (U_{n-1} - U_0) + D
   if ((s = sp_cuda(c, launch_axpby(D, 1.0, D, 1.0, Xl, L, st), "axpby")) != SP_OK) return s;
   if ((s = sp_cuda(c, launch_axpby(D, 1.0, D, -1.0, U, L, st), "axpby")) != SP_OK) return s;
   c->traj_n = n;
+  c->traj_base_n = keep ? n : 0;
   c->has_base = 0;  // the single-step base fields are overwritten along the trajectory
   return SP_OK;
 }
@@ -602,7 +650,9 @@ extern "C" sp_status sp_jvp_n(sp_ctx* c, const double* du, double* Jdu, int n_di
     if ((s = sp_cuda(c, cudaMemcpyAsync(g, u, (size_t)nb * L * 8, cudaMemcpyDeviceToDevice, st), "copy")) != SP_OK)
       return s;
     for (int k = 0; k < c->traj_n; ++k) {
-      if ((s = base_fields(c, c->traj + (size_t)k * L, st)) != SP_OK) return s;
+      if (c->traj_base_n == c->traj_n) s = base_slot(c, k, false, st);
+      else s = base_fields(c, c->traj + (size_t)k * L, st);
+      if (s != SP_OK) return s;
       if ((s = sp_cuda(c, traced(c, SP_STAGE_YINV, st, [&] { return launch_yinv(c, f32, g, c->ws6, nb, st); }), "yinv")) != SP_OK)
         return s;
       if ((s = sp_cuda(c, traced(c, SP_STAGE_XZ, st, [&] { return launch_xz(c, f32, XZ_TANGENT, c->ws6, c->ws3, nb, st); }),

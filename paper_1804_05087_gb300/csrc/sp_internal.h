@@ -121,6 +121,12 @@ struct sp_ctx {
   double* traj = nullptr;        // [traj_cap] states: U_0 .. U_{n-1} of the last sp_set_base_n
   int traj_cap = 0;
   int traj_n = 0;                // steps of the stored trajectory (0: none)
+  // base fields of every trajectory step, in the precision the tangent reads (float base32 and
+  // base32t in mixed mode, base64 in FP64), so that sp_jvp_n does not recompute them; not
+  // kept (traj_base_n = 0) when they would take more than a quarter of the free memory
+  unsigned char* traj_base = nullptr;
+  size_t traj_base_bytes = 0;
+  int traj_base_n = 0;
   double* nbuf = nullptr;        // [2] states: scratch of sp_step_n
   // host-buffer tangent (sp_jvp_host): two copy streams, double-buffered device slots
   cudaStream_t hs_in = nullptr, hs_out = nullptr;
