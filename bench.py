@@ -148,7 +148,7 @@ def kernel_flops(stage, n_dir):
 # one ncu capture of that launch (dram__bytes_read.sum, dram__bytes_write.sum). The
 # reads are 64 x (values + state) plus the per-mode operators once; both scale with the
 # directions except the operators.
-K_SOLVE_DRAM_64 = (164491520, 72370944)
+K_SOLVE_DRAM_64 = (164997632, 72500224)
 
 
 def solve_traffic(n_dir):
