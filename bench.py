@@ -77,6 +77,35 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+# ----------------------------------------------------------------- replicas (one process per GPU)
+# The path has no exchange step: every rank processes its own units and the ranks meet only
+# to time the slowest one.
+def rank_direction_seeds(rank, nd):
+    """Seeds of one rank's nd tangent directions: disjoint across ranks (weak scaling)."""
+    return [DIR_SEED0 + rank * nd + i for i in range(nd)]
+
+
+def shard(units, rank, world):
+    """Round-robin share of independent units (directions, group members) for one rank."""
+    return list(units)[rank::world]
+
+
+def max_over_ranks(ms, world, device="cuda"):
+    """The slowest rank's time: one all-reduce of a scalar, the only collective."""
+    if world == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, units_per_rank, steps, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank * steps / (ms * 1e-3)
+
+
 # ----------------------------------------------------------------- workload sizes
 def dims():
     kx, kz = (NX - 1) // 3, (NZ - 1) // 3
@@ -1037,8 +1066,9 @@ def main():
         return ctx.sp_seed_state(*tr, amp, U)
     U = seeded(BASE_SEED, 0.1)
     D = ctx.zeros(nd)
+    dir_seeds = rank_direction_seeds(rank, nd)
     for i in range(nd):
-        D[i].copy_(seeded(DIR_SEED0 + rank * nd + i, 1.0))
+        D[i].copy_(seeded(dir_seeds[i], 1.0))
     OUT = ctx.zeros(nd)
     stream = torch.cuda.current_stream()
     tune = ctx.sp_autotune(nd)  # tile shapes of the solve kernel, before any timing
@@ -1065,11 +1095,8 @@ def main():
     trace = ctx.sp_trace_read()
     ctx.sp_trace_enable(False)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * nd * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(ms, world)
+    value = aggregate_rate(world, nd, args.steps, ms)
     launches = int(sum(v[1] for v in trace.values()))
 
     # end to end through the public API with host buffers (pinned), copies timed
@@ -1095,11 +1122,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms_e], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms_e = float(t.item())
-        e2e = {"value": world * nd * args.steps / (ms_e * 1e-3), "unit": "JVP/s",
+        ms_e = max_over_ranks(ms_e, world)
+        e2e = {"value": aggregate_rate(world, nd, args.steps, ms_e), "unit": "JVP/s",
                "h2d_bytes_per_step": hD.numel() * 16 + hU.numel() * 16, "d2h_bytes_per_step": hO.numel() * 16}
 
     # roofline of the dominant kernel (live CUDA-event durations)
