@@ -370,7 +370,7 @@ def run_config4(args):
     U4 = seeded(ctx_la, 6000, 0.1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rep3 = ctx_la.sp_newton_gmres(U4, max_newton=20, max_krylov=300, tol=1e-10, eta=1e-3)
+    rep3 = ctx_la.sp_newton_gmres(U4, max_newton=40, max_krylov=300, tol=1e-10, eta=1e-3)
     torch.cuda.synchronize()
     rep3["wall_s"] = time.perf_counter() - t0
     rep3["norm_U"] = math.sqrt(ctx_la.sp_inner(U4, U4)[0])
@@ -380,7 +380,7 @@ def run_config4(args):
            "gradient_check": {"directions": 32, "h": h, "max_rel_err": max(errs), "median_rel_err": statistics.median(errs),
                               "vjp_ms": 1e3 * t_vjp},
            "newton": rep, "newton_to_convergence": dict(rep2, max_newton=20, max_krylov=300),
-           "newton_laminar_advection_in_L": dict(rep3, max_newton=20, max_krylov=300)}
+           "newton_laminar_advection_in_L": dict(rep3, max_newton=40, max_krylov=300)}
     print(json.dumps(out))
 
 
