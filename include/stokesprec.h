@@ -336,6 +336,30 @@ typedef struct {
 sp_status sp_newton_gmres(sp_ctx* ctx, double* U_inout, const sp_newton_opts* opts,
                           sp_newton_report* report, void* stream);
 
+/* One Newton linear system G_U X = F (Sec. 2, Eq. linear) solved by a
+ * short-recurrence method (Sec. 3.6): krylov = 1 BiCGSTAB(l) (Sleijpen and
+ * Fokkema), krylov = 2 IDR(s) with biorthogonalised bases (van Gijzen and
+ * Sonneveld), param = l or s (1..8), from X = 0 until |r| <= eta |F| or
+ * max_act Jacobian actions (tangent steps at the linearisation point of the
+ * last sp_set_base, in the context's precision). The same solvers run inside
+ * sp_newton_gmres with opts->krylov = 1, 2.
+ * F, X: device states (layout and inner product as above), not aliased.
+ * shadow: device pointer to the BiCGSTAB shadow residual (one state) or to
+ * the s IDR shadow vectors (s consecutive states, used as given: the caller
+ * makes them orthonormal), or NULL (F, resp. seeded vectors orthonormalised
+ * by the library).
+ * hist (host, max_hist entries): |r| at every residual update, |F| first
+ * (BiCGSTAB(l): after each minimal-residual part; IDR(s): after every update
+ * of r); *n_hist receives the full count (may exceed max_hist), *n_act the
+ * actions used (both may be NULL). A recurrence that breaks down or diverges
+ * hands back its smallest-residual iterate. The Krylov work vectors are
+ * allocated on first use and kept with the context. Synchronous.
+ * Errors: SP_EINVAL (bad arguments, no linearisation point), SP_ENOMEM,
+ * SP_ECUDA. */
+sp_status sp_krylov_solve(sp_ctx* ctx, const double* F, double* X, int krylov, int param, int max_act,
+                          double eta, const double* shadow, double* hist, int max_hist, int* n_hist,
+                          int* n_act, void* stream);
+
 /* ---- many independent problems at once -------------------------------------
  *
  * A group holds n independent plane Couette problems, each with its own grid,

@@ -123,3 +123,131 @@ def newton_hookstep(G, make_jvp, inner, U0, tol=1e-10, max_newton=20, max_k=30,
         if log is not None:
             log(rec)
     return U, history
+
+
+# --------------------------------------------------------------------------
+# Short-recurrence Krylov solvers (Sec. 3.6 names BiCGSTAB(l) and IDR as the
+# remedy for GMRES's K^2 orthogonalisation cost). Both solve A x = b from
+# x = 0 with the problem's inner product and stop when |r| <= eta |b| or after
+# max_act actions of A. They return (x, hist, acts): hist lists |r| at the
+# points the algorithms update r (BiCGSTAB(l): once per outer cycle, after the
+# minimal-residual part; IDR(s): after every residual update), starting with
+# |b|.
+
+def bicgstab_ell(apply_a, b, inner, ell, max_act, eta, r_shadow=None):
+    """BiCGSTAB(l) of Sleijpen and Fokkema (1993), in the paper's order:
+    l BiCG steps extend the bases r_0..r_l and u_0..u_l, then a minimal-residual
+    polynomial of degree l (modified Gram-Schmidt on r_1..r_l) updates x, r_0, u_0."""
+    nb = math.sqrt(inner(b, b))
+    x = np.zeros_like(b)
+    r = [b.copy()] + [np.zeros_like(b) for _ in range(ell)]
+    u = [np.zeros_like(b) for _ in range(ell + 1)]
+    rt = b.copy() if r_shadow is None else r_shadow
+    rho0, alpha, omega = 1.0, 0.0, 1.0
+    hist, acts = [nb], 0
+    rn = nb
+    while acts < max_act and rn > eta * nb:
+        rho0 = -omega * rho0
+        # BiCG part
+        for j in range(ell):
+            rho1 = inner(r[j], rt)
+            beta = alpha * rho1 / rho0
+            rho0 = rho1
+            for i in range(j + 1):
+                u[i] = r[i] - beta * u[i]
+            u[j + 1] = apply_a(u[j])
+            gamma = inner(u[j + 1], rt)
+            alpha = rho0 / gamma
+            for i in range(j + 1):
+                r[i] = r[i] - alpha * u[i + 1]
+            r[j + 1] = apply_a(r[j])
+            x = x + alpha * u[0]
+            acts += 2
+        # minimal-residual part
+        tau = np.zeros((ell + 1, ell + 1))
+        sigma = np.zeros(ell + 1)
+        gp = np.zeros(ell + 1)
+        for j in range(1, ell + 1):
+            for i in range(1, j):
+                tau[i, j] = inner(r[j], r[i]) / sigma[i]
+                r[j] = r[j] - tau[i, j] * r[i]
+            sigma[j] = inner(r[j], r[j])
+            gp[j] = inner(r[0], r[j]) / sigma[j]
+        g = np.zeros(ell + 1)
+        g[ell] = gp[ell]
+        omega = g[ell]
+        for j in range(ell - 1, 0, -1):
+            g[j] = gp[j] - sum(tau[j, i] * g[i] for i in range(j + 1, ell + 1))
+        gpp = np.zeros(ell + 1)
+        for j in range(1, ell):
+            gpp[j] = g[j + 1] + sum(tau[j, i] * g[i + 1] for i in range(j + 1, ell))
+        x = x + g[1] * r[0]
+        r[0] = r[0] - gp[ell] * r[ell]
+        u[0] = u[0] - g[ell] * u[ell]
+        for j in range(1, ell):
+            u[0] = u[0] - g[j] * u[j]
+            x = x + gpp[j] * r[j]
+            r[0] = r[0] - gp[j] * r[j]
+        rn = math.sqrt(inner(r[0], r[0]))
+        hist.append(rn)
+        if not np.isfinite(rn):
+            break
+    return x, hist, acts
+
+
+def idr_s(apply_a, b, inner, P, max_act, eta, kappa=0.7):
+    """IDR(s) with biorthogonalised bases (van Gijzen and Sonneveld, 2011), in their
+    order: per cycle s directions u_k (g_k = A u_k) made biorthogonal to the shadow
+    vectors P, each followed by a residual update; then the dimension-reduction
+    step with the minimal-residual omega, raised to kappa |r|/|t| relative size when
+    the angle between t = A r and r is small ("maintaining the convergence";
+    kappa = 0 turns that off)."""
+    s = len(P)
+    nb = math.sqrt(inner(b, b))
+    x = np.zeros_like(b)
+    r = b.copy()
+    g = [np.zeros_like(b) for _ in range(s)]
+    u = [np.zeros_like(b) for _ in range(s)]
+    M = np.eye(s)
+    omega = 1.0
+    hist, acts = [nb], 0
+    rn = nb
+    while acts < max_act and rn > eta * nb:
+        f = np.array([inner(P[i], r) for i in range(s)])
+        for k in range(s):
+            c = np.zeros(s)
+            for i in range(k, s):  # M[k:, k:] c = f[k:], lower triangular
+                c[i] = (f[i] - sum(M[i, j] * c[j] for j in range(k, i))) / M[i, i]
+            v = r - sum(c[i] * g[i] for i in range(k, s))
+            u[k] = omega * v + sum(c[i] * u[i] for i in range(k, s))
+            g[k] = apply_a(u[k])
+            acts += 1
+            for i in range(k):
+                a = inner(P[i], g[k]) / M[i, i]
+                g[k] = g[k] - a * g[i]
+                u[k] = u[k] - a * u[i]
+            for i in range(k, s):
+                M[i, k] = inner(P[i], g[k])
+            beta = f[k] / M[k, k]
+            r = r - beta * g[k]
+            x = x + beta * u[k]
+            rn = math.sqrt(inner(r, r))
+            hist.append(rn)
+            if rn <= eta * nb or acts >= max_act:
+                break
+            for i in range(k + 1, s):
+                f[i] = f[i] - beta * M[i, k]
+        if rn <= eta * nb or acts >= max_act:
+            break
+        t = apply_a(r)
+        acts += 1
+        tt, tr = inner(t, t), inner(t, r)
+        omega = tr / tt
+        rho = abs(tr) / (math.sqrt(tt) * rn)
+        if rho < kappa:
+            omega = omega * kappa / rho
+        x = x + omega * r
+        r = r - omega * t
+        rn = math.sqrt(inner(r, r))
+        hist.append(rn)
+    return x, hist, acts

@@ -85,6 +85,8 @@ def _load():
         "sp_jvp_fd": ([P, P, P, I, V], I),
         "sp_inner": ([P, P, P, I, ctypes.POINTER(D), V], I),
         "sp_newton_gmres": ([P, P, ctypes.POINTER(_NewtonOpts), ctypes.POINTER(_NewtonReport), V], I),
+        "sp_krylov_solve": ([P, P, P, I, I, I, D, P, ctypes.POINTER(D), I, ctypes.POINTER(I), ctypes.POINTER(I), V],
+                            I),
         "sp_jvp_static": ([P, P, P, V], I),
         "sp_vjp_euclid": ([P, P, P, I, V], I),
         "sp_trace_enable": ([P, I], I),
@@ -125,7 +127,7 @@ EXPORTS = ("sp_create", "sp_destroy", "sp_last_error", "sp_state_len", "sp_dims"
            "sp_group_state_len", "sp_group_offset", "sp_group_member", "sp_group_step", "sp_group_set_base",
            "sp_group_jvp", "sp_group_inner", "sp_group_newton_gmres", "sp_autotune",
            "sp_set_solve_shape", "sp_step_n", "sp_set_base_n", "sp_jvp_n",
-           "sp_jvp_host")
+           "sp_jvp_host", "sp_krylov_solve")
 STAGES = ("k_yinv", "k_xz", "k_solve", "step", "vector")
 
 
@@ -380,6 +382,22 @@ class Context:
         if st not in (0, 4):
             self._check(st)
         return rep
+
+
+    def sp_krylov_solve(self, F, X, krylov="bicgstab", param=2, max_act=1000, eta=1e-3, shadow=None,
+                        max_hist=4096, stream=None):
+        """Solve G_U X = F at the linearisation point with BiCGSTAB(l) or IDR(s).
+        shadow: None, or 1 (BiCGSTAB) / s (IDR) states. Returns (|r| history, actions)."""
+        pf, _ = self._ptr(F, 1)
+        px, _ = self._ptr(X, 1)
+        ps = None
+        if shadow is not None:
+            ps, n = self._ptr(shadow, 1 if krylov == "bicgstab" else int(param))
+        h = (ctypes.c_double * max_hist)()
+        nh, na = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(_lib.sp_krylov_solve(self._h, pf, px, KRYLOV[krylov], int(param), int(max_act), float(eta), ps,
+                                         h, max_hist, ctypes.byref(nh), ctypes.byref(na), _stream(stream)))
+        return [h[i] for i in range(min(nh.value, max_hist))], na.value
 
 
 KRYLOV = {"gmres": 0, "bicgstab": 1, "idr": 2}

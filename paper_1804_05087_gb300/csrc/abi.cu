@@ -762,6 +762,11 @@ struct ShortKrylov {
   sp_newton_report* rep;
   cudaStream_t st;
   size_t L;
+  const double* shadow = nullptr;      // caller's shadow vector(s) (device), or null
+  std::vector<double>* hist = nullptr;  // |r| at every residual update, or null
+  void record(double rn) const {
+    if (hist) hist->push_back(rn);
+  }
   sp_status dot(const double* a, const double* b, double* out) const { return inner_many(c, a, 1, b, out, st); }
   sp_status dots(const double* V, int k, const double* w, double* out) const { return inner_many(c, V, k, w, out, st); }
   sp_status axpby(double* out, double a, const double* x, double b, const double* y) const {
@@ -793,10 +798,11 @@ static sp_status bicgstab_solve(const ShortKrylov& k, double* W, const double* F
   const int max_act = std::max(2, k.o->max_krylov);
   sp_status s;
   std::vector<double> tau((size_t)(ell + 1) * (ell + 1)), sigma(ell + 1), gp(ell + 1), g(ell + 1), gpp(ell + 1);
-  if ((s = k.copy(r(0), F)) != SP_OK || (s = k.copy(Rt, F)) != SP_OK || (s = k.zero(u(0))) != SP_OK ||
-      (s = k.zero(X)) != SP_OK)
+  if ((s = k.copy(r(0), F)) != SP_OK || (s = k.copy(Rt, k.shadow ? k.shadow : F)) != SP_OK ||
+      (s = k.zero(u(0))) != SP_OK || (s = k.zero(X)) != SP_OK)
     return s;
   double rho0 = 1.0, alpha = 0.0, omega = 1.0, rn = nF, best = nF;
+  k.record(nF);
   if ((s = k.zero(Xb)) != SP_OK) return s;
   int acts = 0;
   bool broke = false;
@@ -859,6 +865,7 @@ static sp_status bicgstab_solve(const ShortKrylov& k, double* W, const double* F
     }
     if ((s = k.dot(r(0), r(0), &rn)) != SP_OK) return s;
     rn = std::sqrt(rn);
+    k.record(rn);
     if (!std::isfinite(rn) || omega == 0.0) broke = true;
     if (std::isfinite(rn) && rn < best) {
       best = rn;
@@ -888,8 +895,13 @@ static sp_status idr_solve(const ShortKrylov& k, double* W, const double* F, dou
   auto uv = [&](int i) { return Us + (size_t)i * L; };
   const int max_act = std::max(2, k.o->max_krylov);
   sp_status s;
-  // shadow space: seeded normal vectors, orthonormalised (modified Gram-Schmidt)
-  {
+  // shadow space: the caller's s vectors as given, else seeded normal vectors
+  // orthonormalised by modified Gram-Schmidt
+  if (k.shadow) {
+    if ((s = k.copy(P, k.shadow)) != SP_OK) return s;
+    for (int i = 1; i < sdim; ++i)
+      if ((s = k.copy(pv(i), k.shadow + (size_t)i * L)) != SP_OK) return s;
+  } else {
     std::vector<double> h((size_t)sdim * L);
     uint64_t z = 0x9E3779B97F4A7C15ull;
     for (size_t i = 0; i < h.size(); ++i) {  // splitmix64 + Box-Muller
@@ -925,6 +937,7 @@ static sp_status idr_solve(const ShortKrylov& k, double* W, const double* F, dou
   std::vector<double> M((size_t)sdim * sdim, 0.0), f(sdim), cc(sdim), col(sdim);
   for (int i = 0; i < sdim; ++i) M[(size_t)i * sdim + i] = 1.0;
   double om = 1.0, rn = nF, best = nF;
+  k.record(nF);
   if ((s = k.zero(Xb)) != SP_OK) return s;
   auto keep_best = [&]() -> sp_status {
     if (std::isfinite(rn) && rn < best) {
@@ -971,6 +984,7 @@ static sp_status idr_solve(const ShortKrylov& k, double* W, const double* F, dou
       if ((s = k.axpby(X, 1.0, X, beta, uv(kk))) != SP_OK) return s;
       if ((s = k.dot(r, r, &rn)) != SP_OK) return s;
       rn = std::sqrt(rn);
+      k.record(rn);
       if (!std::isfinite(rn)) { broke = true; break; }
       if ((s = keep_best()) != SP_OK) return s;
       if (rn <= k.o->eta * nF || acts >= max_act) break;
@@ -991,6 +1005,7 @@ static sp_status idr_solve(const ShortKrylov& k, double* W, const double* F, dou
     if ((s = k.axpby(r, 1.0, r, -om, t)) != SP_OK) return s;
     if ((s = k.dot(r, r, &rn)) != SP_OK) return s;
     rn = std::sqrt(rn);
+    k.record(rn);
     if (!std::isfinite(rn)) break;
     if ((s = keep_best()) != SP_OK) return s;
   }
@@ -1002,20 +1017,31 @@ static sp_status idr_solve(const ShortKrylov& k, double* W, const double* F, dou
 // Newton with a short-recurrence linear solver (krylov = 1: BiCGSTAB(ell), 2: IDR(s)) and a
 // trust region along the computed direction X (the hookstep's radius update): the step
 // s X with s = min(1, delta/|X|), its predicted residual |F - s J X| from one more action.
-static sp_status newton_short(sp_ctx* c, double* U, const sp_newton_opts* o, sp_newton_report* rep, cudaStream_t st) {
-  const size_t L = c->state_len;
-  const int nsolve = o->krylov == 2 ? 3 * idr_s(o) + 3 : 2 * (bicgstab_ell(o) + 1) + 1;
-  const int nvec = nsolve + 5;
+static void drop_newton_graphs(sp_ctx* c);
+
+// work vectors of the short-recurrence solvers: the solver's own plus five
+static sp_status short_vectors(sp_ctx* c, const sp_newton_opts* o, int* nsolve) {
+  *nsolve = o->krylov == 2 ? 3 * idr_s(o) + 3 : 2 * (bicgstab_ell(o) + 1) + 1;
+  const int nvec = *nsolve + 5;
   if (c->kry_cap < nvec) {
+    drop_newton_graphs(c);  // they hold pointers into the old basis
     if (c->kry) cudaFree(c->kry);
     c->kry = nullptr;
     c->kry_cap = 0;
-    if (cudaMalloc((void**)&c->kry, (size_t)nvec * L * 8) != cudaSuccess) {
+    if (cudaMalloc((void**)&c->kry, (size_t)nvec * c->state_len * 8) != cudaSuccess) {
       cudaGetLastError();
       return sp_fail(c, SP_ENOMEM, "short-recurrence Krylov vectors");
     }
     c->kry_cap = nvec;
   }
+  return SP_OK;
+}
+
+static sp_status newton_short(sp_ctx* c, double* U, const sp_newton_opts* o, sp_newton_report* rep, cudaStream_t st) {
+  const size_t L = c->state_len;
+  int nsolve;
+  sp_status sv = short_vectors(c, o, &nsolve);
+  if (sv != SP_OK) return sv;
   double* W = c->kry;
   double* X = c->kry + (size_t)nsolve * L;  // the Newton correction
   double* F = X + L;                        // G(U)
@@ -1082,6 +1108,48 @@ static sp_status newton_short(sp_ctx* c, double* U, const sp_newton_opts* o, sp_
 static void drop_newton_graphs(sp_ctx* c) {
   for (auto& kv : c->ngraphs) cudaGraphExecDestroy(kv.second);
   c->ngraphs.clear();
+}
+
+extern "C" sp_status sp_krylov_solve(sp_ctx* c, const double* F, double* X, int krylov, int param, int max_act,
+                                     double eta, const double* shadow, double* hist, int max_hist, int* n_hist,
+                                     int* n_act, void* stream) {
+  if (!c || !F || !X || (krylov != 1 && krylov != 2) || max_act < 1 || !(eta >= 0.0) || max_hist < 0 ||
+      (max_hist > 0 && !hist))
+    return sp_fail(c, SP_EINVAL, "sp_krylov_solve: bad arguments");
+  if (param < 1 || param > 8) return sp_fail(c, SP_EINVAL, "sp_krylov_solve: l or s must be in 1..8");
+  if (!c->has_base) return sp_fail(c, SP_EINVAL, "sp_krylov_solve: no linearisation point (sp_set_base)");
+  if (F == X) return sp_fail(c, SP_EINVAL, "sp_krylov_solve: F and X must not alias");
+  sp_newton_opts o{};
+  o.krylov = krylov;
+  o.ell = param;
+  o.max_krylov = max_act;
+  o.eta = eta;
+  int nsolve;
+  sp_status s = short_vectors(c, &o, &nsolve);
+  if (s != SP_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t L = c->state_len;
+  double* W = c->kry;
+  double* Xd = c->kry + (size_t)nsolve * L;
+  double* Xb = Xd + L;
+  sp_newton_report rep{};
+  std::vector<double> h;
+  ShortKrylov k{c, &o, &rep, st, L};
+  k.shadow = shadow;
+  k.hist = &h;
+  if ((s = sp_cuda(c, cudaStreamSynchronize(st), "krylov sync")) != SP_OK) return s;
+  double nF;
+  if ((s = k.dot(F, F, &nF)) != SP_OK) return s;
+  nF = std::sqrt(nF);
+  s = krylov == 2 ? idr_solve(k, W, F, nF, Xd, Xb) : bicgstab_solve(k, W, F, nF, Xd, Xb);
+  if (s != SP_OK) return s;
+  if ((s = k.copy(X, Xd)) != SP_OK) return s;
+  if ((s = sp_cuda(c, cudaStreamSynchronize(st), "krylov sync")) != SP_OK) return s;
+  const int nh = (int)std::min<size_t>(h.size(), (size_t)max_hist);
+  for (int i = 0; i < nh; ++i) hist[i] = h[i];
+  if (n_hist) *n_hist = (int)h.size();
+  if (n_act) *n_act = rep.total_jvps;
+  return SP_OK;
 }
 
 extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts* o, sp_newton_report* rep,

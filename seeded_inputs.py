@@ -124,3 +124,13 @@ def pipe_random_coeffs(seed, kz, mt, kmax=2, mmax=3, npoly=4):
                 pm = (-kk) if -kk >= 0 else -kk + mk
                 pol[pm, 0] = np.conj(pol[p, 0])
     return streak, pol
+
+
+def idr_shadow(s: int, nx: int, ny: int, nz: int, seed: int = 77):
+    """``s`` state-shaped standard-normal arrays complex128 [3][MX][MZ][NY]: the raw
+    shadow vectors of IDR(s) (and, with s = 1, a BiCGSTAB shadow residual). The
+    solver's caller projects and orthonormalises them in its own inner product."""
+    kx, kz, mx, mz, nyy = couette_dims(nx, ny, nz)
+    rng = np.random.default_rng(seed)
+    r = rng.standard_normal((s, 2, 3, mx, mz, nyy))
+    return [r[i, 0] + 1j * r[i, 1] for i in range(s)]
