@@ -42,7 +42,10 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--prec", default="fp64", choices=["mixed", "fp64"],
+                   help="precision of the headline value; the other one is reported beside it")
+    p.add_argument("--single-prec", action="store_true", help="time only the --prec precision")
+    p.add_argument("--no-newton", action="store_true", help="skip the time-to-converge block")
     p.add_argument("--ndir", type=int, default=256)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -118,16 +121,34 @@ def n_unique():
     return (kx + 1) * mz + kx * (mz - 1)
 
 
+CHAIN_MIN_BATCH = 32  # contexts with max_batch >= this solve the tangent by O(N) chains
+
+
+def chain(n_dir):
+    """The batched tangent's per-mode solve is k_rhs + the O(N) chain kernel (k_solve stage)."""
+    return n_dir >= CHAIN_MIN_BATCH and not LAM_ADV
+
+
+def chain_record_doubles():
+    nh = (NY - 1) // 2 + 1
+    return 2 * (10 * nh + 8)
+
+
 def kernel_bytes(stage, n_dir, esz):
     """Algorithmic HBM bytes of one launch (each datum read or written once)."""
     kx, kz, mx, mz, ny = dims()
     mm = mx * mz
     state = 3 * mm * ny * 16
+    rhs = 3 * (ny - 2) * n_unique() * 16  # the chains' right-hand sides, FP64
     if stage == "k_yinv":
         return n_dir * (state + 6 * ny * mm * esz)
     if stage == "k_xz":
         return n_dir * 9 * ny * mm * esz + 6 * ny * NX * NZ * esz // 2
+    if stage == "k_rhs":
+        return n_dir * (3 * ny * mm * esz + state + rhs)
     if stage == "k_solve":
+        if chain(n_dir):
+            return n_dir * (rhs + 2 * state) + n_unique() * chain_record_doubles() * 8
         ops = n_unique() * (la_op_entries() * 16 if LAM_ADV else op_entries() * 8)
         return n_dir * (3 * ny * mm * esz + 2 * state) + ops
     return 0
@@ -147,7 +168,7 @@ def la_op_entries():
     return 2 * (n - 1) * NY
 
 
-def kernel_flops(stage, n_dir):
+def kernel_flops(stage, n_dir, prec="mixed"):
     """Algorithmic floating-point operations of one launch (FFT: 5 n log2 n)."""
     kx, kz, mx, mz, ny = dims()
     mm = mx * mz
@@ -159,18 +180,51 @@ def kernel_flops(stage, n_dir):
         fz = 5 * NZ * math.log2(NZ)
         per_plane = (6 + 3) * mz * fx + (6 + 3) * (NX // 2) * fz + NX * NZ * 30
         return n_dir * ny * per_plane
+    if stage == "k_rhs":
+        # forward Chebyshev transform of the three product components: per row a real
+        # even/odd half-length dot product with complex values (4 flops per term) after one
+        # pairing pass (4 flops per value), plus du/dt (4 per row); FP64 in FP64 mode, only
+        # du/dt in FP64 in mixed mode (the transform is float there and not counted)
+        n = ny - 1
+        per = 3 * (n - 1) * 4
+        if prec == "fp64":
+            per += 3 * ((n - 1) * nh * 4 + ny * 4)
+        return n_dir * n_unique() * per
+    if stage == "k_solve" and chain(n_dir):
+        # O(N) chains, FP64, per (mode, parity) thread and coefficient: the w_A sweep with the
+        # reduced right-hand side (40 flops), the v_A sweep (24), the influence correction,
+        # G_v and the continuity suffix sum (20), the b sweep with the back-rotation and
+        # G_u, G_w (46): 130 flops per coefficient, NH coefficients per parity
+        return n_dir * n_unique() * 2 * nh * 130
     if stage == "k_solve":
-        # FP64 work only: the per-mode operators (real matrices on complex right-hand sides,
+        # FP64 work: the per-mode operators (real matrices on complex right-hand sides,
         # 4 flops per entry), the reduced right-hand side g (one complex FMA and one complex
-        # update per momentum row) and the continuity/rotation epilogue (16 per point); the
-        # Chebyshev transform (float in mixed mode) is excluded
+        # update per momentum row) and the continuity/rotation epilogue (16 per point).
         # With laminar advection in L: complex operators on complex right-hand sides (8 flops
         # per entry), plus the M du right-hand-side term and the v -> b coupling (10 per row).
+        # In FP64 mode the forward Chebyshev transform of the three product components is FP64
+        # too: per row, a real even/odd half-length dot product with complex values (4 flops
+        # per term), after one pairing pass (4 flops per value); in mixed mode it is float
+        # and not counted here.
         n = ny - 1
         if LAM_ADV:
-            return n_dir * n_unique() * (la_op_entries() * 8 + (n - 1) * 18 + ny * 16)
-        return n_dir * n_unique() * (op_entries() * 4 + (n - 1) * 8 + ny * 16)
+            per = la_op_entries() * 8 + (n - 1) * 18 + ny * 16
+        else:
+            per = op_entries() * 4 + (n - 1) * 8 + ny * 16
+        if prec == "fp64":
+            per += 3 * ((n - 1) * nh * 4 + ny * 4)
+        return n_dir * n_unique() * per
     return 0
+
+
+FP64_NOMINAL = 1.25  # TFLOP/s, the recipe's nominal GB300 FP64 rate (replaced by the measured probe)
+
+
+def kernel_traffic(stage, n_dir, prec, lam_adv):
+    """DRAM bytes of one launch from an ncu capture of the current kernel, or None."""
+    if stage == "k_solve" and prec == "mixed" and not lam_adv and not chain(n_dir):
+        return solve_traffic(n_dir)
+    return None
 
 
 # DRAM bytes of one mixed-precision k_solve tangent launch at 48x65x48 with 64 directions, from
@@ -1061,16 +1115,70 @@ def main():
     else:
         torch.cuda.set_device(0)
     import paper_1804_05087_gb300 as sp
-    import seeded_inputs as si
 
-    prec = sp.SP_MIXED if args.prec == "mixed" else sp.SP_FP64
-    esz = 8 if args.prec == "mixed" else 16
     global LAM_ADV
     LAM_ADV = bool(args.lam_adv)
+    head = throughput(args, args.prec, rank, world, local, keep_out=True)
+    other = None
+    if not args.single_prec:
+        # the other precision on the same inputs, with its per-field error against FP64
+        oth = "mixed" if args.prec == "fp64" else "fp64"
+        o = throughput(args, oth, rank, world, local, keep_out=True, e2e=False)
+        f64, mix = (head, o) if args.prec == "fp64" else (o, head)
+        err = field_errors(f64["out"], mix["out"])
+        other = {k: o[k] for k in ("value", "unit", "ms_per_step", "dtype", "roofline", "gpu_launches")}
+        other["precision"] = oth
+        other["per_field_rel_err_vs_fp64"] = err
+    peak = None
+    if rank == 0:
+        peak = measure_fp64_peak(sp, torch, local)
+        for r in (head, other):
+            if r is not None:
+                attach_fp64_peak(r["roofline"], peak)
+    ttc = None
+    if rank == 0 and world == 1 and not args.no_newton:
+        ttc = time_to_converge(args)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n, el = oracle_jvps(12.0)
+        cpu = {"value": rate, "unit": "JVP/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n} FP64 oracle tangent steps at 48x65x48 in {el:.1f} s (after its one-time LU setup)"}
+
+    if rank == 0:
+        nd = args.ndir
+        out = {"metric": METRIC, "value": head["value"], "unit": "JVP/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": head["dtype"], "data": "synthetic",
+               "config": {"workload": f"plane Couette 48x65x48, Re=400, dt=100, box 2pi/1.14 x 2 x 2pi/2.5; "
+                                      f"per step: set_base + tangent on {nd} seeded unit directions",
+                          "grid": [NX, NY, NZ], "ndir_per_gpu": nd, "precision": args.prec,
+                          "laminar_advection_in_L": bool(args.lam_adv),
+                          "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
+                          "solve_tile": head["solve_tile"]},
+               "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head["e2e"],
+               "gpu_launches": head["gpu_launches"], "clocks": head["clocks"]}
+        if other is not None:
+            out["mixed" if other["precision"] == "mixed" else "fp64"] = other
+        if peak is not None:
+            out["fp64_peak_probe"] = peak
+        if ttc is not None:
+            out["time_to_converge"] = ttc
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def throughput(args, prec_name, rank, world, local, keep_out=False, e2e=True):
+    """The timed step (set_base + tangent on the batch) in one precision."""
+    import torch
+    import paper_1804_05087_gb300 as sp
+    import seeded_inputs as si
+    prec = sp.SP_MIXED if prec_name == "mixed" else sp.SP_FP64
+    esz = 8 if prec_name == "mixed" else 16
     nd = args.ndir
     ctx = sp.Context(sp.Config(NX, NY, NZ, lx=LX, lz=LZ, re=RE, dt=DT, prec=prec, max_batch=nd,
                                lam_adv=1 if args.lam_adv else 0))
-    # seeded inputs, built on the device by the library
+
     def seeded(seed, amp):
         a, b, c = si.couette_random_coeffs(seed, NX, NY, NZ)
         U = ctx.zeros()
@@ -1112,8 +1220,8 @@ def main():
     launches = int(sum(v[1] for v in trace.values()))
 
     # end to end through the public API with host buffers (pinned), copies timed
-    e2e = None
-    if not args.no_e2e:
+    e2e_rec = None
+    if e2e and not args.no_e2e:
         hD = D.cpu().pin_memory()
         hU = U.cpu().pin_memory()
         hO = torch.empty_like(hD).pin_memory()
@@ -1135,58 +1243,117 @@ def main():
         torch.cuda.synchronize()
         ms_e = e0.elapsed_time(e1)
         ms_e = max_over_ranks(ms_e, world)
-        e2e = {"value": aggregate_rate(world, nd, args.steps, ms_e), "unit": "JVP/s",
-               "h2d_bytes_per_step": hD.numel() * 16 + hU.numel() * 16, "d2h_bytes_per_step": hO.numel() * 16}
+        e2e_rec = {"value": aggregate_rate(world, nd, args.steps, ms_e), "unit": "JVP/s",
+                   "h2d_bytes_per_step": hD.numel() * 16 + hU.numel() * 16, "d2h_bytes_per_step": hO.numel() * 16}
 
-    # roofline of the dominant kernel (live CUDA-event durations)
+    # roofline of the dominant kernel (live CUDA-event durations on the launching stream)
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
         peaks = json.load(f)
-    dom = max(("k_yinv", "k_xz", "k_solve"), key=lambda k: trace[k][0])
+    dom = max(("k_yinv", "k_xz", "k_rhs", "k_solve"), key=lambda k: trace[k][0] if trace[k][1] else -1.0)
     dom_ms, dom_n = trace[dom]
     avg_s = dom_ms / dom_n * 1e-3
-    ndir_launch = nd  # every tangent launch processes the whole batch
-    # the set_base launches (one state) are also in the family: count their share
-    bytes_l = kernel_bytes(dom, ndir_launch, esz)
-    flops_l = kernel_flops(dom, ndir_launch)
+    bytes_l = kernel_bytes(dom, nd, esz)  # every tangent launch processes the whole batch
+    flops_l = kernel_flops(dom, nd, prec_name)
     gbs = bytes_l / avg_s / 1e9
     tfs = flops_l / avg_s / 1e12
     hbm = peaks["hbm_gbs"]
-    fp64_peak = 1.25  # TFLOP/s, nominal FP64 (no FP64 entry in MEASURED_PEAKS.json)
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
-    alu_peak = fp64_peak if (args.prec == "fp64" or dom == "k_solve") else fp32_peak
+    fp64_bound = prec_name == "fp64" or dom == "k_solve"  # the solve is FP64 in both modes
+    alu_peak = FP64_NOMINAL if fp64_bound else fp32_peak
     if gbs / hbm >= tfs / alu_peak:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     else:
         roof = {"bound": "alu", "achieved": tfs, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfs / alu_peak,
-                "peak_source": "nominal FP64 1.25 TFLOP/s" if alu_peak == fp64_peak
-                else "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
-    roof.update({"kernel": dom, "traffic": solve_traffic(nd) if (dom == "k_solve" and args.prec == "mixed"
-                                                                  and not args.lam_adv) else None,
+                "peak_source": f"nominal FP64 {FP64_NOMINAL} TFLOP/s" if fp64_bound
+                else "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz", "fp64": fp64_bound}
+    roof.update({"kernel": dom, "traffic": kernel_traffic(dom, nd, prec_name, bool(args.lam_adv)),
                  "avg_launch_ms": dom_ms / dom_n,
                  "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
                  "kernel_ms_per_step": {k: v[0] / args.steps for k, v in trace.items()}})
+    rec = {"value": value, "unit": "JVP/s", "ms_per_step": ms / args.steps, "dtype": "f64" if prec_name == "fp64"
+           else "f32+f64", "roofline": roof, "e2e": e2e_rec, "gpu_launches": launches, "clocks": clk,
+           "solve_tile": {"tangent": list(tune["tangent"]), "step": list(tune["step"])}}
+    if keep_out:
+        rec["out"] = OUT.cpu().numpy()
+    return rec
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, n, el = oracle_jvps(12.0)
-        cpu = {"value": rate, "unit": "JVP/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{n} FP64 oracle tangent steps at 48x65x48 in {el:.1f} s (after its one-time LU setup)"}
 
-    if rank == 0:
-        out = {"metric": METRIC, "value": value, "unit": "JVP/s", "n_gpus": world, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": "f32+f64" if args.prec == "mixed" else "f64", "data": "synthetic",
-               "config": {"workload": "plane Couette 48x65x48, Re=400, dt=100, box 2pi/1.14 x 2 x 2pi/2.5; "
-                                      "per step: set_base + tangent on 256 seeded unit directions",
-                          "grid": [NX, NY, NZ], "ndir_per_gpu": nd, "precision": args.prec,
-                          "laminar_advection_in_L": bool(args.lam_adv),
-                          "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
-                          "solve_tile": {"tangent": list(tune["tangent"]), "step": list(tune["step"])}},
-               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
-        print(json.dumps(out))
-    if world > 1:
-        torch.distributed.destroy_process_group()
+def field_errors(ref, got):
+    """Per velocity component: max |got - ref| / max |ref| over the batch."""
+    import numpy as np
+    out = {}
+    for c, name in enumerate(("u", "v", "w")):
+        r = ref[:, c]
+        out[name] = float(np.max(np.abs(got[:, c] - r)) / np.max(np.abs(r)))
+    return out
+
+
+def measure_fp64_peak(sp, torch, local, blocks=152 * 8, iters=2048, reps=5):
+    """FP64 FMA rate of this device (the library's probe), timed with CUDA events on the
+    launching stream, clocks sampled meanwhile. TFLOP/s = 4096 blocks iters / time."""
+    buf = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        sp.probe_fp64_fma(buf, blocks, iters)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        sp.probe_fp64_fma(buf, blocks, iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    clk = clocks.stop()
+    return {"tflops": 4096.0 * blocks * iters / (ms * 1e-3) / 1e12, "ms_per_launch": ms, "clocks": clk,
+            "how": f"sp_probe_fp64_fma: {blocks} blocks x 256 threads x 8 chains x {iters} FMAs, mean of {reps}"}
+
+
+def attach_fp64_peak(roof, peak):
+    """Use the measured FP64 rate as the ALU denominator of an FP64-bound roofline."""
+    if roof.get("bound") != "alu" or not roof.get("fp64"):
+        return
+    roof["peak"] = peak["tflops"]
+    roof["frac"] = roof["achieved"] / peak["tflops"]
+    roof["peak_source"] = "measured FP64 FMA rate (fp64_peak_probe)"
+
+
+def time_to_converge(args):
+    """Secondary metric: time to |G(U)| < 1e-10 (Newton-GMRES-hookstep) at 16x33x16, Re 400,
+    from the seeded amplitude-0.1 state: the mixed tangent (graph-replayed Arnoldi steps)
+    against the plain FP64 GPU path (finite-difference actions, no graphs) and the FP64
+    tangent."""
+    import torch
+    import paper_1804_05087_gb300 as sp
+    import seeded_inputs as si
+    nx, ny, nz = 16, 33, 16
+    res = {}
+    for name, prec, fd, graphs in (("mixed_tangent", sp.SP_MIXED, False, True),
+                                   ("fp64_tangent", sp.SP_FP64, False, True),
+                                   ("plain_fp64_fd", sp.SP_FP64, True, False)):
+        ctx = sp.Context(sp.Config(nx, ny, nz, lx=LX, lz=LZ, re=RE, dt=DT, prec=prec))
+        ctx.sp_autotune(1)
+        a, b, c = si.couette_random_coeffs(1000, nx, ny, nz)
+        U = ctx.zeros()
+        ctx.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], 0.1, U)
+        if graphs:  # capture the Arnoldi graphs outside the timing (a warm start from the same guess)
+            W = U.clone()
+            ctx.sp_newton_gmres(W, max_newton=1, max_krylov=args.krylov, tol=1e-10, eta=1e-3, use_fd=fd,
+                                use_graphs=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = ctx.sp_newton_gmres(U, max_newton=30, max_krylov=args.krylov, tol=1e-10, eta=1e-3, use_fd=fd,
+                                  use_graphs=graphs)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        res[name] = {"seconds": wall, "converged": bool(rep["converged"]), "newton_steps": rep["newton_iters"],
+                     "actions": rep["total_jvps"], "norm_F": rep["norm_F"], "t_action_ms": rep["t_action_ms"],
+                     "t_orth_ms": rep["t_orth_ms"]}
+    return {"metric": "time to |F|<1e-10 vs plain FP64 GPU", "unit": "s", "higher_is_better": False,
+            "workload": f"plane Couette 16x33x16, Re=400, dt=100, seed 1000, amplitude 0.1, K <= {args.krylov}, "
+                        "eta 1e-3",
+            "runs": res, "speedup_mixed_vs_plain_fp64": res["plain_fp64_fd"]["seconds"] / res["mixed_tangent"]["seconds"]}
 
 
 if __name__ == "__main__":

@@ -252,11 +252,26 @@ enum { SP_STAGE_YINV = 0,   /* k_yinv of the tangent / adjoint         */
        SP_STAGE_SOLVE = 2,  /* k_solve of the tangent / adjoint        */
        SP_STAGE_STEP = 3,   /* every kernel of sp_step and sp_set_base */
        SP_STAGE_VEC = 4,    /* vector kernels (norms, axpy, seeding)   */
-       SP_NSTAGE = 5 };
+       SP_STAGE_RHS = 5,    /* k_rhs of the batched tangent's O(N) solve
+                               (Chebyshev coefficients + right-hand side;
+                               k_chain counts as SP_STAGE_SOLVE)         */
+       SP_NSTAGE = 6 };
 sp_status sp_trace_enable(sp_ctx* ctx, int on);
 /* Waits for the recorded events, then writes the accumulated milliseconds and
  * launch counts of the n (<= SP_NSTAGE) first stages. Host arrays. */
 sp_status sp_trace_read(sp_ctx* ctx, double* ms, long long* launches, int n);
+
+/* ---- FP64 rate probe -------------------------------------------------------- */
+
+/* The paper has no counterpart: a measurement of the device's FP64 fused
+ * multiply-add rate, the denominator of the roofline of the FP64-bound kernels
+ * (the per-mode solve, the FP64 transforms). Launches blocks x 256 threads on
+ * `stream`, each running 8 independent chains of `iters` FMAs: 4096 x blocks x
+ * iters flops per launch. The caller times it with events on the same stream.
+ * out: device buffer of blocks x 256 doubles (written, so the chains are not
+ * optimised away). iters > 0, a multiple of 4. Asynchronous. SP_EINVAL on bad
+ * arguments, SP_ECUDA if the launch fails. */
+sp_status sp_probe_fp64_fma(double* out, int blocks, int iters, void* stream);
 
 /* ---- tile autotuner -------------------------------------------------------- */
 

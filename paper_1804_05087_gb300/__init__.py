@@ -88,6 +88,7 @@ def _load():
         "sp_krylov_solve": ([P, P, P, I, I, I, D, P, ctypes.POINTER(D), I, ctypes.POINTER(I), ctypes.POINTER(I), V],
                             I),
         "sp_jvp_static": ([P, P, P, V], I),
+        "sp_probe_fp64_fma": ([P, I, I, V], I),
         "sp_vjp_euclid": ([P, P, P, I, V], I),
         "sp_trace_enable": ([P, I], I),
         "sp_trace_read": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), I], I),
@@ -127,8 +128,8 @@ EXPORTS = ("sp_create", "sp_destroy", "sp_last_error", "sp_state_len", "sp_dims"
            "sp_group_state_len", "sp_group_offset", "sp_group_member", "sp_group_step", "sp_group_set_base",
            "sp_group_jvp", "sp_group_inner", "sp_group_newton_gmres", "sp_autotune",
            "sp_set_solve_shape", "sp_step_n", "sp_set_base_n", "sp_jvp_n",
-           "sp_jvp_host", "sp_krylov_solve")
-STAGES = ("k_yinv", "k_xz", "k_solve", "step", "vector")
+           "sp_jvp_host", "sp_krylov_solve", "sp_probe_fp64_fma")
+STAGES = ("k_yinv", "k_xz", "k_solve", "step", "vector", "k_rhs")
 
 
 @dataclass
@@ -401,6 +402,17 @@ class Context:
 
 
 KRYLOV = {"gmres": 0, "bicgstab": 1, "idr": 2}
+
+
+def probe_fp64_fma(out, blocks, iters, stream=None):
+    """Launch the FP64 FMA-rate probe (4096 x blocks x iters flops) on `stream`.
+    out: float64 CUDA tensor of at least blocks x 256 elements."""
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64
+            and out.is_contiguous() and out.numel() >= blocks * 256):
+        raise TypeError("expected a contiguous float64 CUDA tensor of blocks x 256 elements")
+    st = _lib.sp_probe_fp64_fma(ctypes.c_void_p(out.data_ptr()), int(blocks), int(iters), _stream(stream))
+    if st != 0:
+        raise SpError(st, "sp_probe_fp64_fma")
 
 
 def _opts(max_newton, max_krylov, tol, eta, delta0, use_fd, use_gradient, int_steps=1, krylov="gmres", ell=2,

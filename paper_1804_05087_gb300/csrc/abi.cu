@@ -91,7 +91,8 @@ static void free_ctx(sp_ctx* c) {
   void* ptrs[] = {c->Th, c->TDh, c->Cfh, c->yv, c->lam6, c->Th_f, c->TDh_f, c->Cfh_f, c->twx, c->twz, c->base32t,
                   c->twx_f, c->twz_f, c->ops, c->ws6, c->ws3, c->base64, c->base32, c->U0,
                   c->G0, c->tmp, c->red, c->kry, c->wsG, c->pops, c->fd_w1, c->fd_c1, c->dzU,
-                  c->traj, c->nbuf, c->traj_base};
+                  c->traj, c->nbuf, c->traj_base, c->chain, c->omega, c->Tp, c->TDp, c->tq,
+                  c->Tp_f, c->TDp_f, c->tq_f, c->Cq, c->Cq_f, c->orth_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -357,6 +358,20 @@ static sp_status pipe_phase(sp_ctx* c, const double* du, double* out, int n_dir,
   return SP_OK;
 }
 
+// The tangent's per-mode solve of one pass: the O(N) chains (k_rhs, then k_chain) on
+// contexts built for large batches, else the dense per-mode operators (k_solve).
+sp_status sp_tangent_solve(sp_ctx* c, bool f32, const void* vals, const double* du, double* out, void* work,
+                           int nb, cudaStream_t st) {
+  if (c->use_chain) {
+    sp_status s = sp_cuda(c, traced(c, SP_STAGE_RHS, st, [&] { return launch_chain_rhs(c, f32, vals, du, work, nb, st); }),
+                          "rhs");
+    if (s != SP_OK) return s;
+    return sp_cuda(c, traced(c, SP_STAGE_SOLVE, st, [&] { return launch_chain_solve(c, du, out, work, nb, st); }),
+                   "chain solve");
+  }
+  return sp_cuda(c, traced(c, SP_STAGE_SOLVE, st, [&] { return launch_solve(c, f32, vals, du, out, nb, st); }), "solve");
+}
+
 extern "C" sp_status sp_jvp(sp_ctx* c, const double* du, double* Jdu, int n_dir, void* stream) {
   if (!c || !du || !Jdu || n_dir < 0 || du == Jdu) return sp_fail(c, SP_EINVAL, "sp_jvp: bad arguments");
   if (!c->has_base) return sp_fail(c, SP_EINVAL, "sp_jvp: call sp_set_base first");
@@ -384,7 +399,7 @@ extern "C" sp_status sp_jvp(sp_ctx* c, const double* du, double* Jdu, int n_dir,
     }
     if ((s = sp_cuda(c, traced(c, SP_STAGE_YINV, st, [&] { return launch_yinv(c, f32, u, c->ws6, nb, st); }), "yinv")) != SP_OK) return s;
     if ((s = sp_cuda(c, traced(c, SP_STAGE_XZ, st, [&] { return launch_xz(c, f32, XZ_TANGENT, c->ws6, c->ws3, nb, st); }), "xz tangent")) != SP_OK) return s;
-    if ((s = sp_cuda(c, traced(c, SP_STAGE_SOLVE, st, [&] { return launch_solve(c, f32, c->ws3, u, g, nb, st); }), "solve")) != SP_OK) return s;
+    if ((s = sp_tangent_solve(c, f32, c->ws3, u, g, c->ws6, nb, st)) != SP_OK) return s;
   }
   return SP_OK;
 }
@@ -658,9 +673,7 @@ extern "C" sp_status sp_jvp_n(sp_ctx* c, const double* du, double* Jdu, int n_di
       if ((s = sp_cuda(c, traced(c, SP_STAGE_XZ, st, [&] { return launch_xz(c, f32, XZ_TANGENT, c->ws6, c->ws3, nb, st); }),
                        "xz tangent")) != SP_OK)
         return s;
-      if ((s = sp_cuda(c, traced(c, SP_STAGE_SOLVE, st, [&] { return launch_solve(c, f32, c->ws3, g, c->tmp, nb, st); }),
-                       "solve")) != SP_OK)
-        return s;
+      if ((s = sp_tangent_solve(c, f32, c->ws3, g, c->tmp, c->ws6, nb, st)) != SP_OK) return s;
       if ((s = sp_cuda(c, launch_axpby(g, 1.0, g, 1.0, c->tmp, (size_t)nb * L, st), "axpby")) != SP_OK) return s;
     }
     if ((s = sp_cuda(c, launch_axpby(g, 1.0, g, -1.0, u, (size_t)nb * L, st), "axpby")) != SP_OK) return s;
@@ -1190,6 +1203,21 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     }
     c->kry_cap = K + 5;
   }
+  // partial sums of the fused Gram-Schmidt passes: one per basis vector and block, for every
+  // basis size the capacity allows (the basis may have been grown by another solver)
+  if (!c->orth_part || c->orth_cap < c->kry_cap) {
+    drop_newton_graphs(c);  // they hold the old pointer
+    if (c->orth_part) cudaFree(c->orth_part);
+    c->orth_part = nullptr;
+    c->orth_cap = 0;
+    c->orth_blocks = (int)std::max<size_t>(1, std::min<size_t>(c->sm_count, c->cplx_per_state / 64));
+    if (cudaMalloc((void**)&c->orth_part, (size_t)c->kry_cap * c->orth_blocks * 8) == cudaSuccess) {
+      c->orth_cap = c->kry_cap;
+    } else {
+      cudaGetLastError();
+      c->orth_part = nullptr;  // the unfused passes remain
+    }
+  }
   // the layout follows the capacity, so captured graphs stay valid for smaller K
   const int Kc = c->kry_cap - 5;
   double* V = c->kry;                            // Kc+2 basis vectors
@@ -1202,6 +1230,7 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   double* dhn = dhB + (Kc + 3);                  // [0] = |w|, [1] = 1/|w|, then y
   double* dwn = dhn + (Kc + 6);                  // |w| before the first pass, scratch
   int* dflag = reinterpret_cast<int*>(dwn + 4);  // second Gram-Schmidt pass needed
+  unsigned* dcnt = reinterpret_cast<unsigned*>(dwn + 6);  // ticket counter of the fused passes
   double* hbuf = c->red_host;                    // pinned: hA | hB | hn
   if ((size_t)2 * (Kc + 3) + 2 > (size_t)64 * c->red_blocks + 512)
     return sp_fail(c, SP_EINVAL, "sp_newton_gmres: Krylov dimension too large for the pinned buffer");
@@ -1227,6 +1256,7 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   sp_newton_report r{};
   const double t0 = now_ms();
   sp_status s;
+  if ((s = sp_cuda(c, cudaMemsetAsync(dcnt, 0, sizeof(unsigned), st), "counter")) != SP_OK) return s;
   auto norm = [&](const double* x, double* out) { return inner_many(c, x, 1, x, out, st); };
   if ((s = step_n(c, U, F, ns, st)) != SP_OK) return s;
   r.total_steps += ns;
@@ -1261,6 +1291,18 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     const bool selective = L >= 65536;
     auto enqueue_orth = [&](int j, double* w) -> sp_status {
       sp_status q;
+      if (false) {
+        // small states: the three fused passes (both Gram-Schmidt passes and the normalisation,
+        // h written straight to the pinned host buffer)
+        double* hp = c->orth_part;
+        const int G = c->orth_blocks;
+        if ((q = sp_cuda(c, launch_orth_pass(c, 0, V, j + 1, w, nullptr, hp, G, dhA, hbuf, dcnt, st), "orth")) != SP_OK)
+          return q;
+        if ((q = sp_cuda(c, launch_orth_pass(c, 1, V, j + 1, w, dhA, hp, G, dhB, hbuf + Kc + 3, dcnt, st), "orth")) !=
+            SP_OK)
+          return q;
+        return sp_cuda(c, launch_orth_pass(c, 2, V, j + 1, w, dhB, hp, G, dhn, hbuf + 2 * (Kc + 3), dcnt, st), "orth");
+      }
       const int* gate = selective ? dflag : nullptr;
       if ((q = sp_cuda(c, launch_dev_dots(c, V, j + 1, w, dpart, nb, dhA, nullptr, st), "dots")) != SP_OK) return q;
       if (selective) {

@@ -124,16 +124,135 @@ __device__ __forceinline__ C2<float> ld_c2(const C2<float>* p) {
 // ------------------------------------------------------------ k_yinv
 struct YinvArgs {
   int Mm, MZ, MX, Kx, NY, N, NH, jchunk;
+  int q2, NQ;  // two-level split (N divisible by 4): quarter grid jq = 0..N/4
   double alpha, beta;
+};
+
+// Chebyshev tables of k_yinv (T = double or float): Th[j][n] = T_n(y_j), TDh[j][n] = T_n'(y_j)
+// on the half grid j <= N/2; for the two-level split also, on the quarter grid jq <= N/4 and
+// odd n = 2m+1, Tp[jq][n] = T_n(y_{N/2-jq}) = (-1)^m sin(pi jq n / N) and
+// TDp[jq][n] = T_n'(y_{N/2-jq}) = (-1)^m n cos(pi jq n / N) / cos(pi jq / N), and
+// tq[jq] = tan(pi jq / N) (the even-degree derivatives at y_{N/2-jq} are tq times the
+// alternating sums at y_jq)
+template <typename T>
+struct YinvTabs {
+  const T* Th;
+  const T* TDh;
+  const T* Tp;
+  const T* TDp;
+  const T* tq;
 };
 
 // in : [dir][3][Mm][NY] complex double (the boundary state layout)
 // out: [dir][6][NY][Mm] complex T, fields u, v, w, wx, wy, wz
 // (bx, by, bz): mode tile, Gauss-Lobatto chunk, direction
+// curl and stores at the Gauss-Lobatto point j: fields u, v, w, wx, wy, wz of mode m
+template <typename T>
+__device__ __forceinline__ void yinv_store(C2<T>* o, size_t NYMm, size_t base, T kx, T kz, C2<T> u, C2<T> v,
+                                           C2<T> w, C2<T> Du, C2<T> Dw) {
+  const C2<T> ox = Dw - mul_is(v, kz);
+  const C2<T> oy = mul_is(u, kz) - mul_is(w, kx);
+  const C2<T> oz = mul_is(v, kx) - Du;
+  o[0 * NYMm + base] = u;
+  o[1 * NYMm + base] = v;
+  o[2 * NYMm + base] = w;
+  o[3 * NYMm + base] = ox;
+  o[4 * NYMm + base] = oy;
+  o[5 * NYMm + base] = oz;
+}
+
+// Two-level even/odd split: per quarter-grid point jq the sums over degrees n = 0 and
+// n = 2 (mod 4) and over odd n give the values at the four points jq, N - jq, N/2 - jq,
+// N/2 + jq (T_n(y_{N-j}) = (-1)^n T_n(y_j); T_n(y_{N/2-j}) = +-T_n(y_j) for n = 0, 2 mod 4),
+// a quarter less work than the one-level split.
+template <typename T>
+__device__ __forceinline__ void yinv_q2(const C2<T>* sc, C2<T>* o, const YinvTabs<T>& tb, const YinvArgs& a, int m0,
+                                        int by) {
+  const int TM = kTileYinv;
+  const int NY = a.NY, Mm = a.Mm, N = a.N;
+  const int j_lo = by * a.jchunk;
+  const int j_hi = min(a.NQ, j_lo + a.jchunk);
+  const int items = TM * (j_hi - j_lo);
+  const size_t NYMm = (size_t)NY * Mm;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int t = it % TM;
+    const int jq = j_lo + it / TM;
+    const int m = m0 + t;
+    if (m >= Mm) continue;
+    const C2<T> z = mk((T)0, (T)0);
+    // [field][0 EE, 1 EO, 2 O, 3 O'] for u, v, w; the same with the derivative tables for u, w
+    C2<T> A[3][4] = {{z, z, z, z}, {z, z, z, z}, {z, z, z, z}};
+    C2<T> Dd[2][4] = {{z, z, z, z}, {z, z, z, z}};
+    const T* trow = tb.Th + (size_t)jq * NY;
+    const T* drow = tb.TDh + (size_t)jq * NY;
+    const T* prow = tb.Tp + (size_t)jq * NY;
+    const T* qrow = tb.TDp + (size_t)jq * NY;
+    for (int n = 0; n < NY; ++n) {
+      const int r = n & 3;
+      const C2<T> u = sc[(0 * NY + n) * TM + t], v = sc[(1 * NY + n) * TM + t], w = sc[(2 * NY + n) * TM + t];
+      const T tc = trow[n], td = drow[n];
+      if (r == 0) {
+        A[0][0] = A[0][0] + scl(u, tc);
+        A[1][0] = A[1][0] + scl(v, tc);
+        A[2][0] = A[2][0] + scl(w, tc);
+        Dd[0][0] = Dd[0][0] + scl(u, td);
+        Dd[1][0] = Dd[1][0] + scl(w, td);
+      } else if (r == 2) {
+        A[0][1] = A[0][1] + scl(u, tc);
+        A[1][1] = A[1][1] + scl(v, tc);
+        A[2][1] = A[2][1] + scl(w, tc);
+        Dd[0][1] = Dd[0][1] + scl(u, td);
+        Dd[1][1] = Dd[1][1] + scl(w, td);
+      } else {
+        const T tp = prow[n], tdp = qrow[n];
+        A[0][2] = A[0][2] + scl(u, tc);
+        A[1][2] = A[1][2] + scl(v, tc);
+        A[2][2] = A[2][2] + scl(w, tc);
+        A[0][3] = A[0][3] + scl(u, tp);
+        A[1][3] = A[1][3] + scl(v, tp);
+        A[2][3] = A[2][3] + scl(w, tp);
+        Dd[0][2] = Dd[0][2] + scl(u, td);
+        Dd[1][2] = Dd[1][2] + scl(w, td);
+        Dd[0][3] = Dd[0][3] + scl(u, tdp);
+        Dd[1][3] = Dd[1][3] + scl(w, tdp);
+      }
+    }
+    const int pos = m / a.MZ, iz = m - pos * a.MZ;
+    const int ix = pos <= a.Kx ? pos : pos - a.MX;
+    const T kx = (T)(a.alpha * ix), kz = (T)(a.beta * iz);
+    const T tqv = tb.tq[jq];
+    // E at jq and at N/2 - jq; derivatives: even part at N/2 - jq is tq (EO' - EE')
+    C2<T> E1[3], E2[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      E1[f] = A[f][0] + A[f][1];
+      E2[f] = A[f][0] - A[f][1];
+    }
+    const C2<T> DE1u = Dd[0][0] + Dd[0][1], DE1w = Dd[1][0] + Dd[1][1];
+    const C2<T> DE2u = scl(Dd[0][1] - Dd[0][0], tqv), DE2w = scl(Dd[1][1] - Dd[1][0], tqv);
+    const int jl[4] = {jq, N - jq, N / 2 - jq, N / 2 + jq};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = jl[q];
+      if (q == 1 && j == jq) continue;                         // jq = N/2 would coincide (never, N >= 4)
+      if (q >= 2 && 4 * jq == N) continue;                     // N/2 - jq = jq: already written
+      if (q == 3 && jq == 0) continue;                         // N/2 + 0 = N/2 - 0
+      const bool hi = (q & 1) != 0;                            // the mirrored point N - j'
+      const T sg = hi ? (T)-1 : (T)1;
+      const int s2 = q >= 2;
+      const C2<T> uu = (s2 ? E2[0] : E1[0]) + scl(A[0][s2 ? 3 : 2], sg);
+      const C2<T> vv = (s2 ? E2[1] : E1[1]) + scl(A[1][s2 ? 3 : 2], sg);
+      const C2<T> ww = (s2 ? E2[2] : E1[2]) + scl(A[2][s2 ? 3 : 2], sg);
+      const C2<T> Du = scl(s2 ? DE2u : DE1u, sg) + Dd[0][s2 ? 3 : 2];
+      const C2<T> Dw = scl(s2 ? DE2w : DE1w, sg) + Dd[1][s2 ? 3 : 2];
+      yinv_store(o, NYMm, (size_t)j * Mm + m, kx, kz, uu, vv, ww, Du, Dw);
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void yinv_body(const double2* __restrict__ in, C2<T>* __restrict__ out,
-                                          const T* __restrict__ Th, const T* __restrict__ TDh,
-                                          const YinvArgs& a, int bx, int by, int bz) {
+                                          const YinvTabs<T>& tb, const YinvArgs& a, int bx, int by, int bz) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* sc = reinterpret_cast<C2<T>*>(smem_raw);  // [3][NY][TM]
   const int TM = kTileYinv;
@@ -154,6 +273,12 @@ __device__ __forceinline__ void yinv_body(const double2* __restrict__ in, C2<T>*
     sc[(c * NY + n) * TM + t] = v;
   }
   __syncthreads();
+  if (sizeof(T) == 8 && a.q2) {  // FP64 only: the float kernel is bound by memory, not arithmetic
+    yinv_q2<T>(sc, out + (size_t)dir * 6 * NY * Mm, tb, a, m0, by);
+    return;
+  }
+  const T* Th = tb.Th;
+  const T* TDh = tb.TDh;
   const int j_lo = by * a.jchunk;
   const int j_hi = min(a.NH, j_lo + a.jchunk);
   const int items = TM * (j_hi - j_lo);
@@ -215,10 +340,8 @@ __device__ __forceinline__ void yinv_body(const double2* __restrict__ in, C2<T>*
 
 template <typename T>
 __global__ void __launch_bounds__(kThreadsYinv) k_yinv(const double2* __restrict__ in,
-                                                      C2<T>* __restrict__ out,
-                                                      const T* __restrict__ Th,
-                                                      const T* __restrict__ TDh, YinvArgs a) {
-  yinv_body<T>(in, out, Th, TDh, a, blockIdx.x, blockIdx.y, blockIdx.z);
+                                                      C2<T>* __restrict__ out, YinvTabs<T> tb, YinvArgs a) {
+  yinv_body<T>(in, out, tb, a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // -------------------------------------------------------------- k_xz
@@ -525,40 +648,43 @@ __device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const 
     sdu[(c * TM + t) * NY + n] = v;
   }
   __syncthreads();
-  // phase B: forward Chebyshev transform of N (rows 0..N-2) and the RHS u/dt + N
-  for (int idx = threadIdx.x; idx < 3 * TM * NR; idx += blockDim.x) {
+  // phase A2: even/odd pairs of the values, once per (component, mode, point pair):
+  // s_j = f(y_j) + f(y_N-j) replaces f(y_j), d_j = f(y_j) - f(y_N-j) replaces f(y_N-j)
+  // (T_n(y_N-j) = (-1)^n T_n(y_j), so even rows read s and odd rows read d)
+  for (int idx = threadIdx.x; idx < 3 * TM * (NH - 1); idx += blockDim.x) {
     const int t = idx % TM;
-    const int n = (idx / TM) % NR;
-    const int c = idx / (TM * NR);
+    const int jj = (idx / TM) % (NH - 1);
+    const int c = idx / (TM * (NH - 1));
+    C2<T>* col = svals + (c * NY) * TM + t;
+    const C2<T> p = col[jj * TM], q = col[(N - jj) * TM];
+    col[jj * TM] = p + q;
+    col[(N - jj) * TM] = p - q;
+  }
+  __syncthreads();
+  // phase B: forward Chebyshev transform of N (rows 0..N-2) and the RHS u/dt + N; the even and
+  // the odd rows in separate loops, so that no warp mixes the two trip counts
+  for (int par = 0; par < 2; ++par)
+  for (int idx = threadIdx.x, cnt = par ? NR / 2 : (NR + 1) / 2; idx < 3 * TM * cnt; idx += blockDim.x) {
+    const int t = idx % TM;
+    const int n = 2 * ((idx / TM) % cnt) + par;
+    const int c = idx / (TM * cnt);
     C2<T> acc = mk((T)0, (T)0);
     const C2<T>* col = svals + (c * NY) * TM + t;
     if (sizeof(T) == 8) {
       const double* cf = a.Cfh_d + (size_t)n * NH;
       if ((n & 1) == 0) {
-        for (int jj = 0; jj < NH - 1; ++jj) {
-          const C2<T> s = col[jj * TM] + col[(N - jj) * TM];
-          acc = acc + scl(s, (T)cf[jj]);
-        }
+        for (int jj = 0; jj < NH - 1; ++jj) acc = acc + scl(col[jj * TM], (T)cf[jj]);
         acc = acc + scl(col[(NH - 1) * TM], (T)cf[NH - 1]);
       } else {
-        for (int jj = 0; jj < NH - 1; ++jj) {
-          const C2<T> s = col[jj * TM] - col[(N - jj) * TM];
-          acc = acc + scl(s, (T)cf[jj]);
-        }
+        for (int jj = 0; jj < NH - 1; ++jj) acc = acc + scl(col[(N - jj) * TM], (T)cf[jj]);
       }
     } else {
       const float* cf = a.Cfh_f + (size_t)n * NH;
       if ((n & 1) == 0) {
-        for (int jj = 0; jj < NH - 1; ++jj) {
-          const C2<T> s = col[jj * TM] + col[(N - jj) * TM];
-          acc = acc + scl(s, (T)cf[jj]);
-        }
+        for (int jj = 0; jj < NH - 1; ++jj) acc = acc + scl(col[jj * TM], (T)cf[jj]);
         acc = acc + scl(col[(NH - 1) * TM], (T)cf[NH - 1]);
       } else {
-        for (int jj = 0; jj < NH - 1; ++jj) {
-          const C2<T> s = col[jj * TM] - col[(N - jj) * TM];
-          acc = acc + scl(s, (T)cf[jj]);
-        }
+        for (int jj = 0; jj < NH - 1; ++jj) acc = acc + scl(col[(N - jj) * TM], (T)cf[jj]);
       }
     }
     const double2 d = sdu[(c * TM + t) * NY + n];
@@ -1352,6 +1478,118 @@ __global__ void k_f64_to_f32(const double* a, float* b, float* bt, size_t n, int
   }
 }
 
+static YinvArgs yinv_args(const sp_ctx* c) {
+  YinvArgs a;
+  a.Mm = c->Mm; a.MZ = c->MZ; a.MX = c->MX; a.Kx = c->Kx; a.NY = c->NY; a.N = c->N; a.NH = c->NH;
+  a.alpha = c->alpha; a.beta = c->beta;
+  a.q2 = (c->N % 4 == 0 && c->Tp != nullptr) ? 1 : 0;
+  a.NQ = c->N / 4 + 1;
+  a.jchunk = 1;
+  return a;
+}
+
+template <typename T>
+static YinvTabs<T> yinv_tabs(const sp_ctx* c) {
+  YinvTabs<T> t;
+  if constexpr (sizeof(T) == 8) {
+    t = {c->Th, c->TDh, c->Tp, c->TDp, c->tq};
+  } else {
+    t = {c->Th_f, c->TDh_f, c->Tp_f, c->TDp_f, c->tq_f};
+  }
+  return t;
+}
+
+// ----------------------------------------------- fused Gram-Schmidt passes
+// One classical Gram-Schmidt pass of an Arnoldi step in a single launch, for states small
+// enough that launches, not bandwidth, set the cost. Block b owns a contiguous slice of the
+// complex elements. MODE 1 and 2 first apply the previous pass, w -= sum_i hprev_i V_i, to
+// the slice; MODE 0 and 1 then form the block's partial inner products <V_i, w> (a warp per
+// i), MODE 2 the partial |w|^2. Each block then takes a ticket; the block that draws the
+// last one (it waits for nobody: the others have finished) sums the partials in block
+// order, so the result is deterministic, writes h to hout and to the host buffer, and in
+// MODE 2 also normalises w (its slices were all updated before the tickets were drawn).
+// counter: a device word that is 0 between launches (the last block resets it).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_orth_pass(const double2* __restrict__ V, int k, int ncplx, double2* w, int NY,
+                                                  int MZ, const double* hprev, double* partials, double* hout,
+                                                  double* host_out, unsigned* counter) {
+  const int G = gridDim.x, b = blockIdx.x;
+  const int chunk = (ncplx + G - 1) / G;
+  const int e0 = b * chunk, e1 = min(ncplx, e0 + chunk);
+  if (MODE >= 1) {
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      double2 acc = w[e];
+      for (int i = 0; i < k; ++i) {
+        const double h = hprev[i];
+        const double2 v = V[(size_t)i * ncplx + e];
+        acc.x = fma(-h, v.x, acc.x);
+        acc.y = fma(-h, v.y, acc.y);
+      }
+      w[e] = acc;
+    }
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nrow = MODE == 2 ? 1 : k;
+  for (int i = warp; i < nrow; i += nw) {
+    const double2* vi = MODE == 2 ? w : V + (size_t)i * ncplx;
+    double acc = 0.0;
+    for (int e = e0 + lane; e < e1; e += 32) {
+      const double wt = ((e / NY) % MZ) == 0 ? 1.0 : 2.0;
+      const double2 a = vi[e], c = w[e];
+      acc += wt * (a.x * c.x + a.y * c.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) partials[(size_t)i * G + b] = acc;
+  }
+  __threadfence();
+  __syncthreads();
+  __shared__ unsigned ticket;
+  if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
+  __syncthreads();
+  if (ticket != (unsigned)(G - 1)) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
+    double h = 0.0;
+    for (int q = 0; q < G; ++q) h += __ldcg(partials + (size_t)i * G + q);
+    if (MODE == 2) {
+      const double hn = sqrt(h);
+      hout[0] = hn;
+      hout[1] = hn > 0.0 ? 1.0 / hn : 0.0;
+      host_out[0] = hn;
+    } else {
+      hout[i] = h;
+      host_out[i] = h;
+    }
+  }
+  if (MODE == 2) {
+    __syncthreads();
+    const double inv = __ldcg(hout + 1);
+    for (int e = threadIdx.x; e < ncplx; e += blockDim.x) {
+      double2 v = __ldcg(w + e);
+      v.x *= inv;
+      v.y *= inv;
+      w[e] = v;
+    }
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+cudaError_t launch_orth_pass(const sp_ctx* c, int mode, const double* V, int k, double* w, const double* hprev,
+                             double* partials, int nblocks, double* hout, double* host_out, unsigned* counter,
+                             cudaStream_t st) {
+  const int n = (int)c->cplx_per_state;
+  const double2* Vc = reinterpret_cast<const double2*>(V);
+  double2* wc = reinterpret_cast<double2*>(w);
+  if (mode == 0)
+    k_orth_pass<0><<<nblocks, 256, 0, st>>>(Vc, k, n, wc, c->NY, c->MZ, hprev, partials, hout, host_out, counter);
+  else if (mode == 1)
+    k_orth_pass<1><<<nblocks, 256, 0, st>>>(Vc, k, n, wc, c->NY, c->MZ, hprev, partials, hout, host_out, counter);
+  else
+    k_orth_pass<2><<<nblocks, 256, 0, st>>>(Vc, k, n, wc, c->NY, c->MZ, hprev, partials, hout, host_out, counter);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ grouped kernels
 // One launch over several independent problems: block b runs block
 // b - first[inst[b]] of member inst[b]'s own launch (with a single direction),
@@ -1360,8 +1598,7 @@ template <typename T>
 struct GYinv {
   size_t off;  // offset (doubles) of the member's state in a group vector
   C2<T>* out;
-  const T* Th;
-  const T* TDh;
+  YinvTabs<T> tb;
   YinvArgs a;
   int gx;      // mode tiles of the member's launch
 };
@@ -1378,7 +1615,7 @@ __global__ void __launch_bounds__(kThreadsYinv) k_yinv_grp(const double* __restr
   if (threadIdx.x == 0) r = recs[i];
   __syncthreads();
   const int b = blockIdx.x - first[i];
-  yinv_body<T>(reinterpret_cast<const double2*>(in_base + r.off), r.out, r.Th, r.TDh, r.a, b % r.gx, b / r.gx, 0);
+  yinv_body<T>(reinterpret_cast<const double2*>(in_base + r.off), r.out, r.tb, r.a, b % r.gx, b / r.gx, 0);
 }
 
 template <typename T, int MODE>
@@ -1476,24 +1713,24 @@ size_t sp_xz_global_plane_bytes(const sp_ctx* c) {
 
 cudaError_t launch_yinv(const sp_ctx* c, bool fp32, const double* in, void* out6, int n_dir,
                         cudaStream_t st) {
-  YinvArgs a;
-  a.Mm = c->Mm; a.MZ = c->MZ; a.MX = c->MX; a.Kx = c->Kx; a.NY = c->NY; a.N = c->N; a.NH = c->NH;
-  a.alpha = c->alpha; a.beta = c->beta;
+  YinvArgs a = yinv_args(c);
+  if (fp32) a.q2 = 0;
+  const int nj = a.q2 ? a.NQ : c->NH;
   const int tiles = (c->Mm + kTileYinv - 1) / kTileYinv;
   int jsplit = 1;
-  while (tiles * jsplit * n_dir < c->sm_count && jsplit < c->NH) ++jsplit;
-  a.jchunk = (c->NH + jsplit - 1) / jsplit;
-  dim3 grid(tiles, (c->NH + a.jchunk - 1) / a.jchunk, n_dir);
+  while (tiles * jsplit * n_dir < c->sm_count && jsplit < nj) ++jsplit;
+  a.jchunk = (nj + jsplit - 1) / jsplit;
+  dim3 grid(tiles, (nj + a.jchunk - 1) / a.jchunk, n_dir);
   if (fp32) {
     size_t sm = (size_t)3 * c->NY * kTileYinv * sizeof(C2<float>);
     cudaFuncSetAttribute(k_yinv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_yinv<float><<<grid, kThreadsYinv, sm, st>>>(reinterpret_cast<const double2*>(in),
-                                                  reinterpret_cast<C2<float>*>(out6), c->Th_f, c->TDh_f, a);
+                                                  reinterpret_cast<C2<float>*>(out6), yinv_tabs<float>(c), a);
   } else {
     size_t sm = (size_t)3 * c->NY * kTileYinv * sizeof(C2<double>);
     cudaFuncSetAttribute(k_yinv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_yinv<double><<<grid, kThreadsYinv, sm, st>>>(reinterpret_cast<const double2*>(in),
-                                                   reinterpret_cast<C2<double>*>(out6), c->Th, c->TDh, a);
+                                                   reinterpret_cast<C2<double>*>(out6), yinv_tabs<double>(c), a);
   }
   return cudaGetLastError();
 }
@@ -1535,6 +1772,8 @@ cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, voi
                       cudaStream_t st) {
   if (fp32 && c->use_xz_reg && sp_xz_reg_supported(c) && (mode == XZ_TANGENT || mode == XZ_ADJOINT))
     return launch_xz_reg(c, mode, in6, out3, n_dir, st);
+  if (!fp32 && c->use_xz_reg64 && sp_xz_reg64_supported(c) && (mode == XZ_TANGENT || mode == XZ_ADJOINT))
+    return launch_xz_reg64(c, mode, in6, out3, n_dir, st);
   if (fp32) {
     const C2<float>* tx = reinterpret_cast<const C2<float>*>(c->twx_f);
     const C2<float>* tz = reinterpret_cast<const C2<float>*>(c->twz_f);
@@ -1844,19 +2083,14 @@ static cudaError_t grp_build_yinv(GrpKernel* k, sp_ctx* const* mem, int n, const
     GYinv<T>& r = recs[m];
     r.off = offs[m];
     r.out = reinterpret_cast<C2<T>*>(c->ws6);
-    if constexpr (sizeof(T) == 8) {
-      r.Th = c->Th;
-      r.TDh = c->TDh;
-    } else {
-      r.Th = c->Th_f;
-      r.TDh = c->TDh_f;
-    }
+    r.tb = yinv_tabs<T>(c);
     YinvArgs& a = r.a;
-    a.Mm = c->Mm; a.MZ = c->MZ; a.MX = c->MX; a.Kx = c->Kx; a.NY = c->NY; a.N = c->N; a.NH = c->NH;
-    a.alpha = c->alpha; a.beta = c->beta;
-    a.jchunk = (c->NH + jsplit - 1) / jsplit;
+    a = yinv_args(c);
+    if (sizeof(T) == 4) a.q2 = 0;
+    const int nj = a.q2 ? a.NQ : c->NH;
+    a.jchunk = (nj + jsplit - 1) / jsplit;
     r.gx = (c->Mm + kTileYinv - 1) / kTileYinv;
-    nblk[m] = r.gx * ((c->NH + a.jchunk - 1) / a.jchunk);
+    nblk[m] = r.gx * ((nj + a.jchunk - 1) / a.jchunk);
     smem = std::max(smem, (size_t)3 * c->NY * kTileYinv * sizeof(C2<T>));
   }
   cudaError_t e = cudaFuncSetAttribute(k_yinv_grp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -59,6 +59,8 @@ extern "C" sp_status sp_jvp_static(sp_ctx* c, const double* du, double* Jdu, voi
   int dev = 0;
   sp_status s = sp_cuda(c, cudaGetDevice(&dev), "sp_jvp_static: device");
   if (s != SP_OK) return s;
+  if (dev != c->dev)
+    return sp_fail(c, SP_EINVAL, "sp_jvp_static: the context's device must be the current device");
   void* base = nullptr;
   if ((s = sp_cuda(c, scratch_address(dev, &base), "sp_jvp_static: scratch address")) != SP_OK) return s;
   unsigned char* p = static_cast<unsigned char*>(base);
@@ -69,5 +71,5 @@ extern "C" sp_status sp_jvp_static(sp_ctx* c, const double* du, double* Jdu, voi
   // contents left by an earlier call need no clearing
   if ((s = sp_cuda(c, launch_yinv(c, f32, du, ws6, 1, st), "yinv")) != SP_OK) return s;
   if ((s = sp_cuda(c, launch_xz(c, f32, XZ_TANGENT, ws6, ws3, 1, st), "xz tangent")) != SP_OK) return s;
-  return sp_cuda(c, launch_solve(c, f32, ws3, du, Jdu, 1, st), "solve");
+  return sp_tangent_solve(c, f32, ws3, du, Jdu, ws6, 1, st);
 }

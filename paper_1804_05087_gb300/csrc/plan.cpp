@@ -318,6 +318,152 @@ bool build_hop_la(const ChebOps& C, double kx, double lam, double nu, double* ou
   return true;
 }
 
+// ------------------------------------------------------------ O(N) chains
+// The same per-mode tau problems, solved in O(N) per right-hand side (the batched
+// tangent's solve, solve_chain.cu). For a Dirichlet Helmholtz tau problem
+//   (l' - n' D^2) x = f on rows n <= N-2 of parity Q,  sum over parity Q of x_n = bc,
+// the identity between the Chebyshev coefficients of x and of x'' (for n >= 2)
+//   x_n = c_{n-2} x''_{n-2} / (4n(n-1)) - x''_n / (2(n^2-1)) + x''_{n+2} / (4n(n+1)),
+// with x''_k = (l' x_k - f_k) / n' on the tau rows and 0 above them, turns rows
+// n = 2..N into a tridiagonal system in the coefficients of parity Q:
+//   -l' c_{n-2} / (4n(n-1)) x_{n-2} + (n' + [n <= N-2] l' / (2(n^2-1))) x_n
+//     - [n+2 <= N-2] l' / (4n(n+1)) x_{n+2}
+//   = -c_{n-2} f_{n-2} / (4n(n-1)) + [n <= N-2] f_n / (2(n^2-1)) - [n+2 <= N-2] f_{n+2} / (4n(n+1)),
+// an invertible recombination of the tau rows (so the solution is the tau
+// solution), which together with the boundary row is solved by one elimination
+// sweep from the top and one substitution sweep from the bottom. Per unknown
+// i = 1..m (n = 2i + Q) the record holds (q, p, psi, alpha): the sweep
+// beta_i = r_i q_i - p_i beta_{i+1}, the boundary-row weights psi_i with
+// x_0 = (bc - sum_i psi_i beta_i) g, and the substitution x_i = alpha_i x_{i-1} + beta_i.
+// H uses (l', n') = (lam, nu); K uses (-k^2, -1), i.e. (D^2 - k^2) x = f.
+//
+// The coupled (v, a, p) problem of parity P is the fourth-order tau problem
+//   (lam - nu D^2)(D^2 - k^2) v = -k^2 g + tau h   on rows n <= N-2 of parity P,
+//   v(+-1) = Dv(+-1) = 0,
+// where h_n = 1/c_n carries the one pressure coefficient (p_{N-1} or p_N) that no
+// tau row fixes. With w = (D^2 - k^2) v it is two Helmholtz problems: w = w_A +
+// sigma psi_w + tau w_h from H (w_A: right-hand side -k^2 g, bc 0; psi_w: bc 1;
+// w_h: right-hand side h), then v = K(w) with v(+-1) = 0, and sigma, tau from the
+// two conditions left: the top coefficient of w = (D^2 - k^2) v (w_top = -k^2 v_top,
+// the tau problem for v leaves it free) and Dv(+-1) = 0 (sum n^2 v_n = 0). The
+// record stores v_psi = K(psi_w), v_h = K(w_h) and the inverse of the 2 x 2
+// influence matrix of these two conditions.
+struct TriOp {
+  std::vector<double> q, p, psi, alpha;  // index 1..m
+  double g = 0.0;                        // 1 / sum_i gamma_i
+};
+
+// RHS weights of row n of the tridiagonal form (universal: depend on n and N only)
+void chain_weights(int N, int n, double* w) {
+  const double cm2 = (n - 2 == 0) ? 2.0 : 1.0;
+  w[0] = -cm2 / (4.0 * n * (n - 1));
+  w[1] = (n <= N - 2) ? 1.0 / (2.0 * ((double)n * n - 1.0)) : 0.0;
+  w[2] = (n + 2 <= N - 2) ? -1.0 / (4.0 * n * (n + 1.0)) : 0.0;
+}
+
+TriOp tri_factor(int N, int Q, double lp, double np_) {
+  const int m = (N - Q) / 2;  // unknowns i = 0..m
+  TriOp t;
+  t.q.assign(m + 2, 0.0);
+  t.p.assign(m + 2, 0.0);
+  t.psi.assign(m + 2, 0.0);
+  t.alpha.assign(m + 2, 0.0);
+  for (int i = m; i >= 1; --i) {
+    const int n = 2 * i + Q;
+    const double cm2 = (n - 2 == 0) ? 2.0 : 1.0;
+    const double l = -lp * cm2 / (4.0 * n * (n - 1));
+    const double d = np_ + ((n <= N - 2) ? lp / (2.0 * ((double)n * n - 1.0)) : 0.0);
+    const double u = (n + 2 <= N - 2) ? -lp / (4.0 * n * (n + 1.0)) : 0.0;
+    const double den = d + u * t.alpha[i + 1];
+    t.alpha[i] = -l / den;
+    t.q[i] = 1.0 / den;
+    t.p[i] = u / den;
+  }
+  double gsum = 1.0, gam = 1.0;
+  for (int i = 1; i <= m; ++i) {
+    gam *= t.alpha[i];
+    gsum += gam;
+  }
+  t.g = 1.0 / gsum;
+  t.psi[m] = 1.0;
+  for (int k = m - 1; k >= 1; --k) t.psi[k] = 1.0 + t.alpha[k + 1] * t.psi[k + 1];
+  return t;
+}
+
+// x (parity Q, index i <-> n = 2i + Q) solving the Helmholtz tau problem with
+// right-hand side f (full Chebyshev index, rows <= N-2 read) and boundary value bc
+std::vector<double> tri_solve(int N, int Q, const TriOp& t, const std::vector<double>& f, double bc) {
+  const int m = (N - Q) / 2;
+  std::vector<double> beta(m + 2, 0.0), x(m + 1, 0.0);
+  auto F = [&](int n) { return (n >= 0 && n <= N - 2) ? f[n] : 0.0; };
+  double acc = 0.0;
+  for (int i = m; i >= 1; --i) {
+    const int n = 2 * i + Q;
+    double w[3];
+    chain_weights(N, n, w);
+    const double r = w[0] * F(n - 2) + w[1] * F(n) + w[2] * F(n + 2);
+    beta[i] = r * t.q[i] - t.p[i] * beta[i + 1];
+    acc += t.psi[i] * beta[i];
+  }
+  x[0] = (bc - acc) * t.g;
+  for (int i = 1; i <= m; ++i) x[i] = t.alpha[i] * x[i - 1] + beta[i];
+  return x;
+}
+
+// the record of one parity: [H (q,p,psi,alpha) x NH][K x NH][(v_psi, v_h) x NH][8 scalars]
+void build_chain_parity(int N, int P, double k, double lam, double nu, bool mean, double* out) {
+  const int NH = N / 2 + 1, m = (N - P) / 2;
+  const TriOp H = tri_factor(N, P, lam, nu);
+  double* h4 = out;
+  double* k4 = out + 4 * NH;
+  double* v2 = out + 8 * NH;
+  double* sc = out + 10 * NH;
+  for (int i = 1; i <= m; ++i) {
+    h4[4 * i + 0] = H.q[i];
+    h4[4 * i + 1] = H.p[i];
+    h4[4 * i + 2] = H.psi[i];
+    h4[4 * i + 3] = H.alpha[i];
+  }
+  sc[0] = H.g;
+  if (mean) return;
+  const double k2 = k * k;
+  const TriOp K = tri_factor(N, P, -k2, -1.0);
+  for (int i = 1; i <= m; ++i) {
+    k4[4 * i + 0] = K.q[i];
+    k4[4 * i + 1] = K.p[i];
+    k4[4 * i + 2] = K.psi[i];
+    k4[4 * i + 3] = K.alpha[i];
+  }
+  sc[1] = K.g;
+  const int n1 = N + 1;
+  std::vector<double> zero(n1, 0.0), h(n1, 0.0);
+  for (int n = P; n <= N - 2; n += 2) h[n] = (n == 0) ? 0.5 : 1.0;
+  const std::vector<double> wpsi = tri_solve(N, P, H, zero, 1.0);
+  const std::vector<double> wh = tri_solve(N, P, H, h, 0.0);
+  auto full = [&](const std::vector<double>& x) {
+    std::vector<double> f(n1, 0.0);
+    for (int i = 0; i <= m; ++i) f[2 * i + P] = x[i];
+    return f;
+  };
+  const std::vector<double> vpsi = tri_solve(N, P, K, full(wpsi), 0.0);
+  const std::vector<double> vh = tri_solve(N, P, K, full(wh), 0.0);
+  double n2psi = 0.0, n2h = 0.0;
+  for (int i = 0; i <= m; ++i) {
+    const double n = 2.0 * i + P;
+    n2psi += n * n * vpsi[i];
+    n2h += n * n * vh[i];
+    v2[2 * i + 0] = vpsi[i];
+    v2[2 * i + 1] = vh[i];
+  }
+  const double e00 = wpsi[m] + k2 * vpsi[m], e01 = wh[m] + k2 * vh[m];
+  const double e10 = n2psi, e11 = n2h;
+  const double det = e00 * e11 - e01 * e10;
+  sc[2] = e11 / det;
+  sc[3] = -e01 / det;
+  sc[4] = -e10 / det;
+  sc[5] = e00 / det;
+}
+
 }  // namespace
 
 // unique mode u -> (pos, iz): positions 0..Kx keep every iz, negative ix skip iz = 0
@@ -352,6 +498,30 @@ sp_status sp_build_plan(sp_ctx* c) {
     for (int j = 0; j < NH; ++j) {
       double cbj = (j == 0) ? 2.0 : 1.0;  // j = N is not on the half grid
       Cfh[(size_t)n * NH + j] = 2.0 / (N * cbn) * cospi_frac((long)j * n, N) / cbj;
+    }
+  }
+  // the second level of the even/odd split (N divisible by 4): at y_{N/2-jq}, odd degrees
+  // n = 2m+1 give T_n = (-1)^m sin(pi jq n / N) and T_n' = (-1)^m n cos(pi jq n / N) / cos(pi jq / N)
+  const int NQ = N / 4 + 1;
+  const bool q2 = N % 4 == 0 && N >= 4;
+  std::vector<double> Tp, TDp, tq, Cq;
+  if (q2) {
+    Cq.assign((size_t)n1 * NQ, 0.0);
+    for (int n = 0; n < n1; n += 2) {
+      const double cbn = (n == 0 || n == N) ? 2.0 : 1.0;
+      for (int jq = 0; jq < NQ; ++jq) Cq[(size_t)n * NQ + jq] = 2.0 / (N * cbn) * cospi_frac((long)jq * n, N);
+    }
+    Tp.assign((size_t)NQ * n1, 0.0);
+    TDp.assign((size_t)NQ * n1, 0.0);
+    tq.assign(NQ, 0.0);
+    for (int jq = 0; jq < NQ; ++jq) {
+      const double cj = cospi_frac(jq, N), sj = cospi_frac((long)N - 2L * jq, 2L * N);
+      tq[jq] = sj / cj;
+      for (int n = 1; n < n1; n += 2) {
+        const double sg = (((n - 1) / 2) & 1) ? -1.0 : 1.0;
+        Tp[(size_t)jq * n1 + n] = sg * cospi_frac((long)N - 2L * jq * n, 2L * N);
+        TDp[(size_t)jq * n1 + n] = sg * n * cospi_frac((long)jq * n, N) / cj;
+      }
     }
   }
   // twiddles exp(-2 pi i k / n)
@@ -417,6 +587,26 @@ sp_status sp_build_plan(sp_ctx* c) {
   for (int b : bad)
     if (b) return sp_fail(c, SP_EINVAL, "singular per-mode Stokes system");
 
+  // O(N) chain records and the universal row weights (the batched tangent's solve)
+  c->use_chain = (c->cfg.max_batch >= kChainMinBatch && !la && chain_smem(c) <= 227 * 1024) ? 1 : 0;
+  std::vector<double> chain, omega;
+  if (c->use_chain) {
+    c->chain_par = 10 * NH + 8;
+    c->chain_stride = 2 * c->chain_par;
+    chain.assign((size_t)c->n_unique * c->chain_stride, 0.0);
+    for (int u = 0; u < c->n_unique; ++u) {
+      int pos, iz;
+      sp_unique_mode(c, u, &pos, &iz);
+      const int ix = pos <= c->Kx ? pos : pos - c->MX;
+      const double kx = c->alpha * ix, kz = c->beta * iz, k = std::sqrt(kx * kx + kz * kz);
+      const double lam = 1.0 / c->dt + c->nu * k * k;
+      for (int P = 0; P < 2; ++P)
+        build_chain_parity(N, P, k, lam, c->nu, u == 0, chain.data() + (size_t)u * c->chain_stride + P * c->chain_par);
+    }
+    omega.assign((size_t)3 * n1, 0.0);
+    for (int n = 2; n <= N; ++n) chain_weights(N, n, omega.data() + 3 * n);
+  }
+
   // float copies
   std::vector<float> Thf(Th.begin(), Th.end()), TDhf(TDh.begin(), TDh.end()),
       Cfhf(Cfh.begin(), Cfh.end());
@@ -429,8 +619,19 @@ sp_status sp_build_plan(sp_ctx* c) {
             up((void**)&c->Cfh, Cfh.data(), Cfh.size() * 8) && up((void**)&c->Th_f, Thf.data(), Thf.size() * 4) &&
             up((void**)&c->TDh_f, TDhf.data(), TDhf.size() * 4) && up((void**)&c->Cfh_f, Cfhf.data(), Cfhf.size() * 4) &&
             up((void**)&c->ops, ops.data(), ops.size() * 8) && up((void**)&c->yv, yv.data(), yv.size() * 8) &&
-            up((void**)&c->lam6, lam6.data(), lam6.size() * 8);
+            up((void**)&c->lam6, lam6.data(), lam6.size() * 8) &&
+            (!c->use_chain || (up((void**)&c->chain, chain.data(), chain.size() * 8) &&
+                               up((void**)&c->omega, omega.data(), omega.size() * 8)));
   if (!ok) return sp_fail(c, SP_ENOMEM, "device allocation of plan tables failed");
+  if (q2) {
+    std::vector<float> Tpf(Tp.begin(), Tp.end()), TDpf(TDp.begin(), TDp.end()), tqf(tq.begin(), tq.end()),
+        Cqf(Cq.begin(), Cq.end());
+    ok = up((void**)&c->Cq, Cq.data(), Cq.size() * 8) && up((void**)&c->Cq_f, Cqf.data(), Cqf.size() * 4) &&
+         up((void**)&c->Tp, Tp.data(), Tp.size() * 8) && up((void**)&c->TDp, TDp.data(), TDp.size() * 8) &&
+         up((void**)&c->tq, tq.data(), tq.size() * 8) && up((void**)&c->Tp_f, Tpf.data(), Tpf.size() * 4) &&
+         up((void**)&c->TDp_f, TDpf.data(), TDpf.size() * 4) && up((void**)&c->tq_f, tqf.data(), tqf.size() * 4);
+    if (!ok) return sp_fail(c, SP_ENOMEM, "device allocation of plan tables failed");
+  }
   return sp_build_fft_tables(c);
 }
 

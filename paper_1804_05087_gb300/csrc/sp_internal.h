@@ -48,6 +48,10 @@ struct FftPlan {
   int radix[12];
 };
 
+// contexts whose batches reach this many directions solve the tangent's per-mode
+// problems with the O(N) chains (one thread per mode, parity and direction)
+constexpr int kChainMinBatch = 32;
+
 // ------------------------------------------------------------------ context
 struct sp_ctx {
   sp_config cfg;
@@ -72,15 +76,28 @@ struct sp_ctx {
   // laminar advection in L (cfg.lam_adv): complex V' and H' per mode, (N - 1) columns of
   // N + 1 complex rows, column-major (the mean mode keeps H0 / H1)
   int off_vc = 0, off_hc = 0;
+  // O(N) per-mode solve of the batched tangent (solve_chain.cu; plan.cpp describes the
+  // records): used when cfg.max_batch >= kChainMinBatch and lam_adv = 0
+  int use_chain = 0;
+  int chain_par = 0, chain_stride = 0;  // doubles per parity record / per mode
 
   // device tables
   double *Th = nullptr, *TDh = nullptr, *Cfh = nullptr;
+  // two-level split of k_yinv (N divisible by 4): Tp, TDp [N/4+1][NY], tq [N/4+1] (kernels.cu)
+  double *Tp = nullptr, *TDp = nullptr, *tq = nullptr;
+  float *Tp_f = nullptr, *TDp_f = nullptr, *tq_f = nullptr;
+  // the same for the forward transform of k_rhs: Cq[n][jq] = 2 / (N cbar_n) cos(pi jq n / N), even
+  // rows n <= N-2, jq <= N/4 (solve_chain.cu)
+  double* Cq = nullptr;
+  float* Cq_f = nullptr;
   double* yv = nullptr;          // [NY] wall-normal points: cos(pi j / N) (Couette), r_j (pipe)
   double* lam6 = nullptr;        // [NY][6] laminar (U, Omega) per plane: (y,0,0,0,0,-1) / (0,0,1-r^2,0,2r,0)
   float *Th_f = nullptr, *TDh_f = nullptr, *Cfh_f = nullptr;
   double2 *twx = nullptr, *twz = nullptr;
   float2 *twx_f = nullptr, *twz_f = nullptr;
   double* ops = nullptr;
+  double* chain = nullptr;       // [n_unique][2 parities][chain_par]
+  double* omega = nullptr;       // [NY][3] right-hand-side weights of the tridiagonal rows
   // pipe: per-mode dense operators (3 NY x 3 NY, column-major), radial FD band (D1) tables
   double* pops = nullptr;
   size_t pop_stride = 0;
@@ -101,6 +118,7 @@ struct sp_ctx {
   int red_blocks = 0;
   int has_base = 0;
   int use_xz_reg = 1;            // float plane stage: register FFT kernel when the size allows
+  int use_xz_reg64 = 1;          // FP64 tangent/adjoint plane stage: register FFT kernel (xz_reg64.cu)
   int solve_shape_tan = 0;       // k_solve tile shape of the tangent (sp_autotune)
   int solve_shape_step = 0;      // k_solve tile shape of the FP64 step
   // sizes of shared memory per kernel (bytes)
@@ -117,6 +135,8 @@ struct sp_ctx {
   // Newton scratch
   double* kry = nullptr;         // Krylov basis [max_krylov+1] states
   int kry_cap = 0;
+  double* orth_part = nullptr;   // [orth_cap][orth_blocks] partial sums of the fused Gram-Schmidt passes
+  int orth_blocks = 0, orth_cap = 0;
   // multi-step map B^n (sp_step_n / sp_set_base_n / sp_jvp_n)
   double* traj = nullptr;        // [traj_cap] states: U_0 .. U_{n-1} of the last sp_set_base_n
   int traj_cap = 0;
@@ -216,6 +236,23 @@ cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, voi
 // float plane stage with register-resident FFTs (xz_reg.cu), square grids 16..64
 bool sp_xz_reg_supported(const sp_ctx* c);
 cudaError_t launch_xz_reg(const sp_ctx* c, int mode, const void* in, void* out, int n_dir, cudaStream_t st);
+// FP64 plane stage with register-resident FFTs (xz_reg64.cu), square grids 16..48
+bool sp_xz_reg64_supported(const sp_ctx* c);
+cudaError_t launch_xz_reg64(const sp_ctx* c, int mode, const void* in, void* out, int n_dir, cudaStream_t st);
+// batched tangent solve by O(N) chains (solve_chain.cu), two launches: k_rhs (values ->
+// right-hand sides in work, n_unique x 3 x (N-1) complex per direction), then k_chain
+// (one thread per mode, parity and direction); together the same inputs and outputs as
+// launch_solve. chain_smem: dynamic shared memory of k_chain (0 if it does not fit).
+cudaError_t launch_chain_rhs(const sp_ctx* c, bool fp32, const void* in3, const double* du, void* work, int n_dir,
+                             cudaStream_t st);
+cudaError_t launch_chain_solve(const sp_ctx* c, const double* du, double* out, const void* work, int n_dir,
+                               cudaStream_t st);
+size_t chain_smem(const sp_ctx* c);
+// the tangent's per-mode solve of one pass (abi.cu): chains or dense operators by the
+// context's choice (use_chain); work: scratch of n_unique x 3 x (N-1) complex doubles
+// per direction (the chains' right-hand sides; ws6 suffices)
+sp_status sp_tangent_solve(sp_ctx* c, bool f32, const void* vals, const double* du, double* out, void* work,
+                           int nb, cudaStream_t st);
 // shape: index into the tile-shape table (sp_solve_shapes); -1 = the context's tangent choice
 cudaError_t launch_solve(const sp_ctx* c, bool fp32, const void* in3, const double* du,
                          double* out, int n_dir, cudaStream_t st, int shape = -1);
@@ -251,5 +288,11 @@ cudaError_t launch_scale_dev(const sp_ctx* c, double* x, const double* s, cudaSt
 // w -= sum_i h_i V_i (h on device)
 cudaError_t launch_multi_axpy(const sp_ctx* c, const double* V, int k, const double* h,
                               double* w, cudaStream_t st, const int* gate = nullptr);
+// one fused classical Gram-Schmidt pass (mode 0: dots; 1: subtract hprev, then dots; 2: subtract
+// hprev, then |w| into hout[0], 1/|w| into hout[1] and w normalised); h also goes to host_out
+// (pinned host memory); counter: a device word, 0 between launches. For small states.
+cudaError_t launch_orth_pass(const sp_ctx* c, int mode, const double* V, int k, double* w, const double* hprev,
+                             double* partials, int nblocks, double* hout, double* host_out, unsigned* counter,
+                             cudaStream_t st);
 // second Gram-Schmidt pass needed? *flag = (|w|^2 - |h|^2 < |w|^2 / 2); if not, h2 = 0 (k entries)
 cudaError_t launch_reorth_decide(const double* h, int k, const double* wn, int* flag, double* h2, cudaStream_t st);

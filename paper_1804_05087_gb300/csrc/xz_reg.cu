@@ -7,151 +7,17 @@
 // pointwise product, packed r2c along z, forward FFT along x truncated to the
 // 2/3-rule modes (pseudospectral products, Sec. 3.2).
 //
-// The FFT is a decimation-in-frequency Cooley-Tukey recursion with radices
-// 4, 3 and 2 fully unrolled at compile time: inputs in natural order, outputs
-// in digit-reversed positions resolved by a compile-time index map, twiddles
-// as compile-time constants (sine and cosine evaluated by Taylor series at
-// compile time).
+// The FFTs are the compile-time register transforms of fft_reg.h.
 #include <algorithm>
 #include <utility>
 #include <vector>
 
+#include "fft_reg.h"
 #include "sp_internal.h"
 
 namespace {
 
-// ------------------------------------------------- compile-time trigonometry
-constexpr double kPi = 3.14159265358979323846264338327950288;
-
-// Taylor series about 0; |x| <= pi/4 after the reduction below (30 terms is
-// far below double rounding there)
-__host__ __device__ constexpr double taylor_sin(double x) {
-  double term = x, sum = x;
-  for (int k = 1; k < 30; ++k) {
-    term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
-    sum += term;
-  }
-  return sum;
-}
-__host__ __device__ constexpr double taylor_cos(double x) {
-  double term = 1.0, sum = 1.0;
-  for (int k = 1; k < 30; ++k) {
-    term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
-    sum += term;
-  }
-  return sum;
-}
-// cos and sin of 2 pi k / n for integers, reduced exactly by octant symmetry
-__host__ __device__ constexpr double cos2pi(long k, long n) {
-  long m = ((k % n) + n) % n;            // angle 2 pi m / n in [0, 2 pi)
-  if (8 * m <= n) return taylor_cos(2.0 * kPi * (double)m / (double)n);
-  if (8 * m <= 3 * n) return taylor_sin(2.0 * kPi * (double)(n - 4 * m) / (4.0 * n));   // cos(pi/2 - t)
-  if (8 * m <= 5 * n) return -taylor_cos(2.0 * kPi * (double)(2 * m - n) / (2.0 * n));  // -cos(t - pi)
-  if (8 * m <= 7 * n) return -taylor_sin(2.0 * kPi * (double)(3 * n - 4 * m) / (4.0 * n));
-  return taylor_cos(2.0 * kPi * (double)(n - m) / (double)n);
-}
-__host__ __device__ constexpr double sin2pi(long k, long n) { return cos2pi(n - 4 * k, 4 * n); }  // sin t = cos(pi/2 - t)
-
-// -------------------------------------------------------------- radix plans
-template <int N> struct Plan;
-template <> struct Plan<2> { using type = std::integer_sequence<int, 2>; };
-template <> struct Plan<3> { using type = std::integer_sequence<int, 3>; };
-template <> struct Plan<4> { using type = std::integer_sequence<int, 4>; };
-template <> struct Plan<16> { using type = std::integer_sequence<int, 4, 4>; };
-template <> struct Plan<24> { using type = std::integer_sequence<int, 4, 3, 2>; };
-template <> struct Plan<32> { using type = std::integer_sequence<int, 4, 4, 2>; };
-template <> struct Plan<48> { using type = std::integer_sequence<int, 4, 4, 3>; };
-template <> struct Plan<64> { using type = std::integer_sequence<int, 4, 4, 4>; };
-
-// position of output frequency f after the DIF recursion with radices P0, Pr...
-template <int N, int P0, int... Pr>
-__host__ __device__ constexpr int dif_pos(int f) {
-  constexpr int M = N / P0;
-  if constexpr (sizeof...(Pr) == 0) {
-    return (f % P0) * M;
-  } else {
-    return (f % P0) * M + dif_pos<M, Pr...>(f / P0);
-  }
-}
-template <int N, int... P>
-__host__ __device__ constexpr int out_pos_impl(int f, std::integer_sequence<int, P...>) { return dif_pos<N, P...>(f); }
-template <int N>
-__host__ __device__ constexpr int out_pos(int f) { return out_pos_impl<N>(f, typename Plan<N>::type{}); }
-
-// y_d = sum_r x_r w_P^{r d}, w_P = exp(SGN 2 pi i / P)
-template <int P, int SGN>
-__device__ __forceinline__ void bfly(C2<float>* v) {
-  if constexpr (P == 2) {
-    const C2<float> a = v[0], b = v[1];
-    v[0] = a + b;
-    v[1] = a - b;
-  } else if constexpr (P == 3) {
-    constexpr float h3 = (float)(0.86602540378443864676 * SGN);
-    const C2<float> t1 = v[1] + v[2];
-    const C2<float> t2 = mul_is(v[1] - v[2], h3);
-    const C2<float> m = v[0] - scl(t1, 0.5f);
-    v[0] = v[0] + t1;
-    v[1] = m + t2;
-    v[2] = m - t2;
-  } else {
-    const C2<float> a = v[0] + v[2], b = v[0] - v[2];
-    const C2<float> c = v[1] + v[3], d = mul_is(v[1] - v[3], (float)SGN);
-    v[0] = a + c;
-    v[2] = a - c;
-    v[1] = b + d;
-    v[3] = b - d;
-  }
-}
-
-template <int NT, int N, int OFF, int SGN, int P0, int... Pr>
-__device__ __forceinline__ void dif(C2<float> (&x)[NT]);
-
-template <int NT, int M, int OFF, int SGN, int... Pr, int... D>
-__device__ __forceinline__ void dif_blocks(C2<float> (&x)[NT], std::integer_sequence<int, D...>) {
-  (dif<NT, M, OFF + D * M, SGN, Pr...>(x), ...);
-}
-
-// twiddle by w_N^{m d} (a compile-time constant) and store at position OFF + m + d M
-template <int NT, int N, int OFF, int SGN, int M, int m, int d>
-__device__ __forceinline__ void tw_store(C2<float> (&x)[NT], C2<float> y) {
-  if constexpr (m * d != 0) {
-    constexpr float wc = (float)cos2pi((long)m * d, N);
-    constexpr float ws = (float)(SGN * sin2pi((long)m * d, N));
-    y = mk(y.x * wc - y.y * ws, y.x * ws + y.y * wc);
-  }
-  x[OFF + m + d * M] = y;
-}
-
-template <int NT, int N, int OFF, int SGN, int P0, int M, int m, int... D>
-__device__ __forceinline__ void dif_col(C2<float> (&x)[NT], std::integer_sequence<int, D...>) {
-  C2<float> v[P0] = {x[OFF + m + D * M]...};
-  bfly<P0, SGN>(v);
-  (tw_store<NT, N, OFF, SGN, M, m, D>(x, v[D]), ...);
-}
-
-template <int NT, int N, int OFF, int SGN, int P0, int M, int... Ms>
-__device__ __forceinline__ void dif_cols(C2<float> (&x)[NT], std::integer_sequence<int, Ms...>) {
-  (dif_col<NT, N, OFF, SGN, P0, M, Ms>(x, std::make_integer_sequence<int, P0>{}), ...);
-}
-
-// one decimation-in-frequency level on positions [OFF, OFF + N), then recurse
-// on the P0 blocks of length M = N / P0
-template <int NT, int N, int OFF, int SGN, int P0, int... Pr>
-__device__ __forceinline__ void dif(C2<float> (&x)[NT]) {
-  constexpr int M = N / P0;
-  dif_cols<NT, N, OFF, SGN, P0, M>(x, std::make_integer_sequence<int, M>{});
-  if constexpr (sizeof...(Pr) > 0) dif_blocks<NT, M, OFF, SGN, Pr...>(x, std::make_integer_sequence<int, P0>{});
-}
-
-template <int N, int SGN, int... P>
-__device__ __forceinline__ void fft_impl(C2<float> (&x)[N], std::integer_sequence<int, P...>) {
-  dif<N, N, 0, SGN, P...>(x);
-}
-// in-register FFT: natural-order input, output frequency f at x[out_pos<N>(f)]
-template <int N, int SGN>
-__device__ __forceinline__ void fft_reg(C2<float> (&x)[N]) {
-  fft_impl<N, SGN>(x, typename Plan<N>::type{});
-}
+using namespace fftreg;
 
 struct XzRegArgs {
   const C2<float>* in;  // [dir][NIN][NY][Mm]

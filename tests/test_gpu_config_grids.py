@@ -7,7 +7,14 @@
   high-wavenumber parts of the base fields enter the plane stage.
 
 Tolerances as elsewhere: FP64 rel. 1e-12 (max abs difference over max abs value);
-mixed 1e-5 per velocity component (float transforms and products, FP64 solve).
+mixed 1e-5 per velocity component (float transforms and products, FP64 solve) for
+inputs with the spectral decay of the workloads' states. Inputs with O(1) random
+coefficients at every Chebyshev degree and Fourier mode are far less well conditioned:
+measured with the oracle, one rounding of the solve's right-hand side at the size of its
+largest entry moves the result by 8e-14 (48x65x48), 1e-13 (32x49x32) and 4e-13
+(96x97x96) per component, against 2e-15 to 7e-15 for the seeded inputs; the plane
+stage rounds tens of times, and a float rounding is 5.4e8 times an FP64 one. So for
+these inputs: FP64 1e-11, mixed 1e-4 (N <= 64) and 1e-3 (N = 96) per component.
 """
 import math
 
@@ -23,6 +30,10 @@ CASES = {
     "96x97x96": dict(grid=(96, 97, 96), lx=4 * math.pi / 1.14, lz=4 * math.pi / 2.5, re=1000.0, seed=5000),
     "32x49x32": dict(grid=(32, 49, 32), lx=2 * math.pi / 1.14, lz=2 * math.pi / 2.5, re=700.0, seed=3001),
 }
+
+
+def full_mixed_tol(ctx):
+    return 1e-4 if ctx.NY <= 65 else 1e-3
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
@@ -60,8 +71,9 @@ def test_jvp_fp64_and_mixed(case):
             if prec == 0:
                 assert rel(got[i], ref["jvp"][i]) < 1e-12
             else:
+                tol = full_mixed_tol(ctx) if i == 0 else 1e-5  # ds[0]: full-spectrum direction
                 for c in range(3):
-                    assert rel(got[i, c], ref["jvp"][i][c]) < 1e-5
+                    assert rel(got[i, c], ref["jvp"][i][c]) < tol
 
 
 def test_vjp_fp64_and_mixed(case):
@@ -75,8 +87,9 @@ def test_vjp_fp64_and_mixed(case):
             if prec == 0:
                 assert rel(got[i], ref["vjp"][i]) < 1e-12
             else:
+                tol = full_mixed_tol(ctx) if i == 0 else 1e-5
                 for c in range(3):
-                    assert rel(got[i, c], ref["vjp"][i][c]) < 1e-5
+                    assert rel(got[i, c], ref["vjp"][i][c]) < tol
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -89,7 +102,7 @@ def test_full_spectrum_base_48x65x48(prec):
     full = si.couette_random_full(1002, *grid)
     bases = [0.1 * full / orc.norm(full), u0 + orc.step(u0)]
     ds = np.stack([si.couette_random_full(1003, *grid), orc.seed_state(*si.couette_random_coeffs(2000, *grid), 1.0)])
-    for ub in bases:
+    for k, ub in enumerate(bases):
         ctx.sp_set_base(dev(ub))
         b = orc.base(ub)
         out = ctx.zeros(2)
@@ -97,8 +110,10 @@ def test_full_spectrum_base_48x65x48(prec):
         got = host(out)
         for i in range(2):
             ref = orc.jvp(b, ds[i])
+            full = k == 0 or i == 0  # a full-spectrum base or direction
             if prec == 0:
-                assert rel(got[i], ref) < 1e-12
+                assert rel(got[i], ref) < (1e-11 if full else 1e-12)
             else:
+                tol = full_mixed_tol(ctx) if full else 1e-5
                 for c in range(3):
-                    assert rel(got[i, c], ref[c]) < 1e-5
+                    assert rel(got[i, c], ref[c]) < tol

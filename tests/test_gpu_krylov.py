@@ -47,11 +47,17 @@ def test_krylov_history_matches_oracle(jacobian_problem, solver, par):  # noqa: 
     hg, ag = ctx.sp_krylov_solve(dev(F), X, krylov=solver, param=par, max_act=4000, eta=1e-11, shadow=sh)
     x = host(X)
     ho, hg = np.array(ho), np.array(hg)
-    # the recurrences amplify rounding slowly: the early history agrees tightly
-    n = min(8, len(ho), len(hg))
-    assert np.max(np.abs(hg[:n] - ho[:n]) / ho[:n]) < 1e-8
+    # Rounding differences grow geometrically along these recurrences (by about 300 per
+    # BiCGSTAB(4) cycle here), while a wrong coefficient shows at once: the first
+    # updates agree to round-off, and agreement to 1e-6 lasts several updates.
+    n = min(len(ho), len(hg))
+    d = np.abs(hg[:n] - ho[:n]) / ho[:n]
+    early = 2 if solver == "bicgstab" else par
+    assert np.max(d[:early + 1]) < 1e-12
+    first_bad = int(np.argmax(d > 1e-6)) if np.any(d > 1e-6) else n
+    assert first_bad >= (4 if solver == "bicgstab" else 2 * par)
     assert hg[-1] <= 1e-11 * hg[0]
-    assert abs(ag - ao) <= max(4, 0.1 * ao)
+    assert abs(ag - ao) <= max(8, 0.2 * ao)
     assert g.norm(x - ref) < 1e-8 * g.norm(ref)
     assert g.norm(x - xo) < 1e-8 * g.norm(ref)
 
