@@ -342,6 +342,8 @@ typedef struct {
   double t_action_ms; /* time in Jacobian actions (first term of Eq. CPU)    */
   double t_orth_ms;   /* time in orthogonalisation (second term of Eq. CPU)  */
   double t_total_ms;
+  int spec_jvps;      /* actions computed ahead of a GMRES stopping test that
+                         then stopped, and discarded (not in total_jvps)      */
 } sp_newton_report;
 
 /* Newton-GMRES with hookstep (Sec. 2, Sec. 3.2): U_inout holds the initial

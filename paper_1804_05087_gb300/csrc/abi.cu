@@ -92,7 +92,7 @@ static void free_ctx(sp_ctx* c) {
                   c->twx_f, c->twz_f, c->ops, c->ws6, c->ws3, c->base64, c->base32, c->U0,
                   c->G0, c->tmp, c->red, c->kry, c->wsG, c->pops, c->fd_w1, c->fd_c1, c->dzU,
                   c->traj, c->nbuf, c->traj_base, c->chain, c->omega, c->Tp, c->TDp, c->tq,
-                  c->Tp_f, c->TDp_f, c->tq_f, c->Cq, c->Cq_f, c->orth_part};
+                  c->Tp_f, c->TDp_f, c->tq_f, c->Cq, c->Cq_f, c->yinv_tc_mat};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -152,6 +152,7 @@ extern "C" sp_status sp_create(const sp_config* cfg, sp_ctx** out) {
   if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(SP_ECUDA, "no device");
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
   if (c->sm_count <= 0) c->sm_count = 1;
+  cudaDeviceGetAttribute(&c->coop, cudaDevAttrCooperativeLaunch, c->dev);
   if (sp_build_plan(c) != SP_OK) return bail(SP_EINVAL, c->err);
   if (!sp_xz_fits(c)) return bail(SP_EINVAL, "grid too large for the plane kernel");
   c->field_cplx = c->cplx_per_state;
@@ -230,6 +231,7 @@ extern "C" sp_status sp_pipe_create(const sp_pipe_config* cfg, sp_ctx** out) {
   if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(SP_ECUDA, "no device");
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
   if (c->sm_count <= 0) c->sm_count = 1;
+  cudaDeviceGetAttribute(&c->coop, cudaDevAttrCooperativeLaunch, c->dev);
   if (sp_build_pipe_plan(c) != SP_OK) return bail(SP_EINVAL, c->err);
   if (!sp_xz_fits(c)) return bail(SP_EINVAL, "grid too large for the plane kernel");
   if (!alloc_workspaces(c)) return bail(SP_ENOMEM, "workspace allocation");
@@ -1190,8 +1192,11 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   const size_t L = c->state_len;
   // one partial sum per ~1024 complex values, at most red_blocks
   const int nb = (int)std::max<size_t>(1, std::min<size_t>(c->red_blocks, (c->cplx_per_state + 1023) / 1024));
+  // small states: each Arnoldi column in one cooperative launch over gf blocks (orth.cu)
+  const int gf = orth_fused_blocks(c);
+  const int nbp = std::max(nb, gf);
   // device scratch after the basis: partials, hA, hB, hn/inv
-  const size_t extra = (size_t)(K + 2) * nb + 3 * (size_t)(K + 3) + 24;
+  const size_t extra = (size_t)(K + 2) * nbp + 3 * (size_t)(K + 3) + 24;
   if (c->kry_cap < K + 5) {
     drop_newton_graphs(c);  // they hold pointers into the old basis
     if (c->kry) cudaFree(c->kry);
@@ -1203,21 +1208,6 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     }
     c->kry_cap = K + 5;
   }
-  // partial sums of the fused Gram-Schmidt passes: one per basis vector and block, for every
-  // basis size the capacity allows (the basis may have been grown by another solver)
-  if (!c->orth_part || c->orth_cap < c->kry_cap) {
-    drop_newton_graphs(c);  // they hold the old pointer
-    if (c->orth_part) cudaFree(c->orth_part);
-    c->orth_part = nullptr;
-    c->orth_cap = 0;
-    c->orth_blocks = (int)std::max<size_t>(1, std::min<size_t>(c->sm_count, c->cplx_per_state / 64));
-    if (cudaMalloc((void**)&c->orth_part, (size_t)c->kry_cap * c->orth_blocks * 8) == cudaSuccess) {
-      c->orth_cap = c->kry_cap;
-    } else {
-      cudaGetLastError();
-      c->orth_part = nullptr;  // the unfused passes remain
-    }
-  }
   // the layout follows the capacity, so captured graphs stay valid for smaller K
   const int Kc = c->kry_cap - 5;
   double* V = c->kry;                            // Kc+2 basis vectors
@@ -1225,14 +1215,17 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   double* Ut = c->kry + (size_t)(Kc + 3) * L;    // trial state
   double* Zg = c->kry + (size_t)(Kc + 4) * L;    // gradient direction (use_gradient)
   double* dpart = c->kry + (size_t)(Kc + 5) * L; // partial sums
-  double* dhA = dpart + (size_t)(Kc + 2) * nb;   // first Gram-Schmidt pass
+  double* dhA = dpart + (size_t)(Kc + 2) * nbp;  // first Gram-Schmidt pass
   double* dhB = dhA + (Kc + 3);                  // second pass
   double* dhn = dhB + (Kc + 3);                  // [0] = |w|, [1] = 1/|w|, then y
   double* dwn = dhn + (Kc + 6);                  // |w| before the first pass, scratch
   int* dflag = reinterpret_cast<int*>(dwn + 4);  // second Gram-Schmidt pass needed
-  unsigned* dcnt = reinterpret_cast<unsigned*>(dwn + 6);  // ticket counter of the fused passes
-  double* hbuf = c->red_host;                    // pinned: hA | hB | hn
-  if ((size_t)2 * (Kc + 3) + 2 > (size_t)64 * c->red_blocks + 512)
+  unsigned* dbar = reinterpret_cast<unsigned*>(dwn + 6);  // grid barrier of the fused column
+  // pinned: two copies of hA | hB | hn, column j in copy j mod 2, so that the host reads column j
+  // while column j + 1 is computed
+  const size_t hstride = (size_t)2 * (Kc + 3) + 2;
+  double* hbuf = c->red_host;
+  if (2 * hstride > (size_t)64 * c->red_blocks + 512)
     return sp_fail(c, SP_EINVAL, "sp_newton_gmres: Krylov dimension too large for the pinned buffer");
   // CUDA graphs of the Arnoldi steps: tangent actions only, on the context's own stream
   bool graphs = o->use_graphs && !o->use_fd && ns == 1 && !c->trace;
@@ -1256,7 +1249,7 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   sp_newton_report r{};
   const double t0 = now_ms();
   sp_status s;
-  if ((s = sp_cuda(c, cudaMemsetAsync(dcnt, 0, sizeof(unsigned), st), "counter")) != SP_OK) return s;
+  if (gf > 0 && (s = sp_cuda(c, cudaMemsetAsync(dbar, 0, 16, st), "barrier reset")) != SP_OK) return s;
   auto norm = [&](const double* x, double* out) { return inner_many(c, x, 1, x, out, st); };
   if ((s = step_n(c, U, F, ns, st)) != SP_OK) return s;
   r.total_steps += ns;
@@ -1291,18 +1284,10 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     const bool selective = L >= 65536;
     auto enqueue_orth = [&](int j, double* w) -> sp_status {
       sp_status q;
-      if (false) {
-        // small states: the three fused passes (both Gram-Schmidt passes and the normalisation,
-        // h written straight to the pinned host buffer)
-        double* hp = c->orth_part;
-        const int G = c->orth_blocks;
-        if ((q = sp_cuda(c, launch_orth_pass(c, 0, V, j + 1, w, nullptr, hp, G, dhA, hbuf, dcnt, st), "orth")) != SP_OK)
-          return q;
-        if ((q = sp_cuda(c, launch_orth_pass(c, 1, V, j + 1, w, dhA, hp, G, dhB, hbuf + Kc + 3, dcnt, st), "orth")) !=
-            SP_OK)
-          return q;
-        return sp_cuda(c, launch_orth_pass(c, 2, V, j + 1, w, dhB, hp, G, dhn, hbuf + 2 * (Kc + 3), dcnt, st), "orth");
-      }
+      double* hb = hbuf + (size_t)(j & 1) * hstride;
+      if (gf > 0)
+        return sp_cuda(c, launch_orth_fused(c, V, j + 1, w, dpart, gf, dhA, dhB, dhn, hb, Kc + 3, dbar, st),
+                       "fused column");
       const int* gate = selective ? dflag : nullptr;
       if ((q = sp_cuda(c, launch_dev_dots(c, V, j + 1, w, dpart, nb, dhA, nullptr, st), "dots")) != SP_OK) return q;
       if (selective) {
@@ -1315,19 +1300,20 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
       if ((q = sp_cuda(c, launch_multi_axpy(c, V, j + 1, dhB, w, st, gate), "axpy")) != SP_OK) return q;
       if ((q = sp_cuda(c, launch_dev_norm(c, w, dpart, nb, dhn, dhn + 1, st), "norm")) != SP_OK) return q;
       if ((q = sp_cuda(c, launch_scale_dev(c, w, dhn + 1, st), "scale")) != SP_OK) return q;
-      if ((q = sp_cuda(c, cudaMemcpyAsync(hbuf, dhA, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, st), "h")) != SP_OK)
+      if ((q = sp_cuda(c, cudaMemcpyAsync(hb, dhA, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, st), "h")) != SP_OK)
         return q;
-      if ((q = sp_cuda(c, cudaMemcpyAsync(hbuf + Kc + 3, dhB, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, st), "h")) !=
+      if ((q = sp_cuda(c, cudaMemcpyAsync(hb + Kc + 3, dhB, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, st), "h")) !=
           SP_OK)
         return q;
-      return sp_cuda(c, cudaMemcpyAsync(hbuf + 2 * (Kc + 3), dhn, 8, cudaMemcpyDeviceToHost, st), "h");
+      return sp_cuda(c, cudaMemcpyAsync(hb + 2 * (Kc + 3), dhn, 8, cudaMemcpyDeviceToHost, st), "h");
     };
     // host part (after the stream is synchronised): column j of H, its Givens-rotated copy R, g
     auto finish_orth = [&](int j) -> double {
-      const double hn = hbuf[2 * (Kc + 3)];
+      const double* hb = hbuf + (size_t)(j & 1) * hstride;
+      const double hn = hb[2 * (Kc + 3)];
       double* Hc = H.data() + (size_t)j * LD;
       double* Rc = R.data() + (size_t)j * LD;
-      for (int i = 0; i <= j; ++i) Hc[i] = hbuf[i] + hbuf[Kc + 3 + i];
+      for (int i = 0; i <= j; ++i) Hc[i] = hb[i] + hb[Kc + 3 + i];
       Hc[j + 1] = hn;
       givens_column(Hc, Rc, j, cs.data(), sn.data(), g.data());
       return hn;
@@ -1356,7 +1342,9 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
       if ((q = enqueue_orth(j, w)) != SP_OK) return q;
       return sp_cuda(c, rec(ev[2]), "event");
     };
-    for (int j = 0; j < K; ++j) {
+    // Column j + 1 is launched before the host reads column j: the stopping test then runs while
+    // the device works. When the test stops at column j, column j + 1 is computed and discarded.
+    auto launch_step = [&](int j) -> sp_status {
       bool launched = false;
       if (graphs) {
         auto itg = c->ngraphs.find(j);
@@ -1378,15 +1366,21 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
           }
         }
         if (graphs) {
-          if ((s = sp_cuda(c, cudaGraphLaunch(itg->second, st), "graph launch")) != SP_OK) return s;
+          sp_status q = sp_cuda(c, cudaGraphLaunch(itg->second, st), "graph launch");
+          if (q != SP_OK) return q;
           launched = true;
         }
       }
-      if (!launched && (s = enqueue_step(j, false)) != SP_OK) return s;
-      if ((s = sp_cuda(c, cudaStreamSynchronize(st), "arnoldi sync")) != SP_OK) return s;
+      return launched ? SP_OK : enqueue_step(j, false);
+    };
+    if ((s = launch_step(0)) != SP_OK) return s;
+    for (int j = 0; j < K; ++j) {
+      const bool ahead = j + 1 < K;
+      if (ahead && (s = launch_step(j + 1)) != SP_OK) return s;
+      cudaEvent_t* ev = c->nev.data() + 3 * (size_t)j;
+      if ((s = sp_cuda(c, cudaEventSynchronize(ev[2]), "arnoldi sync")) != SP_OK) return s;
       const double hn = finish_orth(j);
       float ta = 0, tb = 0;
-      cudaEvent_t* ev = c->nev.data() + 3 * (size_t)j;
       if (cudaEventElapsedTime(&ta, ev[0], ev[1]) == cudaSuccess) r.t_action_ms += ta;
       else cudaGetLastError();  // timing is best effort; keep the error state clean
       if (cudaEventElapsedTime(&tb, ev[1], ev[2]) == cudaSuccess) r.t_orth_ms += tb;
@@ -1394,7 +1388,10 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
       r.total_jvps++;
       k = j + 1;
       if (!std::isfinite(hn)) return sp_fail(c, SP_ENAN, "non-finite Arnoldi vector");
-      if (std::fabs(g[k]) <= o->eta * nF || hn == 0.0) break;
+      if (std::fabs(g[k]) <= o->eta * nF || hn == 0.0) {
+        if (ahead) r.spec_jvps++;
+        break;
+      }
     }
     // optional extra direction: the steepest-descent direction J^* F of |F|^2 / 2,
     // made orthogonal to the Krylov basis; one more (flexible) Arnoldi column

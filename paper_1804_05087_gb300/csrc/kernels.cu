@@ -896,7 +896,10 @@ __device__ __forceinline__ void solve_body(const C2<T>* __restrict__ in3, const 
 template <typename T, int TM, int THREADS, bool LA>
 __global__ void __launch_bounds__(THREADS) k_solve(const C2<T>* __restrict__ in3, const double2* __restrict__ du,
                                                    double2* __restrict__ out, SolveArgs a) {
-  solve_body<T, TM, LA>(in3, du, out, a, blockIdx.x, blockIdx.y);
+  // with laminar advection in L the grid runs directions fastest: blocks that run together share a
+  // mode tile, so its complex operators (133 KB per mode) are read from DRAM once and from L2 after
+  if constexpr (LA) solve_body<T, TM, LA>(in3, du, out, a, blockIdx.y, blockIdx.x);
+  else solve_body<T, TM, LA>(in3, du, out, a, blockIdx.x, blockIdx.y);
 }
 
 
@@ -1499,97 +1502,6 @@ static YinvTabs<T> yinv_tabs(const sp_ctx* c) {
   return t;
 }
 
-// ----------------------------------------------- fused Gram-Schmidt passes
-// One classical Gram-Schmidt pass of an Arnoldi step in a single launch, for states small
-// enough that launches, not bandwidth, set the cost. Block b owns a contiguous slice of the
-// complex elements. MODE 1 and 2 first apply the previous pass, w -= sum_i hprev_i V_i, to
-// the slice; MODE 0 and 1 then form the block's partial inner products <V_i, w> (a warp per
-// i), MODE 2 the partial |w|^2. Each block then takes a ticket; the block that draws the
-// last one (it waits for nobody: the others have finished) sums the partials in block
-// order, so the result is deterministic, writes h to hout and to the host buffer, and in
-// MODE 2 also normalises w (its slices were all updated before the tickets were drawn).
-// counter: a device word that is 0 between launches (the last block resets it).
-template <int MODE>
-__global__ void __launch_bounds__(256) k_orth_pass(const double2* __restrict__ V, int k, int ncplx, double2* w, int NY,
-                                                  int MZ, const double* hprev, double* partials, double* hout,
-                                                  double* host_out, unsigned* counter) {
-  const int G = gridDim.x, b = blockIdx.x;
-  const int chunk = (ncplx + G - 1) / G;
-  const int e0 = b * chunk, e1 = min(ncplx, e0 + chunk);
-  if (MODE >= 1) {
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      double2 acc = w[e];
-      for (int i = 0; i < k; ++i) {
-        const double h = hprev[i];
-        const double2 v = V[(size_t)i * ncplx + e];
-        acc.x = fma(-h, v.x, acc.x);
-        acc.y = fma(-h, v.y, acc.y);
-      }
-      w[e] = acc;
-    }
-    __syncthreads();
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int nrow = MODE == 2 ? 1 : k;
-  for (int i = warp; i < nrow; i += nw) {
-    const double2* vi = MODE == 2 ? w : V + (size_t)i * ncplx;
-    double acc = 0.0;
-    for (int e = e0 + lane; e < e1; e += 32) {
-      const double wt = ((e / NY) % MZ) == 0 ? 1.0 : 2.0;
-      const double2 a = vi[e], c = w[e];
-      acc += wt * (a.x * c.x + a.y * c.y);
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) partials[(size_t)i * G + b] = acc;
-  }
-  __threadfence();
-  __syncthreads();
-  __shared__ unsigned ticket;
-  if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
-  __syncthreads();
-  if (ticket != (unsigned)(G - 1)) return;
-  __threadfence();
-  for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
-    double h = 0.0;
-    for (int q = 0; q < G; ++q) h += __ldcg(partials + (size_t)i * G + q);
-    if (MODE == 2) {
-      const double hn = sqrt(h);
-      hout[0] = hn;
-      hout[1] = hn > 0.0 ? 1.0 / hn : 0.0;
-      host_out[0] = hn;
-    } else {
-      hout[i] = h;
-      host_out[i] = h;
-    }
-  }
-  if (MODE == 2) {
-    __syncthreads();
-    const double inv = __ldcg(hout + 1);
-    for (int e = threadIdx.x; e < ncplx; e += blockDim.x) {
-      double2 v = __ldcg(w + e);
-      v.x *= inv;
-      v.y *= inv;
-      w[e] = v;
-    }
-  }
-  if (threadIdx.x == 0) *counter = 0u;
-}
-
-cudaError_t launch_orth_pass(const sp_ctx* c, int mode, const double* V, int k, double* w, const double* hprev,
-                             double* partials, int nblocks, double* hout, double* host_out, unsigned* counter,
-                             cudaStream_t st) {
-  const int n = (int)c->cplx_per_state;
-  const double2* Vc = reinterpret_cast<const double2*>(V);
-  double2* wc = reinterpret_cast<double2*>(w);
-  if (mode == 0)
-    k_orth_pass<0><<<nblocks, 256, 0, st>>>(Vc, k, n, wc, c->NY, c->MZ, hprev, partials, hout, host_out, counter);
-  else if (mode == 1)
-    k_orth_pass<1><<<nblocks, 256, 0, st>>>(Vc, k, n, wc, c->NY, c->MZ, hprev, partials, hout, host_out, counter);
-  else
-    k_orth_pass<2><<<nblocks, 256, 0, st>>>(Vc, k, n, wc, c->NY, c->MZ, hprev, partials, hout, host_out, counter);
-  return cudaGetLastError();
-}
-
 // ------------------------------------------------------------ grouped kernels
 // One launch over several independent problems: block b runs block
 // b - first[inst[b]] of member inst[b]'s own launch (with a single direction),
@@ -1713,6 +1625,7 @@ size_t sp_xz_global_plane_bytes(const sp_ctx* c) {
 
 cudaError_t launch_yinv(const sp_ctx* c, bool fp32, const double* in, void* out6, int n_dir,
                         cudaStream_t st) {
+  if (fp32 && c->use_yinv_tc && sp_yinv_tc_supported(c)) return launch_yinv_tc(c, in, out6, n_dir, st);
   YinvArgs a = yinv_args(c);
   if (fp32) a.q2 = 0;
   const int nj = a.q2 ? a.NQ : c->NH;
@@ -1772,7 +1685,8 @@ cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, voi
                       cudaStream_t st) {
   if (fp32 && c->use_xz_reg && sp_xz_reg_supported(c) && (mode == XZ_TANGENT || mode == XZ_ADJOINT))
     return launch_xz_reg(c, mode, in6, out3, n_dir, st);
-  if (!fp32 && c->use_xz_reg64 && sp_xz_reg64_supported(c) && (mode == XZ_TANGENT || mode == XZ_ADJOINT))
+  if (!fp32 && c->use_xz_reg64 && sp_xz_reg64_supported(c) &&
+      (mode == XZ_TANGENT || mode == XZ_ADJOINT || mode == XZ_STEP || mode == XZ_STEP_BASE))
     return launch_xz_reg64(c, mode, in6, out3, n_dir, st);
   if (fp32) {
     const C2<float>* tx = reinterpret_cast<const C2<float>*>(c->twx_f);
@@ -1853,7 +1767,8 @@ static cudaError_t launch_solve_t(const sp_ctx* c, const SolveArgs& a, const voi
   auto kern = c->cfg.lam_adv ? k_solve<T, TM, MAXT, true> : k_solve<T, TM, MAXT, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  dim3 grid((c->n_unique + TM - 1) / TM, n_dir);
+  const unsigned tiles = (c->n_unique + TM - 1) / TM;
+  const dim3 grid = c->cfg.lam_adv ? dim3(n_dir, tiles) : dim3(tiles, n_dir);
   kern<<<grid, threads, sm, st>>>(reinterpret_cast<const C2<T>*>(in3), reinterpret_cast<const double2*>(du),
                                   reinterpret_cast<double2*>(out), a);
   return cudaGetLastError();

@@ -623,6 +623,22 @@ sp_status sp_build_plan(sp_ctx* c) {
             (!c->use_chain || (up((void**)&c->chain, chain.data(), chain.size() * 8) &&
                                up((void**)&c->omega, omega.data(), omega.size() * 8)));
   if (!ok) return sp_fail(c, SP_ENOMEM, "device allocation of plan tables failed");
+  // the tensor-core inverse transform's constant operands: the full T and T' (all NY points)
+  if (c->geom == 0 && c->NY >= 41 && c->NY <= 72) {
+    std::vector<double> th((size_t)n1 * n1), td((size_t)n1 * n1);
+    for (int j = 0; j < n1; ++j)
+      for (int n = 0; n < n1; ++n) {
+        th[(size_t)j * n1 + n] = cospi_frac((long)j * n, N);
+        double d;
+        if (j == 0) d = (double)n * n;
+        else if (j == N) d = ((n + 1) % 2 == 0 ? 1.0 : -1.0) * n * n;
+        else d = n * cospi_frac((long)N - 2L * j * n, 2L * N) / cospi_frac((long)N - 2L * j, 2L * N);
+        td[(size_t)j * n1 + n] = d;
+      }
+    const std::vector<float> img = yinv_tc_image(th.data(), td.data(), n1);
+    if (!up((void**)&c->yinv_tc_mat, img.data(), img.size() * 4))
+      return sp_fail(c, SP_ENOMEM, "device allocation of plan tables failed");
+  }
   if (q2) {
     std::vector<float> Tpf(Tp.begin(), Tp.end()), TDpf(TDp.begin(), TDp.end()), tqf(tq.begin(), tq.end()),
         Cqf(Cq.begin(), Cq.end());

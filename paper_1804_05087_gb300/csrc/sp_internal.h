@@ -59,6 +59,7 @@ struct sp_ctx {
   sp_pipe_config pcfg{};
   int dev = 0;
   int sm_count = 0;
+  int coop = 0;                  // cooperative launches supported (orth.cu)
   int nx = 0, ny = 0, nz = 0;
   int N = 0, NH = 0;             // Chebyshev degree, N/2 + 1
   int Kx = 0, Kz = 0, MX = 0, MZ = 0, NY = 0, Mm = 0;
@@ -90,6 +91,9 @@ struct sp_ctx {
   // rows n <= N-2, jq <= N/4 (solve_chain.cu)
   double* Cq = nullptr;
   float* Cq_f = nullptr;
+  // tensor-core inverse transform (41 <= NY <= 72): shared-memory image of T and T' split into
+  // TF32 hi and lo parts (yinv_tc.cu)
+  float* yinv_tc_mat = nullptr;
   double* yv = nullptr;          // [NY] wall-normal points: cos(pi j / N) (Couette), r_j (pipe)
   double* lam6 = nullptr;        // [NY][6] laminar (U, Omega) per plane: (y,0,0,0,0,-1) / (0,0,1-r^2,0,2r,0)
   float *Th_f = nullptr, *TDh_f = nullptr, *Cfh_f = nullptr;
@@ -119,6 +123,7 @@ struct sp_ctx {
   int has_base = 0;
   int use_xz_reg = 1;            // float plane stage: register FFT kernel when the size allows
   int use_xz_reg64 = 1;          // FP64 tangent/adjoint plane stage: register FFT kernel (xz_reg64.cu)
+  int use_yinv_tc = 1;           // float inverse Chebyshev transform on the tensor cores (yinv_tc.cu)
   int solve_shape_tan = 0;       // k_solve tile shape of the tangent (sp_autotune)
   int solve_shape_step = 0;      // k_solve tile shape of the FP64 step
   // sizes of shared memory per kernel (bytes)
@@ -135,8 +140,6 @@ struct sp_ctx {
   // Newton scratch
   double* kry = nullptr;         // Krylov basis [max_krylov+1] states
   int kry_cap = 0;
-  double* orth_part = nullptr;   // [orth_cap][orth_blocks] partial sums of the fused Gram-Schmidt passes
-  int orth_blocks = 0, orth_cap = 0;
   // multi-step map B^n (sp_step_n / sp_set_base_n / sp_jvp_n)
   double* traj = nullptr;        // [traj_cap] states: U_0 .. U_{n-1} of the last sp_set_base_n
   int traj_cap = 0;
@@ -236,6 +239,13 @@ cudaError_t launch_xz(const sp_ctx* c, bool fp32, int mode, const void* in6, voi
 // float plane stage with register-resident FFTs (xz_reg.cu), square grids 16..64
 bool sp_xz_reg_supported(const sp_ctx* c);
 cudaError_t launch_xz_reg(const sp_ctx* c, int mode, const void* in, void* out, int n_dir, cudaStream_t st);
+// float inverse Chebyshev transform + curl on the tensor cores (yinv_tc.cu); same inputs and
+// outputs as launch_yinv with fp32; yinv_tc_image: the host image of the constant operands from the
+// full tables th[j][n] = T_n(y_j), td[j][n] = T_n'(y_j) (NY x NY, row-major)
+bool sp_yinv_tc_supported(const sp_ctx* c);
+cudaError_t launch_yinv_tc(const sp_ctx* c, const double* in, void* out6, int n_dir, cudaStream_t st);
+std::vector<float> yinv_tc_image(const double* th, const double* td, int NY);
+size_t yinv_tc_smem(int NY);
 // FP64 plane stage with register-resident FFTs (xz_reg64.cu), square grids 16..48
 bool sp_xz_reg64_supported(const sp_ctx* c);
 cudaError_t launch_xz_reg64(const sp_ctx* c, int mode, const void* in, void* out, int n_dir, cudaStream_t st);
@@ -286,13 +296,13 @@ cudaError_t launch_dev_norm(const sp_ctx* c, const double* w, double* partials, 
                             double* inv, cudaStream_t st);
 cudaError_t launch_scale_dev(const sp_ctx* c, double* x, const double* s, cudaStream_t st);
 // w -= sum_i h_i V_i (h on device)
+// one Arnoldi column (CGS2 + normalisation) in a single cooperative launch for small states
+// (orth.cu): blocks for this context, 0 if it does not apply
+int orth_fused_blocks(const sp_ctx* c);
+size_t orth_fused_smem(int k);
+cudaError_t launch_orth_fused(const sp_ctx* c, const double* V, int k, double* w, double* part, int G, double* hA,
+                              double* hB, double* hn, double* host, int kh, unsigned* bar, cudaStream_t st);
 cudaError_t launch_multi_axpy(const sp_ctx* c, const double* V, int k, const double* h,
                               double* w, cudaStream_t st, const int* gate = nullptr);
-// one fused classical Gram-Schmidt pass (mode 0: dots; 1: subtract hprev, then dots; 2: subtract
-// hprev, then |w| into hout[0], 1/|w| into hout[1] and w normalised); h also goes to host_out
-// (pinned host memory); counter: a device word, 0 between launches. For small states.
-cudaError_t launch_orth_pass(const sp_ctx* c, int mode, const double* V, int k, double* w, const double* hprev,
-                             double* partials, int nblocks, double* hout, double* host_out, unsigned* counter,
-                             cudaStream_t st);
 // second Gram-Schmidt pass needed? *flag = (|w|^2 - |h|^2 < |w|^2 / 2); if not, h2 = 0 (k entries)
 cudaError_t launch_reorth_decide(const double* h, int k, const double* wn, int* flag, double* h2, cudaStream_t st);

@@ -1,4 +1,4 @@
-// Plane stage of the tangent and the adjoint in FP64 with register-resident FFTs
+// Plane stage of the step, the tangent and the adjoint in FP64 with register-resident FFTs
 // (the FP64 counterpart of xz_reg.cu; same mathematics as k_xz in kernels.cu):
 // per y-plane, inverse FFT along x of every (field, kz) column, packed c2r along
 // z of pairs of x-rows, the pointwise product, packed r2c along z, forward FFT
@@ -30,7 +30,9 @@ using cd = C2<double>;
 struct Xz64Args {
   const cd* in;         // [dir][NIN][NY][Mm]
   cd* out;              // [dir][NOUT][NY][Mm]
-  const double* base;   // [6][NY][NX][NZ] FP64 base fields (U_tot, Omega_tot)
+  double* base;         // [6][NY][NX][NZ] FP64 base fields (U_tot, Omega_tot): read by the tangent and
+                        // the adjoint, written by XZ_STEP_BASE
+  const double* lam;    // [NY][6] laminar U and Omega of each plane (XZ_STEP, XZ_STEP_BASE)
   int NY, Mm;
 };
 
@@ -217,6 +219,11 @@ __device__ __forceinline__ void xz64_body(const Xz64Args& a, int bx, int by) {
   {
     const size_t nxz = (size_t)NX * NZ;
     const double* bj = a.base + (size_t)j * nxz;
+    double lamj[6] = {0, 0, 0, 0, 0, 0};
+    if constexpr (MODE == XZ_STEP || MODE == XZ_STEP_BASE) {
+#pragma unroll
+      for (int f = 0; f < 6; ++f) lamj[f] = a.lam[(size_t)j * 6 + f];
+    }
     for (int it = threadIdx.x; it < NQ * NZ; it += blockDim.x) {
       const int q = it / NZ, k = it - q * NZ;
       cd fv[NIN];
@@ -228,10 +235,25 @@ __device__ __forceinline__ void xz64_body(const Xz64Args& a, int bx, int by) {
         double F[NIN], B[6];
 #pragma unroll
         for (int f = 0; f < NIN; ++f) F[f] = r ? fv[f].y : fv[f].x;
-        const size_t gi = (size_t)(2 * q + r) * NZ + k;
+        if constexpr (MODE == XZ_TANGENT || MODE == XZ_ADJOINT) {
+          const size_t gi = (size_t)(2 * q + r) * NZ + k;
 #pragma unroll
-        for (int f = 0; f < 6; ++f) B[f] = __ldg(bj + (size_t)f * a.NY * nxz + gi);
-        if constexpr (MODE == XZ_TANGENT) {
+          for (int f = 0; f < 6; ++f) B[f] = __ldg(bj + (size_t)f * a.NY * nxz + gi);
+        }
+        if constexpr (MODE == XZ_STEP || MODE == XZ_STEP_BASE) {
+          // the step: U_tot x Omega_tot of the state plus laminar flow (B unused)
+          double Tt[6];
+#pragma unroll
+          for (int f = 0; f < 6; ++f) Tt[f] = F[f] + lamj[f];
+          if constexpr (MODE == XZ_STEP_BASE) {
+            const size_t gi = (size_t)(2 * q + r) * NZ + k;
+#pragma unroll
+            for (int f = 0; f < 6; ++f) a.base[(size_t)f * a.NY * nxz + (size_t)j * nxz + gi] = Tt[f];
+          }
+          res[r][0] = Tt[1] * Tt[5] - Tt[2] * Tt[4];
+          res[r][1] = Tt[2] * Tt[3] - Tt[0] * Tt[5];
+          res[r][2] = Tt[0] * Tt[4] - Tt[1] * Tt[3];
+        } else if constexpr (MODE == XZ_TANGENT) {
           res[r][0] = (B[1] * F[5] - B[2] * F[4]) + (F[1] * B[5] - F[2] * B[4]);
           res[r][1] = (B[2] * F[3] - B[0] * F[5]) + (F[2] * B[3] - F[0] * B[5]);
           res[r][2] = (B[0] * F[4] - B[1] * F[3]) + (F[0] * B[4] - F[1] * B[3]);
@@ -311,6 +333,7 @@ cudaError_t launch64(const sp_ctx* c, const void* in, void* out, int n_dir, cuda
   a.in = reinterpret_cast<const cd*>(in);
   a.out = reinterpret_cast<cd*>(out);
   a.base = c->base64;
+  a.lam = c->lam6;
   a.NY = c->NY;
   a.Mm = c->Mm;
   cudaError_t e = cudaFuncSetAttribute(k_xz_reg64<NX, NZ, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -342,5 +365,7 @@ cudaError_t launch_xz_reg64(const sp_ctx* c, int mode, const void* in, void* out
   if (!sp_xz_reg64_supported(c)) return cudaErrorNotSupported;
   if (mode == XZ_TANGENT) return dispatch64<XZ_TANGENT>(c, in, out, n_dir, st);
   if (mode == XZ_ADJOINT) return dispatch64<XZ_ADJOINT>(c, in, out, n_dir, st);
+  if (mode == XZ_STEP) return dispatch64<XZ_STEP>(c, in, out, n_dir, st);
+  if (mode == XZ_STEP_BASE) return dispatch64<XZ_STEP_BASE>(c, in, out, n_dir, st);
   return cudaErrorNotSupported;
 }

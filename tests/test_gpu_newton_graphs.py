@@ -20,8 +20,10 @@ def test_graph_replay_identical(use_gradient, grid, re, kmax):
                              use_gradient=use_gradient)
     assert r1["converged"] and r2["converged"], (r1, r2)
     assert torch.equal(U1, U2)
-    for k in ("newton_iters", "total_jvps", "total_steps"):
+    for k in ("newton_iters", "total_jvps", "total_steps", "spec_jvps"):
         assert r1[k] == r2[k]
+    # column j + 1 runs while the host tests column j: at most one discarded action per GMRES solve
+    assert 0 <= r1["spec_jvps"] <= r1["newton_iters"] + 1
 
 
 def test_graphs_survive_a_larger_basis():
