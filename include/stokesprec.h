@@ -344,6 +344,10 @@ typedef struct {
   double t_total_ms;
   int spec_jvps;      /* actions computed ahead of a GMRES stopping test that
                          then stopped, and discarded (not in total_jvps)      */
+  int hook_trials;    /* hookstep trials (residual evaluations) over all steps */
+  double delta;       /* trust-region radius at exit                         */
+  double lin_rel;     /* relative residual |F - J X| / |F| of the last linear
+                         solve (GMRES; -1 for the short recurrences)          */
 } sp_newton_report;
 
 /* Newton-GMRES with hookstep (Sec. 2, Sec. 3.2): U_inout holds the initial

@@ -96,6 +96,7 @@ static void free_ctx(sp_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
+  if (c->kry_host) cudaFreeHost(c->kry_host);
   if (c->hbuf) cudaFree(c->hbuf);
   for (cudaEvent_t e : {c->hev_start, c->hev_in[0], c->hev_in[1], c->hev_comp[0], c->hev_comp[1], c->hev_out[0],
                         c->hev_out[1]})
@@ -152,7 +153,6 @@ extern "C" sp_status sp_create(const sp_config* cfg, sp_ctx** out) {
   if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(SP_ECUDA, "no device");
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
   if (c->sm_count <= 0) c->sm_count = 1;
-  cudaDeviceGetAttribute(&c->coop, cudaDevAttrCooperativeLaunch, c->dev);
   if (sp_build_plan(c) != SP_OK) return bail(SP_EINVAL, c->err);
   if (!sp_xz_fits(c)) return bail(SP_EINVAL, "grid too large for the plane kernel");
   c->field_cplx = c->cplx_per_state;
@@ -231,7 +231,6 @@ extern "C" sp_status sp_pipe_create(const sp_pipe_config* cfg, sp_ctx** out) {
   if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(SP_ECUDA, "no device");
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
   if (c->sm_count <= 0) c->sm_count = 1;
-  cudaDeviceGetAttribute(&c->coop, cudaDevAttrCooperativeLaunch, c->dev);
   if (sp_build_pipe_plan(c) != SP_OK) return bail(SP_EINVAL, c->err);
   if (!sp_xz_fits(c)) return bail(SP_EINVAL, "grid too large for the plane kernel");
   if (!alloc_workspaces(c)) return bail(SP_ENOMEM, "workspace allocation");
@@ -1041,7 +1040,9 @@ static sp_status short_vectors(sp_ctx* c, const sp_newton_opts* o, int* nsolve) 
   if (c->kry_cap < nvec) {
     drop_newton_graphs(c);  // they hold pointers into the old basis
     if (c->kry) cudaFree(c->kry);
+    if (c->kry_host) cudaFreeHost(c->kry_host);
     c->kry = nullptr;
+    c->kry_host = nullptr;  // no GMRES scratch in this allocation: sp_newton_gmres reallocates
     c->kry_cap = 0;
     if (cudaMalloc((void**)&c->kry, (size_t)nvec * c->state_len * 8) != cudaSuccess) {
       cudaGetLastError();
@@ -1092,6 +1093,7 @@ static sp_status newton_short(sp_ctx* c, double* U, const sp_newton_opts* o, sp_
     bool accepted = false;
     double nT = nF;
     for (int trial = 0; trial < 12 && nX > 0 && std::isfinite(nX); ++trial) {
+      rep->hook_trials++;
       const double sc = std::min(1.0, delta / nX);
       const double pred = std::sqrt(std::max(0.0, nF * nF - 2.0 * sc * fj + sc * sc * jj));
       if ((s = k.axpby(Ut, 1.0, U, -sc, X)) != SP_OK) return s;
@@ -1114,6 +1116,8 @@ static sp_status newton_short(sp_ctx* c, double* U, const sp_newton_opts* o, sp_
   }
   if ((s = sp_cuda(c, cudaStreamSynchronize(st), "newton sync")) != SP_OK) return s;
   rep->norm_F = nF;
+  rep->delta = delta;
+  rep->lin_rel = -1.0;
   rep->t_total_ms = now_ms() - t0;
   rep->t_action_ms = -1.0;  // not split for the short-recurrence solvers
   if (result == SP_ENOTCONV) c->err = "Newton did not reach the tolerance";
@@ -1192,17 +1196,17 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   const size_t L = c->state_len;
   // one partial sum per ~1024 complex values, at most red_blocks
   const int nb = (int)std::max<size_t>(1, std::min<size_t>(c->red_blocks, (c->cplx_per_state + 1023) / 1024));
-  // small states: each Arnoldi column in one cooperative launch over gf blocks (orth.cu)
-  const int gf = orth_fused_blocks(c);
-  const int nbp = std::max(nb, gf);
   // device scratch after the basis: partials, hA, hB, hn/inv
-  const size_t extra = (size_t)(K + 2) * nbp + 3 * (size_t)(K + 3) + 24;
-  if (c->kry_cap < K + 5) {
+  const size_t extra = (size_t)(K + 2) * nb + 3 * (size_t)(K + 3) + 24 + (size_t)orth_small_blocks(c);
+  if (c->kry_cap < K + 5 || !c->kry_host) {
     drop_newton_graphs(c);  // they hold pointers into the old basis
     if (c->kry) cudaFree(c->kry);
+    if (c->kry_host) cudaFreeHost(c->kry_host);
     c->kry = nullptr;
+    c->kry_host = nullptr;
     c->kry_cap = 0;
-    if (cudaMalloc((void**)&c->kry, ((size_t)(K + 5) * L + extra) * 8) != cudaSuccess) {
+    if (cudaMalloc((void**)&c->kry, ((size_t)(K + 5) * L + extra) * 8) != cudaSuccess ||
+        cudaMallocHost((void**)&c->kry_host, ((size_t)4 * (K + 3) + 4) * 8) != cudaSuccess) {
       cudaGetLastError();
       return sp_fail(c, SP_ENOMEM, "Krylov basis allocation");
     }
@@ -1215,18 +1219,17 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   double* Ut = c->kry + (size_t)(Kc + 3) * L;    // trial state
   double* Zg = c->kry + (size_t)(Kc + 4) * L;    // gradient direction (use_gradient)
   double* dpart = c->kry + (size_t)(Kc + 5) * L; // partial sums
-  double* dhA = dpart + (size_t)(Kc + 2) * nbp;  // first Gram-Schmidt pass
+  double* dhA = dpart + (size_t)(Kc + 2) * nb;   // first Gram-Schmidt pass
   double* dhB = dhA + (Kc + 3);                  // second pass
   double* dhn = dhB + (Kc + 3);                  // [0] = |w|, [1] = 1/|w|, then y
   double* dwn = dhn + (Kc + 6);                  // |w| before the first pass, scratch
   int* dflag = reinterpret_cast<int*>(dwn + 4);  // second Gram-Schmidt pass needed
-  unsigned* dbar = reinterpret_cast<unsigned*>(dwn + 6);  // grid barrier of the fused column
+  double* dnorm = dwn + 8;                         // partial norms of the small-state column
   // pinned: two copies of hA | hB | hn, column j in copy j mod 2, so that the host reads column j
   // while column j + 1 is computed
+  // (a buffer of its own: the actions of column j + 1 may use the context's reduction buffer)
   const size_t hstride = (size_t)2 * (Kc + 3) + 2;
-  double* hbuf = c->red_host;
-  if (2 * hstride > (size_t)64 * c->red_blocks + 512)
-    return sp_fail(c, SP_EINVAL, "sp_newton_gmres: Krylov dimension too large for the pinned buffer");
+  double* hbuf = c->kry_host;
   // CUDA graphs of the Arnoldi steps: tangent actions only, on the context's own stream
   bool graphs = o->use_graphs && !o->use_fd && ns == 1 && !c->trace;
   if (graphs && !c->nstream) {
@@ -1249,7 +1252,6 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   sp_newton_report r{};
   const double t0 = now_ms();
   sp_status s;
-  if (gf > 0 && (s = sp_cuda(c, cudaMemsetAsync(dbar, 0, 16, st), "barrier reset")) != SP_OK) return s;
   auto norm = [&](const double* x, double* out) { return inner_many(c, x, 1, x, out, st); };
   if ((s = step_n(c, U, F, ns, st)) != SP_OK) return s;
   r.total_steps += ns;
@@ -1278,16 +1280,17 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     // orthogonalise w = (action on column j) against V[0..j] (CGS2 on the device), normalise it
     // into V[j+1], and update column j of H, its Givens-rotated copy R and the residual g
     // device part of one Arnoldi column (capturable): classical Gram-Schmidt twice, normalisation,
-    // copies to the host. For large states the second pass runs only when the first one lost
-    // too much (|w'| < |w|/sqrt(2), decided on the device): it halves the basis traffic; small
-    // states are latency-bound and keep the shorter launch sequence of the full second pass.
+    // the column to the host. For large states the second pass runs only when the first one lost
+    // too much (|w'| < |w|/sqrt(2), decided on the device): it halves the basis traffic. Small
+    // states are bound by FP64 work and launch latency: orth.cu (the same selective second pass).
     const bool selective = L >= 65536;
+    const bool small = !selective && orth_small_applies(c, nb);
     auto enqueue_orth = [&](int j, double* w) -> sp_status {
       sp_status q;
       double* hb = hbuf + (size_t)(j & 1) * hstride;
-      if (gf > 0)
-        return sp_cuda(c, launch_orth_fused(c, V, j + 1, w, dpart, gf, dhA, dhB, dhn, hb, Kc + 3, dbar, st),
-                       "fused column");
+      if (small)
+        return sp_cuda(c, launch_orth_small(c, V, j + 1, w, dpart, nb, dhA, dhB, dhn, hb, Kc + 3, dflag, dnorm, st),
+                       "column");
       const int* gate = selective ? dflag : nullptr;
       if ((q = sp_cuda(c, launch_dev_dots(c, V, j + 1, w, dpart, nb, dhA, nullptr, st), "dots")) != SP_OK) return q;
       if (selective) {
@@ -1422,11 +1425,13 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     // hookstep: minimise |g - R y| (R = rotated k x k Hessenberg) subject to |y| <= delta.
     // The constrained minimiser is y(mu) = (R^T R + mu I)^-1 R^T g with mu >= 0 chosen so that
     // |y(mu)| = delta; R^T R = Q T Q^T (tridiagonal T) makes every |y(mu)| an O(k) solve.
+    r.lin_rel = std::fabs(g[k]) / nF;
     Hookstep hs;
     hs.init(R.data(), LD, k, g.data());
     bool accepted = false;
     double nT = nF;
     for (int trial = 0; trial < 12; ++trial) {
+      r.hook_trials++;
       double pred = 0, ylen = 0;
       const std::vector<double> y = hs.solve(delta, &pred, &ylen);
       if ((s = sp_cuda(c, cudaMemcpyAsync(Ut, U, L * 8, cudaMemcpyDeviceToDevice, st), "copy")) != SP_OK) return s;
@@ -1456,6 +1461,7 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
   }
   if ((s = sp_cuda(c, cudaStreamSynchronize(st), "newton sync")) != SP_OK) return s;
   r.norm_F = nF;
+  r.delta = delta;
   r.t_total_ms = now_ms() - t0;
   if (rep) *rep = r;
   if (result == SP_ENOTCONV) c->err = "Newton did not reach the tolerance";

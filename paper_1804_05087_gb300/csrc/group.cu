@@ -725,6 +725,7 @@ extern "C" sp_status sp_group_newton_gmres(sp_group* g, double* U, const sp_newt
     }
     // ---- hookstep trials, all members that need one in lock step
     for (int i = 0; i < n; ++i) {
+      if (run[i] && kk[i] > 0) r[i].lin_rel = std::fabs(gv[i][kk[i]]) / nF[i];
       tr[i] = run[i] && kk[i] > 0;
       if (tr[i]) hs[i].init(R[i].data(), LD, kk[i], gv[i].data());
     }
@@ -749,6 +750,7 @@ extern "C" sp_status sp_group_newton_gmres(sp_group* g, double* U, const sp_newt
       for (int i = 0; i < n; ++i) {
         if (!tr[i]) continue;
         r[i].total_steps++;
+        r[i].hook_trials++;
         if (trust_update(nF[i], pred[i], nT[i], ylen[i], &delta[i])) {
           acc[i] = 1;
           tr[i] = 0;
@@ -773,6 +775,7 @@ extern "C" sp_status sp_group_newton_gmres(sp_group* g, double* U, const sp_newt
   for (int i = 0; i < n; ++i) {
     if (stat[i] == 0 && nF[i] < o->tol) stat[i] = 1;
     r[i].norm_F = nF[i];
+    r[i].delta = delta[i];
     r[i].t_action_ms = t_action;
     r[i].t_orth_ms = t_orth;
     r[i].t_total_ms = ttot;

@@ -1354,12 +1354,13 @@ __global__ void k_multi_inner8(const double2* V, int k, size_t ncplx, const doub
   unsigned rr = e0 % (unsigned)NY, iz = (e0 / (unsigned)NY) % (unsigned)MZ;
   for (size_t e = e0; e < ncplx; e += S) {
     const double wt = iz == 0 ? 1.0 : 2.0;
-    const double2 b = w[e];
+    const double2 b0 = w[e];
+    const double2 b = make_double2(wt * b0.x, wt * b0.y);  // the weight once per entry
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       if (i0 + q < k) {
         const double2 a = V[(size_t)(i0 + q) * ncplx + e];
-        acc[q] += wt * (a.x * b.x + a.y * b.y);
+        acc[q] = fma(a.y, b.y, fma(a.x, b.x, acc[q]));
       }
     }
     rr += dr;
@@ -1917,6 +1918,14 @@ cudaError_t launch_dev_dots(const sp_ctx* c, const double* V, int k, const doubl
   k_multi_inner8<<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(V), k, c->cplx_per_state,
                                        reinterpret_cast<const double2*>(w), c->NY, c->MZ, partials, gate);
   k_reduce_rows<<<k, 256, 0, st>>>(partials, nblocks, out, add, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_partial_dots(const sp_ctx* c, const double* V, int k, const double* w, double* partials, int nb,
+                                cudaStream_t st, const int* gate) {
+  dim3 grid(nb, (k + 7) / 8);
+  k_multi_inner8<<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(V), k, c->cplx_per_state,
+                                       reinterpret_cast<const double2*>(w), c->NY, c->MZ, partials, gate);
   return cudaGetLastError();
 }
 

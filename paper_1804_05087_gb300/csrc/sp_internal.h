@@ -59,7 +59,6 @@ struct sp_ctx {
   sp_pipe_config pcfg{};
   int dev = 0;
   int sm_count = 0;
-  int coop = 0;                  // cooperative launches supported (orth.cu)
   int nx = 0, ny = 0, nz = 0;
   int N = 0, NH = 0;             // Chebyshev degree, N/2 + 1
   int Kx = 0, Kz = 0, MX = 0, MZ = 0, NY = 0, Mm = 0;
@@ -119,6 +118,7 @@ struct sp_ctx {
   double* tmp = nullptr;         // [batch] states
   double* red = nullptr;         // reduction partials
   double* red_host = nullptr;    // pinned
+  double* kry_host = nullptr;    // pinned: two Hessenberg columns of sp_newton_gmres
   int red_blocks = 0;
   int has_base = 0;
   int use_xz_reg = 1;            // float plane stage: register FFT kernel when the size allows
@@ -296,12 +296,17 @@ cudaError_t launch_dev_norm(const sp_ctx* c, const double* w, double* partials, 
                             double* inv, cudaStream_t st);
 cudaError_t launch_scale_dev(const sp_ctx* c, double* x, const double* s, cudaStream_t st);
 // w -= sum_i h_i V_i (h on device)
-// one Arnoldi column (CGS2 + normalisation) in a single cooperative launch for small states
-// (orth.cu): blocks for this context, 0 if it does not apply
-int orth_fused_blocks(const sp_ctx* c);
-size_t orth_fused_smem(int k);
-cudaError_t launch_orth_fused(const sp_ctx* c, const double* V, int k, double* w, double* part, int G, double* hA,
-                              double* hB, double* hn, double* host, int kh, unsigned* bar, cudaStream_t st);
+// partial weighted dot products <V[i], w> (i < k) into partials[i][nb] (kernels.cu)
+// (gate: if non-null, the launch does nothing unless *gate is set)
+cudaError_t launch_partial_dots(const sp_ctx* c, const double* V, int k, const double* w, double* partials, int nb,
+                                cudaStream_t st, const int* gate);
+// one Arnoldi column (Gram-Schmidt with selective second pass, normalisation) for small states
+// (orth.cu); w must be V + k * state_len; normpart holds orth_small_blocks(c) doubles
+bool orth_small_applies(const sp_ctx* c, int nb);
+int orth_small_blocks(const sp_ctx* c);
+cudaError_t launch_orth_small(const sp_ctx* c, const double* V, int k, double* w, double* part, int nb, double* hA,
+                              double* hB, double* hn, double* host, int kh, int* flag, double* normpart,
+                              cudaStream_t st);
 cudaError_t launch_multi_axpy(const sp_ctx* c, const double* V, int k, const double* h,
                               double* w, cudaStream_t st, const int* gate = nullptr);
 // second Gram-Schmidt pass needed? *flag = (|w|^2 - |h|^2 < |w|^2 / 2); if not, h2 = 0 (k entries)
