@@ -560,64 +560,85 @@ def run_config2(args):
 
 
 def run_convergence(args):
-    """Newton to |G(U)| < 1e-10 on every workload, each from its seeded perturbed-laminar guess:
-    config 0 (16x33x16), config 1's grid (48x65x48), the 64 members of config 2 (lock-step
-    group), config 4 (96x97x96, Re 1000, doubled box). The Stokes step first; where its Krylov
-    spaces at high Re exceed the budget (Sec. 3.3: K grows with Re), the step with laminar
-    advection folded into L (Sec. 3.6) and larger Krylov spaces."""
-    import numpy as np
+    """Newton to |G(U)| < 1e-10 on every workload, each from its seeded guess: config 0
+    (16x33x16), config 1's grid (48x65x48), the 64 members of config 2 (lock-step group), the pipe
+    of config 3 and config 4 (96x97x96, Re 1000, doubled box). The Stokes step first; at high Re,
+    where its Krylov spaces exceed the budget (Sec. 3.3: K grows with Re), the step with laminar
+    advection folded into L (Sec. 3.6). Every run that stops short reports what stopped it: the
+    trust radius, the relative residual of the last linear solve and the length of the last
+    unconstrained Newton step."""
     import torch
     torch.cuda.set_device(0)
     import paper_1804_05087_gb300 as sp
     import seeded_inputs as si
     out = {"metric": "Newton to |F| < 1e-10 on every workload", "unit": "s", "runs": {}}
+    keep = ("newton_iters", "total_jvps", "total_steps", "norm_F0", "norm_F", "converged", "wall_s", "t_action_ms",
+            "t_orth_ms", "delta", "lin_rel", "newton_len", "hook_trials")
 
-    def single(name, grid, re, seed, lx=LX, lz=LZ, lam_adv=0, krylov=300, max_newton=30, prec=None):
-        prec = sp.SP_MIXED if prec is None else prec
-        ctx = sp.Context(sp.Config(*grid, lx=lx, lz=lz, re=re, dt=DT, prec=prec, lam_adv=lam_adv))
+    def single(name, grid, re, seed, lx=LX, lz=LZ, lam_adv=0, krylov=300, max_newton=30, use_gradient=False):
+        ctx = sp.Context(sp.Config(*grid, lx=lx, lz=lz, re=re, dt=DT, prec=sp.SP_MIXED, lam_adv=lam_adv))
         ctx.sp_autotune(1)
         a, b, c = si.couette_random_coeffs(seed, *grid)
         U = ctx.zeros()
         ctx.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], 0.1, U)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rep = ctx.sp_newton_gmres(U, max_newton=max_newton, max_krylov=krylov, tol=1e-10, eta=1e-3)
+        rep = ctx.sp_newton_gmres(U, max_newton=max_newton, max_krylov=krylov, tol=1e-10, eta=1e-3,
+                                  use_gradient=use_gradient)
         torch.cuda.synchronize()
         rep["wall_s"] = time.perf_counter() - t0
-        rep["norm_U"] = math.sqrt(ctx.sp_inner(U, U)[0])
-        rep.update({"grid": list(grid), "re": re, "lam_adv": lam_adv, "max_krylov": krylov, "max_newton": max_newton})
-        out["runs"][name] = rep
+        r = {k: rep[k] for k in keep}
+        r["norm_U"] = math.sqrt(ctx.sp_inner(U, U)[0])
+        r.update({"grid": list(grid), "re": re, "lam_adv": lam_adv, "max_krylov": krylov, "max_newton": max_newton,
+                  "seed": seed, "use_gradient": use_gradient})
+        out["runs"][name] = r
         ctx.close()
 
     single("config0_16x33x16_re400", (16, 33, 16), RE, 1000)
     single("config1_48x65x48_re400", (NX, NY, NZ), RE, BASE_SEED)
-    lx4, lz4 = 4 * math.pi / 1.14, 4 * math.pi / 2.5
-    single("config4_96x97x96_re1000_lam_adv_K1000", (96, 97, 96), 1000.0, 6000, lx=lx4, lz=lz4, lam_adv=1,
-           krylov=1000, max_newton=20)
-    # config 2: the 64 members in lock step
+    # config 2: the 64 members in lock step, laminar advection in L
     members = config2_members()
-    for lam_adv, krylov in ((1, 300),):
-        grp = sp.Group([sp.Config(*g, lx=LX, lz=LZ, re=re, dt=DT, prec=sp.SP_MIXED, lam_adv=lam_adv)
-                        for g, re in members])
-        U = grp.zeros()
-        for i, m in enumerate(grp.members):
-            a, b, c = si.couette_random_coeffs(3001 + i, m.cfg.nx, m.cfg.ny, m.cfg.nz)
-            m.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], 0.1, grp.member_view(U, i))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ok, reps = grp.sp_group_newton_gmres(U, max_newton=30, max_krylov=krylov, tol=1e-10, eta=1e-3,
-                                             use_graphs=True)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        conv = [r["norm_F"] < 1e-10 for r in reps]
-        out["runs"][f"config2_64_members_lam_adv{lam_adv}_K{krylov}"] = {
-            "wall_s": wall, "converged": int(sum(conv)), "members": len(reps),
-            "max_norm_F": float(max(r["norm_F"] for r in reps)),
-            "newton_iters_max": int(max(r["newton_iters"] for r in reps)),
-            "total_jvps": int(sum(r["total_jvps"] for r in reps)),
-            "not_converged": [{"member": i, "grid": list(members[i][0]), "re": members[i][1],
-                               "norm_F": reps[i]["norm_F"]} for i in range(len(reps)) if not conv[i]]}
-        grp.close()
+    grp = sp.Group([sp.Config(*g, lx=LX, lz=LZ, re=re, dt=DT, prec=sp.SP_MIXED, lam_adv=1) for g, re in members])
+    U = grp.zeros()
+    for i, m in enumerate(grp.members):
+        a, b, c = si.couette_random_coeffs(3001 + i, m.cfg.nx, m.cfg.ny, m.cfg.nz)
+        m.sp_seed_state(*[torch.from_numpy(x).cuda() for x in (a, b, c)], 0.1, grp.member_view(U, i))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ok, reps = grp.sp_group_newton_gmres(U, max_newton=60, max_krylov=300, tol=1e-10, eta=1e-3, use_graphs=True)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    conv = [r["norm_F"] < 1e-10 for r in reps]
+    out["runs"]["config2_64_members_lam_adv_K300_N60"] = {
+        "wall_s": wall, "converged": int(sum(conv)), "members": len(reps),
+        "newton_iters_max": int(max(r["newton_iters"] for r in reps)),
+        "total_jvps": int(sum(r["total_jvps"] for r in reps)),
+        "not_converged": [{"member": i, "grid": list(members[i][0]), "re": members[i][1],
+                           "norm_F": reps[i]["norm_F"], "delta": reps[i]["delta"], "lin_rel": reps[i]["lin_rel"],
+                           "newton_len": reps[i]["newton_len"]} for i in range(len(reps)) if not conv[i]]}
+    grp.close()
+    # config 3: pipe, Hagen-Poiseuille plus seeded streaks, the speed c an unknown
+    ctx = sp.Context(sp.PipeConfig(prec=sp.SP_MIXED, max_batch=1))
+    st, pol = si.pipe_random_coeffs(4000, ctx.cfg.kz, ctx.cfg.mt)
+    U = ctx.zeros()
+    ctx.sp_pipe_seed_state(st, pol, 0.05, 0.1, 0.5, U)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep = ctx.sp_newton_gmres(U, max_newton=20, max_krylov=300, tol=1e-10, eta=1e-3)
+    torch.cuda.synchronize()
+    r = {k: rep[k] for k in keep if k in rep}
+    r["wall_s"] = time.perf_counter() - t0
+    u, c = ctx.pipe_split(U)
+    r.update({"speed_c": c, "deviation_norm": float(torch.linalg.vector_norm(u)), "seed": 4000})
+    out["runs"]["config3_pipe_re2500"] = r
+    ctx.close()
+    # config 4: the Stokes step with the gradient direction (K-limited at Re 1000), then laminar
+    # advection in L with a longer Newton budget
+    lx4, lz4 = 4 * math.pi / 1.14, 4 * math.pi / 2.5
+    single("config4_96x97x96_re1000_gradient_K300", (96, 97, 96), 1000.0, 6000, lx=lx4, lz=lz4, krylov=300,
+           max_newton=20, use_gradient=True)
+    single("config4_96x97x96_re1000_lam_adv_K300", (96, 97, 96), 1000.0, 6000, lx=lx4, lz=lz4, lam_adv=1,
+           krylov=300, max_newton=60)
     print(json.dumps(out))
 
 

@@ -348,6 +348,8 @@ typedef struct {
   double delta;       /* trust-region radius at exit                         */
   double lin_rel;     /* relative residual |F - J X| / |F| of the last linear
                          solve (GMRES; -1 for the short recurrences)          */
+  double newton_len;  /* length |X| of the last unconstrained Newton step
+                         (before the trust region cuts it)                   */
 } sp_newton_report;
 
 /* Newton-GMRES with hookstep (Sec. 2, Sec. 3.2): U_inout holds the initial

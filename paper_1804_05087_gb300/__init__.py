@@ -62,7 +62,8 @@ class _NewtonReport(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("total_jvps", ctypes.c_int), ("total_steps", ctypes.c_int),
                 ("norm_F", ctypes.c_double), ("norm_F0", ctypes.c_double), ("t_action_ms", ctypes.c_double),
                 ("t_orth_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double), ("spec_jvps", ctypes.c_int),
-                ("hook_trials", ctypes.c_int), ("delta", ctypes.c_double), ("lin_rel", ctypes.c_double)]
+                ("hook_trials", ctypes.c_int), ("delta", ctypes.c_double), ("lin_rel", ctypes.c_double),
+                ("newton_len", ctypes.c_double)]
 
 
 def _load():

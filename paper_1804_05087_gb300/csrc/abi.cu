@@ -90,7 +90,7 @@ static void drop_newton_graphs(sp_ctx* c);
 static void free_ctx(sp_ctx* c) {
   void* ptrs[] = {c->Th, c->TDh, c->Cfh, c->yv, c->lam6, c->Th_f, c->TDh_f, c->Cfh_f, c->twx, c->twz, c->base32t,
                   c->twx_f, c->twz_f, c->ops, c->ws6, c->ws3, c->base64, c->base32, c->U0,
-                  c->G0, c->tmp, c->red, c->kry, c->wsG, c->pops, c->fd_w1, c->fd_c1, c->dzU,
+                  c->G0, c->tmp, c->red, c->kry, c->wsG, c->pb_fac, c->pb_uh, c->pb_dinv, c->fd_w1, c->fd_c1, c->dzU,
                   c->traj, c->nbuf, c->traj_base, c->chain, c->omega, c->Tp, c->TDp, c->tq,
                   c->Tp_f, c->TDp_f, c->tq_f, c->Cq, c->Cq_f, c->yinv_tc_mat};
   for (void* p : ptrs)
@@ -1090,6 +1090,7 @@ static sp_status newton_short(sp_ctx* c, double* U, const sp_newton_opts* o, sp_
     if ((s = k.dot(X, X, &xx)) != SP_OK || (s = k.dot(F, JX, &fj)) != SP_OK || (s = k.dot(JX, JX, &jj)) != SP_OK)
       return s;
     const double nX = std::sqrt(xx);
+    rep->newton_len = nX;
     bool accepted = false;
     double nT = nF;
     for (int trial = 0; trial < 12 && nX > 0 && std::isfinite(nX); ++trial) {
@@ -1428,6 +1429,7 @@ extern "C" sp_status sp_newton_gmres(sp_ctx* c, double* U, const sp_newton_opts*
     r.lin_rel = std::fabs(g[k]) / nF;
     Hookstep hs;
     hs.init(R.data(), LD, k, g.data());
+    r.newton_len = hs.ny0;
     bool accepted = false;
     double nT = nF;
     for (int trial = 0; trial < 12; ++trial) {

@@ -727,7 +727,10 @@ extern "C" sp_status sp_group_newton_gmres(sp_group* g, double* U, const sp_newt
     for (int i = 0; i < n; ++i) {
       if (run[i] && kk[i] > 0) r[i].lin_rel = std::fabs(gv[i][kk[i]]) / nF[i];
       tr[i] = run[i] && kk[i] > 0;
-      if (tr[i]) hs[i].init(R[i].data(), LD, kk[i], gv[i].data());
+      if (tr[i]) {
+        hs[i].init(R[i].data(), LD, kk[i], gv[i].data());
+        r[i].newton_len = hs[i].ny0;
+      }
     }
     for (int trial = 0; trial < 12 && count(tr) > 0; ++trial) {
       std::vector<int> acc(n, 0);

@@ -7,8 +7,8 @@
 //             written plane-major (one radial point per plane).
 //   k_psolve: per Fourier mode, the right-hand side u/dt + N + c du/dz (for the
 //             tangent + dc dU/dz), rotation to u+- = u_r +- i u_theta and
-//             u~_z = -i u_z, the dense per-mode Stokes operator (FP64), and
-//             G = u_new - u with a Hermitian output.
+//             u~_z = -i u_z, the per-mode Stokes problem by banded solves and one
+//             influence coefficient (FP64), and G = u_new - u with a Hermitian output.
 // Index conventions: position pos over the axial wavenumbers in FFT order
 // (k = alpha kz), iz = m' (m = sym m').
 #include "dev_util.h"
@@ -18,15 +18,15 @@ namespace {
 
 constexpr int kTileP = 8;        // modes per k_pvals block
 constexpr int kThreadsP = 256;
-constexpr int kTilePS = 2;       // modes per k_psolve block
-constexpr int kThreadsPS = 256;
 
 struct PArgs {
   const double* r;      // [NR]
   const double* w1;     // [2][NR][9]
   const int* c1;        // [2][NR][9]
-  const double* pops;   // [n_unique][3NR][3NR], column-major
-  size_t pop_stride;
+  const unsigned char* pb_fac;  // banded factors of the per-mode radial problems (plan_pipe.cpp)
+  size_t pb_chunk;
+  const double* pb_uh;  // [n_unique][3][NR]
+  const double* pb_dinv;
   size_t sstride;       // complex values per state (field + speed)
   int Mm, MX, MZ, Kx, NR, n_unique;
   double alpha, sym, inv_dt;
@@ -114,19 +114,154 @@ __device__ __forceinline__ double2 sym_load(const double2* s, int c, int pos, in
   return v;
 }
 
-// in3: [dir][3][NR][Mm] values of N (T); u: the states (step: the state itself,
-// tangent: the directions); U0: the base state (tangent only); out: states.
-template <typename T, bool TANGENT>
-__global__ void __launch_bounds__(kThreadsPS) k_psolve(const C2<T>* __restrict__ in3, const double2* __restrict__ u,
-                                                       const double2* __restrict__ U0, double2* __restrict__ out,
-                                                       PArgs a) {
+// Banded solve of one real right-hand side in place (b: every second double, the real or the
+// imaginary part of a complex vector in shared memory), with one matrix's factors from
+// plan_pipe.cpp staged in shared memory: row interchanges and multipliers forward, then the upper
+// band backward (two partial sums per row). NR > 0: the vector is held in registers and the loops
+// are unrolled (the row interchange of step k is a select among rows k .. k + KL); NR = 0: any
+// size, the vector stays in shared memory.
+// (the unrolled form is one out-of-line function shared by every kernel that uses it)
+template <int NR>
+__device__ __noinline__ void band_solve_reg(double* b, const unsigned char* fac) {
+  constexpr int KL = kPipeKL, KW = kPipeKW;
+  const double* U = reinterpret_cast<const double*>(fac);
+  const double* L = U + (size_t)NR * KW;
+  const int* piv = reinterpret_cast<const int*>(L + (size_t)NR * KL);
+  {
+    double x[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) x[i] = b[2 * i];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      const int p = piv[k];
+      double xk = x[k];
+#pragma unroll
+      for (int q = 1; q <= KL; ++q) {
+        if (k + q < NR) {
+          const bool sw = p == k + q;
+          const double t = x[k + q];
+          x[k + q] = sw ? x[k] : t;
+          xk = sw ? t : xk;
+        }
+      }
+      x[k] = xk;
+#pragma unroll
+      for (int q = 0; q < KL; ++q)
+        if (k + 1 + q < NR) x[k + 1 + q] = fma(-L[k * KL + q], xk, x[k + 1 + q]);
+    }
+#pragma unroll
+    for (int i = NR - 1; i >= 0; --i) {
+      double s0 = x[i], s1 = 0.0;
+#pragma unroll
+      for (int q = 1; q < KW; ++q) {
+        if (i + q < NR) {
+          if (q & 1) s1 = fma(-U[i * KW + q], x[i + q], s1);
+          else s0 = fma(-U[i * KW + q], x[i + q], s0);
+        }
+      }
+      x[i] = (s0 + s1) * U[i * KW];
+    }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) b[2 * i] = x[i];
+  }
+}
+
+template <int NR>
+__device__ __forceinline__ void band_solve_d(double* b, const unsigned char* fac, int n) {
+  constexpr int KL = kPipeKL, KW = kPipeKW;
+  const double* U = reinterpret_cast<const double*>(fac);
+  const double* L = U + (size_t)n * KW;
+  const int* piv = reinterpret_cast<const int*>(L + (size_t)n * KL);
+  if constexpr (NR > 0) {
+    band_solve_reg<NR>(b, fac);
+  } else {
+    for (int k = 0; k < n; ++k) {
+      const int p = piv[k];
+      double bk = b[2 * k];
+      if (p != k) {
+        const double t = b[2 * p];
+        b[2 * p] = bk;
+        bk = t;
+        b[2 * k] = bk;
+      }
+#pragma unroll
+      for (int q = 0; q < KL; ++q)
+        if (k + 1 + q < n) b[2 * (k + 1 + q)] -= L[k * KL + q] * bk;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double s0 = b[2 * i], s1 = 0.0;
+#pragma unroll
+      for (int q = 1; q < KW; ++q) {
+        if (i + q < n) {
+          if (q & 1) s1 = fma(-U[i * KW + q], b[2 * (i + q)], s1);
+          else s0 = fma(-U[i * KW + q], b[2 * (i + q)], s0);
+        }
+      }
+      b[2 * i] = (s0 + s1) * U[i * KW];
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// bounded wait on an mbarrier phase; false if the limit ran out
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Shared-memory vectors are NRP >= NR entries apart, NRP = 1 mod 8: the 16 vectors that the 32 lanes
+// of a warp walk through (two lanes, real and imaginary part, per vector) then start 4 banks apart
+// and a warp's 8-byte accesses take the minimum two wavefronts.
+__host__ __device__ __forceinline__ int psolve_nrp(int NR) { return NR + ((9 - (NR & 7)) & 7); }
+
+// threads per block: at least two warps for the parallel phases, one per serial solve
+__host__ __device__ constexpr int psolve_threads(int TM, int ND) {
+  return 6 * TM * ND <= 64 ? 64 : (6 * TM * ND + 31) / 32 * 32;
+}
+
+__host__ __device__ __forceinline__ size_t psolve_smem(int TM, int ND, int NR, size_t chunk) {
+  return (size_t)TM * 4 * chunk + (size_t)TM * ND * 4 * psolve_nrp(NR) * 16 + (size_t)2 * NR * 9 * (8 + 4);
+}
+
+// in3: [dir][3][NR][Mm] values of N (T); u: the states (step: the state itself, tangent: the
+// directions); U0: the base state (tangent only); out: states. One block: TM modes of ND directions.
+// Per mode the Stokes problem is solved by banded solves (plan_pipe.cpp): the pressure p_f (Poisson,
+// wall value zero), the three velocity components driven by f - grad p_f, and the influence
+// coefficient a of the precomputed u_h from the wall continuity row. The stencil work (div_h f,
+// grad p) runs over all threads, row by row in parallel; only the banded substitutions are serial,
+// one thread per (mode, direction, component, real/imaginary part). The TM modes' factors (4
+// matrices each) come into shared memory by bulk TMA copies while the right-hand sides are formed;
+// their wait has an iteration limit, past which the block writes NaN into its outputs.
+template <typename T, bool TANGENT, int TM, int ND, int NRT>
+__global__ void __launch_bounds__(psolve_threads(TM, ND)) k_psolve(const C2<T>* __restrict__ in3,
+                                                                   const double2* __restrict__ u,
+                                                                   const double2* __restrict__ U0,
+                                                                   double2* __restrict__ out, PArgs a, int n_dir) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int TM = kTilePS, NR = a.NR, Mm = a.Mm, n3 = 3 * NR;
-  double2* su = reinterpret_cast<double2*>(smem_raw);  // [TM][3NR] projected input u
-  double2* sf = su + TM * n3;                          // [TM][3NR] (f+, f-, f~z)
-  double2* sx = sf + TM * n3;                          // [TM][3NR] (u+, u-, u~z)
-  __shared__ int s_pos[kTilePS], s_iz[kTilePS], s_u[kTilePS];
-  const int u0 = blockIdx.x * TM, dir = blockIdx.y;
+  const int NR = NRT > 0 ? NRT : a.NR, Mm = a.Mm, NRP = psolve_nrp(NR), n3 = 3 * NRP;
+  const size_t chunk = a.pb_chunk;
+  unsigned char* sfac = smem_raw;                                             // [TM][4][chunk]
+  double2* sf = reinterpret_cast<double2*>(smem_raw + (size_t)TM * 4 * chunk);  // [TM ND][3][NRP]
+  double2* sp = sf + TM * ND * n3;                                            // [TM ND][NRP] pressure
+  double* sw = reinterpret_cast<double*>(sp + TM * ND * NRP);                 // [2][NR][9] D1 weights
+  int* sc = reinterpret_cast<int*>(sw + 2 * NR * 9);                          // [2][NR][9] their columns
+  __shared__ int s_pos[TM], s_iz[TM], s_u[TM];
+  __shared__ double s_alpha[TM * ND][2];
+  __shared__ __align__(8) uint64_t s_bar;
+  const int u0 = blockIdx.x * TM, d0 = blockIdx.y * ND;
+  const uint32_t bar = smem_addr(&s_bar);
   if (threadIdx.x < TM) {
     const int uu = u0 + threadIdx.x;
     int pos = 0, iz = 0;
@@ -135,81 +270,204 @@ __global__ void __launch_bounds__(kThreadsPS) k_psolve(const C2<T>* __restrict__
     s_iz[threadIdx.x] = iz;
     s_u[threadIdx.x] = uu;
   }
-  __syncthreads();
-  const double2* us = u + (size_t)dir * a.sstride;
-  const C2<T>* vin = in3 + (size_t)dir * 3 * NR * Mm;
-  // speed terms: step c du/dz; tangent c0 du/dz + dc dU0/dz
-  double c_eff, dc = 0.0;
-  if (TANGENT) {
-    c_eff = __ldg(U0 + a.sstride - 1).x;
-    dc = __ldg(us + a.sstride - 1).x;
-  } else {
-    c_eff = __ldg(us + a.sstride - 1).x;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int idx = threadIdx.x; idx < TM * n3; idx += blockDim.x) {
-    const int t = idx / n3, rem = idx - t * n3, c = rem / NR, j = rem - c * NR;
-    if (s_u[t] >= a.n_unique) continue;
+  __syncthreads();
+  const int nvalid = min(TM, a.n_unique - u0);
+  if (threadIdx.x == 0) {
+    // the factors of the block's modes: one bulk copy per (mode, matrix), contiguous in global memory
+    const uint32_t bytes = (uint32_t)(nvalid * 4 * chunk);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    for (int q = 0; q < nvalid * 4; ++q)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_addr(sfac + (size_t)q * chunk)),
+                   "l"(a.pb_fac + ((size_t)u0 * 4 + q) * chunk), "r"((uint32_t)chunk), "r"(bar)
+                   : "memory");
+  }
+  for (int i = threadIdx.x; i < 2 * NR * 9; i += blockDim.x) {
+    sw[i] = __ldg(a.w1 + i);
+    sc[i] = __ldg(a.c1 + i);
+  }
+  // f = u/dt + N + speed terms, rotated to (f+, f-, f~z) = (f_r + i f_theta, f_r - i f_theta, -i f_z)
+  for (int idx = threadIdx.x; idx < TM * ND * NR; idx += blockDim.x) {
+    const int tm = idx / NR, j = idx - tm * NR, t = tm / ND, dir = d0 + tm - t * ND;
+    if (s_u[t] >= a.n_unique || dir >= n_dir) continue;
     const int pos = s_pos[t], iz = s_iz[t];
-    const double2 v = sym_load(us, c, pos, iz, j, a);
-    su[idx] = v;
-    const C2<T> nv = vin[((size_t)c * NR + j) * Mm + pos * a.MZ + iz];
     const int kzi = pos <= a.Kx ? pos : pos - a.MX;
     const double k = a.alpha * kzi;
-    double2 f = make_double2(v.x * a.inv_dt + (double)nv.x - c_eff * k * v.y,
-                             v.y * a.inv_dt + (double)nv.y + c_eff * k * v.x);
-    if (TANGENT) {
-      const double2 w = sym_load(U0, c, pos, iz, j, a);
-      f.x -= dc * k * w.y;
-      f.y += dc * k * w.x;
-    }
-    if (pos == 0 && iz == 0) f.y = 0.0;
-    sf[idx] = f;  // (f_r, f_theta, f_z) for now
-  }
-  __syncthreads();
-  // rotate to (f+, f-, f~z) = (f_r + i f_theta, f_r - i f_theta, -i f_z)
-  for (int idx = threadIdx.x; idx < TM * NR; idx += blockDim.x) {
-    const int t = idx / NR, j = idx - t * NR;
-    double2* f = sf + t * n3;
-    const double2 fr = f[j], ft = f[NR + j], fz = f[2 * NR + j];
-    if (s_pos[t] == 0 && s_iz[t] == 0) continue;  // mean mode keeps (f_r, f_theta, f_z)
-    f[j] = make_double2(fr.x - ft.y, fr.y + ft.x);
-    f[NR + j] = make_double2(fr.x + ft.y, fr.y - ft.x);
-    f[2 * NR + j] = make_double2(fz.y, -fz.x);
-  }
-  __syncthreads();
-  // dense per-mode operator (FP64)
-  for (int idx = threadIdx.x; idx < TM * n3; idx += blockDim.x) {
-    const int t = idx / n3, row = idx - t * n3;
-    if (s_u[t] >= a.n_unique) continue;
-    const double* S = a.pops + (size_t)s_u[t] * a.pop_stride;
-    const double2* f = sf + t * n3;
-    double2 acc = make_double2(0.0, 0.0);
-    if (s_pos[t] == 0 && s_iz[t] == 0) {
-      // rows NR..2NR-1: u_theta = H1 f_theta; rows 2NR..3NR-1: u_z = H0 f_z; u_r = 0
-      if (row >= NR) {
-        const int blk = row < 2 * NR ? 0 : 1, i = row - (blk + 1) * NR;
-        // column-major blocks: row i of block blk
-        acc = dot4(S + (size_t)blk * NR * NR + i, NR, f + (blk + 1) * NR, 1, NR);
+    const double2* us = u + (size_t)dir * a.sstride;
+    const C2<T>* vin = in3 + (size_t)dir * 3 * NR * Mm;
+    // speed terms: step c du/dz; tangent c0 du/dz + dc dU0/dz
+    const double c_eff = TANGENT ? __ldg(U0 + a.sstride - 1).x : __ldg(us + a.sstride - 1).x;
+    const double dc = TANGENT ? __ldg(us + a.sstride - 1).x : 0.0;
+    double2 f[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double2 v = sym_load(us, c, pos, iz, j, a);
+      const C2<T> nv = vin[((size_t)c * NR + j) * Mm + pos * a.MZ + iz];
+      f[c] = make_double2(v.x * a.inv_dt + (double)nv.x - c_eff * k * v.y,
+                          v.y * a.inv_dt + (double)nv.y + c_eff * k * v.x);
+      if (TANGENT) {
+        const double2 w = sym_load(U0, c, pos, iz, j, a);
+        f[c].x -= dc * k * w.y;
+        f[c].y += dc * k * w.x;
       }
-    } else {
-      acc = dot4(S + row, n3, f, 1, n3);  // row `row` of the column-major operator
+      if (pos == 0 && iz == 0) f[c].y = 0.0;
     }
-    sx[idx] = acc;
-  }
-  __syncthreads();
-  double2* dst = out + (size_t)dir * a.sstride;
-  for (int idx = threadIdx.x; idx < TM * NR; idx += blockDim.x) {
-    const int t = idx / NR, j = idx - t * NR;
-    if (s_u[t] >= a.n_unique) continue;
-    const int pos = s_pos[t], iz = s_iz[t];
-    const double2* x = sx + t * n3;
-    double2 vr, vt, vz;
-    if (pos == 0 && iz == 0) {
-      vr = make_double2(0.0, 0.0);
-      vt = make_double2(x[NR + j].x, 0.0);
-      vz = make_double2(x[2 * NR + j].x, 0.0);
+    double2* d = sf + tm * n3;
+    if (pos == 0 && iz == 0) {  // the mean mode keeps (f_r, f_theta, f_z)
+      d[j] = f[0];
+      d[NRP + j] = f[1];
+      d[2 * NRP + j] = f[2];
     } else {
-      const double2 up = x[j], um = x[NR + j], uzt = x[2 * NR + j];
+      d[j] = make_double2(f[0].x - f[1].y, f[0].y + f[1].x);
+      d[NRP + j] = make_double2(f[0].x + f[1].y, f[0].y - f[1].x);
+      d[2 * NRP + j] = make_double2(f[2].y, -f[2].x);
+    }
+  }
+  bool ok = mbar_wait_bounded(bar, 0);
+  if (!ok) (void)mbar_wait_bounded(bar, 0);  // copies still in flight: a second limit before going on
+  ok = __syncthreads_and(ok) != 0;            // the same decision in every thread of the block
+  if (ok) {
+    // pressure right-hand side: div_h f on the inner rows, wall value 0 (all rows in parallel)
+    for (int idx = threadIdx.x; idx < TM * ND * NR; idx += blockDim.x) {
+      const int tm = idx / NR, i = idx - tm * NR, t = tm / ND, dir = d0 + tm - t * ND;
+      const int pos = s_pos[t], iz = s_iz[t];
+      double2 g = make_double2(0.0, 0.0);
+      if (s_u[t] < a.n_unique && dir < n_dir && !(pos == 0 && iz == 0) && i > 0) {
+        const int kzi = pos <= a.Kx ? pos : pos - a.MX;
+        const double k = a.alpha * kzi, mm = a.sym * iz;
+        const int pe = (((int)mm) + 1) & 1;
+        const double2* fp = sf + tm * n3;
+        const double2* fm = fp + NRP;
+        const double2* fz = fp + 2 * NRP;
+        double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          const int col = sc[(pe * NR + i) * 9 + q];
+          const double w = sw[(pe * NR + i) * 9 + q];
+          acc.x = fma(w, fp[col].x + fm[col].x, acc.x);
+          acc.y = fma(w, fp[col].y + fm[col].y, acc.y);
+        }
+        const double ir = 1.0 / __ldg(a.r + i);
+        g.x = 0.5 * acc.x + 0.5 * ir * ((1.0 + mm) * fp[i].x + (1.0 - mm) * fm[i].x) - k * fz[i].x;
+        g.y = 0.5 * acc.y + 0.5 * ir * ((1.0 + mm) * fp[i].y + (1.0 - mm) * fm[i].y) - k * fz[i].y;
+      }
+      sp[tm * NRP + i] = g;
+    }
+    __syncthreads();
+    // serial tasks go round-robin over the warps (task = lane * warps + warp), so that every warp
+    // of the block, on its own scheduler, runs some of the chains
+    constexpr int kWarps = psolve_threads(TM, ND) / 32;
+    const int task = (threadIdx.x & 31) * kWarps + (threadIdx.x >> 5);
+    // pressure solve: one task per (mode, direction, part)
+    if (task < 2 * TM * ND) {
+      const int tm = task >> 1, part = task & 1, t = tm / ND, dir = d0 + tm - t * ND;
+      if (s_u[t] < a.n_unique && dir < n_dir && !(s_pos[t] == 0 && s_iz[t] == 0))
+        band_solve_d<NRT>(reinterpret_cast<double*>(sp + tm * NRP) + part, sfac + (size_t)t * 4 * chunk, NR);
+    }
+    __syncthreads();
+    // velocity right-hand sides f - grad p on the inner rows, no slip at the wall (parallel)
+    for (int idx = threadIdx.x; idx < TM * ND * 3 * NR; idx += blockDim.x) {
+      const int tm = idx / (3 * NR), rem = idx - tm * 3 * NR, comp = rem / NR, i = rem - comp * NR;
+      const int t = tm / ND, dir = d0 + tm - t * ND;
+      if (s_u[t] >= a.n_unique || dir >= n_dir) continue;
+      const int pos = s_pos[t], iz = s_iz[t];
+      double2& x = sf[tm * n3 + comp * NRP + i];
+      if (pos == 0 && iz == 0) {  // mean flow: u_r = 0, wall rows zero
+        if (comp == 0 || i == 0) x = make_double2(0.0, 0.0);
+        continue;
+      }
+      if (i == 0) {
+        x = make_double2(0.0, 0.0);
+        continue;
+      }
+      const int kzi = pos <= a.Kx ? pos : pos - a.MX;
+      const double k = a.alpha * kzi, mm = a.sym * iz;
+      const double2* p = sp + tm * NRP;
+      double2 gp;
+      if (comp == 2) {
+        gp = make_double2(k * p[i].x, k * p[i].y);
+      } else {
+        const int pz = ((int)mm) & 1;
+        double2 d1 = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          const int col = sc[(pz * NR + i) * 9 + q];
+          const double w = sw[(pz * NR + i) * 9 + q];
+          d1.x = fma(w, p[col].x, d1.x);
+          d1.y = fma(w, p[col].y, d1.y);
+        }
+        const double mr = mm / __ldg(a.r + i);
+        gp = comp == 0 ? make_double2(d1.x - mr * p[i].x, d1.y - mr * p[i].y)
+                       : make_double2(d1.x + mr * p[i].x, d1.y + mr * p[i].y);
+      }
+      x.x -= gp.x;
+      x.y -= gp.y;
+    }
+    __syncthreads();
+    // velocity solves: one task per (mode, direction, component, part)
+    if (task < 6 * TM * ND) {
+      const int tm = task / 6, rem = task - 6 * tm, comp = rem >> 1, part = rem & 1;
+      const int t = tm / ND, dir = d0 + tm - t * ND;
+      const bool mean = s_pos[t] == 0 && s_iz[t] == 0;
+      if (s_u[t] < a.n_unique && dir < n_dir && !(mean && comp == 0)) {
+        const int slot = mean ? comp : comp + 1;
+        band_solve_d<NRT>(reinterpret_cast<double*>(sf + tm * n3 + comp * NRP) + part,
+                          sfac + ((size_t)t * 4 + slot) * chunk, NR);
+      }
+    }
+    __syncthreads();
+    // influence coefficient from the wall continuity row: 0.5 D1 (u+ + u-) at r = 1 vanishes
+    if (threadIdx.x < 2 * TM * ND) {
+      const int tm = threadIdx.x >> 1, part = threadIdx.x & 1, t = tm / ND;
+      const int uu = s_u[t], pos = s_pos[t], iz = s_iz[t];
+      double al = 0.0;
+      if (uu < a.n_unique && !(pos == 0 && iz == 0)) {
+        const int pe = (((int)(a.sym * iz)) + 1) & 1;
+        const double* up = reinterpret_cast<const double*>(sf + tm * n3) + part;
+        const double* um = up + 2 * NRP;
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          const int col = sc[pe * NR * 9 + q];
+          s += sw[pe * NR * 9 + q] * (up[2 * col] + um[2 * col]);
+        }
+        al = -0.5 * s * __ldg(a.pb_dinv + uu);
+      }
+      s_alpha[tm][part] = al;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < TM * ND * 3 * NR; idx += blockDim.x) {
+      const int tm = idx / (3 * NR), rem = idx - tm * 3 * NR, comp = rem / NR, j = rem - comp * NR;
+      const int t = tm / ND, uu = s_u[t];
+      if (uu >= a.n_unique || (s_pos[t] == 0 && s_iz[t] == 0)) continue;
+      const double h = __ldg(a.pb_uh + (size_t)uu * 3 * NR + rem);
+      double2& x = sf[tm * n3 + comp * NRP + j];
+      x.x += s_alpha[tm][0] * h;
+      x.y += s_alpha[tm][1] * h;
+    }
+    __syncthreads();
+  }
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  for (int idx = threadIdx.x; idx < TM * ND * NR; idx += blockDim.x) {
+    const int tm = idx / NR, j = idx - tm * NR, t = tm / ND, dir = d0 + tm - t * ND;
+    if (s_u[t] >= a.n_unique || dir >= n_dir) continue;
+    const int pos = s_pos[t], iz = s_iz[t];
+    const double2* us = u + (size_t)dir * a.sstride;
+    double2* dst = out + (size_t)dir * a.sstride;
+    const double2* x = sf + tm * n3;
+    double2 vr, vt, vz;
+    if (!ok) {
+      vr = vt = vz = make_double2(nan, nan);
+    } else if (pos == 0 && iz == 0) {
+      vr = make_double2(0.0, 0.0);
+      vt = make_double2(x[NRP + j].x, 0.0);
+      vz = make_double2(x[2 * NRP + j].x, 0.0);
+    } else {
+      const double2 up = x[j], um = x[NRP + j], uzt = x[2 * NRP + j];
       vr = make_double2(0.5 * (up.x + um.x), 0.5 * (up.y + um.y));
       vt = make_double2(0.5 * (up.y - um.y), -0.5 * (up.x - um.x));  // (u+ - u-)/(2i)
       vz = make_double2(-uzt.y, uzt.x);                                // i u~z
@@ -217,7 +475,7 @@ __global__ void __launch_bounds__(kThreadsPS) k_psolve(const C2<T>* __restrict__
     const double2 res[3] = {vr, vt, vz};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const double2 d = su[t * n3 + c * NR + j];
+      const double2 d = sym_load(us, c, pos, iz, j, a);
       double2 g = make_double2(res[c].x - d.x, res[c].y - d.y);
       if (pos == 0 && iz == 0) g.y = 0.0;
       dst[((size_t)c * Mm + pos * a.MZ + iz) * NR + j] = g;
@@ -226,7 +484,8 @@ __global__ void __launch_bounds__(kThreadsPS) k_psolve(const C2<T>* __restrict__
   }
   // the speed slot of a step is zero (no equation of its own); the tangent's
   // phase condition is written afterwards
-  if (blockIdx.x == 0 && threadIdx.x == 0) dst[a.sstride - 1] = make_double2(0.0, 0.0);
+  if (blockIdx.x == 0 && threadIdx.x < ND && d0 + (int)threadIdx.x < n_dir)
+    out[(size_t)(d0 + threadIdx.x) * a.sstride + a.sstride - 1] = make_double2(0.0, 0.0);
 }
 
 // dzU = i k P(U) (P: Hermitian projection), speed slot zero
@@ -308,8 +567,10 @@ PArgs pargs(const sp_ctx* c) {
   a.r = c->yv;
   a.w1 = c->fd_w1;
   a.c1 = c->fd_c1;
-  a.pops = c->pops;
-  a.pop_stride = c->pop_stride;
+  a.pb_fac = c->pb_fac;
+  a.pb_chunk = c->pb_chunk;
+  a.pb_uh = c->pb_uh;
+  a.pb_dinv = c->pb_dinv;
   a.sstride = c->cplx_per_state;
   a.Mm = c->Mm; a.MX = c->MX; a.MZ = c->MZ; a.Kx = c->Kx; a.NR = c->NY; a.n_unique = c->n_unique;
   a.alpha = c->alpha; a.sym = c->beta; a.inv_dt = 1.0 / c->dt;
@@ -334,28 +595,46 @@ cudaError_t launch_pvals(const sp_ctx* c, bool fp32, const double* in, void* out
   return cudaGetLastError();
 }
 
+template <typename T, bool TG, int TM, int ND, int NRT>
+static cudaError_t psolve_t(const sp_ctx* c, const PArgs& a, const void* in3, const double2* uu, const double2* U0,
+                            double2* o, int n_dir, cudaStream_t st) {
+  const size_t sm = psolve_smem(TM, ND, c->NY, c->pb_chunk);
+  auto kern = k_psolve<T, TG, TM, ND, NRT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((c->n_unique + TM - 1) / TM, (n_dir + ND - 1) / ND);
+  kern<<<grid, psolve_threads(TM, ND), sm, st>>>(reinterpret_cast<const C2<T>*>(in3), uu, U0, o, a, n_dir);
+  return cudaGetLastError();
+}
+
+// The radial size of the pipe workload (Nr = 64) has register-resident solves; other sizes use
+// the shared-memory solve. The widest block whose staged factors and vectors fit is taken.
+template <typename T, bool TG>
+static cudaError_t psolve_tm(const sp_ctx* c, const PArgs& a, const void* in3, const double2* uu, const double2* U0,
+                             double2* o, int n_dir, cudaStream_t st) {
+  constexpr size_t kMax = 225 * 1024;
+  auto fits = [&](int tm, int nd) { return psolve_smem(tm, nd, c->NY, c->pb_chunk) <= kMax; };
+  const bool wide = n_dir >= 8 && fits(2, 8);
+  if (c->NY == 64) {
+    return wide ? psolve_t<T, TG, 2, 8, 64>(c, a, in3, uu, U0, o, n_dir, st)
+                : psolve_t<T, TG, 2, 1, 64>(c, a, in3, uu, U0, o, n_dir, st);
+  }
+  if (wide) return psolve_t<T, TG, 2, 8, 0>(c, a, in3, uu, U0, o, n_dir, st);
+  if (fits(2, 1)) return psolve_t<T, TG, 2, 1, 0>(c, a, in3, uu, U0, o, n_dir, st);
+  if (fits(1, 1)) return psolve_t<T, TG, 1, 1, 0>(c, a, in3, uu, U0, o, n_dir, st);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_psolve(const sp_ctx* c, bool fp32, bool tangent, const void* in3, const double* u, double* out,
                           int n_dir, cudaStream_t st) {
   PArgs a = pargs(c);
-  dim3 grid((c->n_unique + kTilePS - 1) / kTilePS, n_dir);
-  const size_t sm = (size_t)3 * kTilePS * 3 * c->NY * sizeof(double2);
   const double2* uu = reinterpret_cast<const double2*>(u);
   const double2* U0 = reinterpret_cast<const double2*>(c->U0);
   double2* o = reinterpret_cast<double2*>(out);
-#define SP_PSOLVE(T, TG)                                                                                     \
-  do {                                                                                                       \
-    cudaFuncSetAttribute(k_psolve<T, TG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);              \
-    k_psolve<T, TG><<<grid, kThreadsPS, sm, st>>>(reinterpret_cast<const C2<T>*>(in3), uu, U0, o, a);        \
-  } while (0)
-  if (fp32) {
-    if (tangent) SP_PSOLVE(float, true);
-    else SP_PSOLVE(float, false);
-  } else {
-    if (tangent) SP_PSOLVE(double, true);
-    else SP_PSOLVE(double, false);
-  }
-#undef SP_PSOLVE
-  return cudaGetLastError();
+  if (fp32) return tangent ? psolve_tm<float, true>(c, a, in3, uu, U0, o, n_dir, st)
+                           : psolve_tm<float, false>(c, a, in3, uu, U0, o, n_dir, st);
+  return tangent ? psolve_tm<double, true>(c, a, in3, uu, U0, o, n_dir, st)
+                 : psolve_tm<double, false>(c, a, in3, uu, U0, o, n_dir, st);
 }
 
 cudaError_t launch_pipe_dz(const sp_ctx* c, const double* U, double* dzU, cudaStream_t st) {

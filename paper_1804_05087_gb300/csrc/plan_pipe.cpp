@@ -19,13 +19,19 @@
 //   div_h u = 0                                        wall
 // with L_q = D2 + D1/r - q^2/r^2 - k^2 and
 // div_h u = (1/2)[(D1 + (1+m)/r) u+ + (D1 + (1-m)/r) u-] - k u~_z.
-// The operator stored per mode maps (f+, f-, f~_z) at all radial points to
-// (u+, u-, u~_z): a dense real 3Nr x 3Nr matrix (stored column-major), the
-// restriction of the inverse of the 4Nr x 4Nr system composed with its
-// right-hand-side map.
+// The system is solved by banded solves and one influence coefficient (the
+// pressure boundary value that the Poisson rows leave free):
+//   p = p_f + a p_h, with L_m p_f = div_h f inside, p_f(1) = 0, and L_m p_h = 0
+//   inside, p_h(1) = 1; u = u_f + a u_h, with u_f the Helmholtz solutions driven by
+//   f - grad p_f and u_h (precomputed) those driven by -grad p_h; a from the wall
+//   continuity row div_h u(1) = 0. Every row of the 4Nr system then holds, so this is
+//   its solution. Per mode the plan stores the banded LU factors (partial pivoting) of
+//   the four Nr x Nr matrices (Poisson for p, Helmholtz for u+, u-, u~_z), u_h and
+//   1 / div_h u_h(1).
 // Mode (0,0): u_r = 0 and two Helmholtz problems (u_theta with L_1, u_z with L_0).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <numeric>
 #include <thread>
 
@@ -59,42 +65,59 @@ void fornberg(double x0, const double* x, int n, int mmax, std::vector<double>& 
   }
 }
 
-bool lu_factor(std::vector<double>& A, int n, std::vector<int>& piv) {
-  piv.resize(n);
+// Banded LU with partial pivoting of a dense n x n matrix A (row-major) whose nonzeros lie within kl
+// sub-diagonals and ku super-diagonals. Row k is exchanged with the row of largest |A[i][k]|,
+// k <= i <= k + kl; after the exchanges the upper factor has kl + ku super-diagonals. Stored as the
+// interchanges piv[k], the multipliers L[k][q] of rows k + 1 + q, and the rows of the upper factor
+// U[i][q] = U(i, i + q), with U[i][0] replaced by its reciprocal. Forward and back substitution in
+// band_solve (here) and k_psolve (pipe.cu) apply them in the same order.
+struct Band {
+  std::vector<int> piv;
+  std::vector<double> L, U;
+};
+
+bool band_factor(std::vector<double> A, int n, int kl, int kw, Band& B) {
+  B.piv.assign(n, 0);
+  B.L.assign((size_t)n * kl, 0.0);
+  B.U.assign((size_t)n * kw, 0.0);
   for (int k = 0; k < n; ++k) {
+    const int last = std::min(n - 1, k + kl);
     int p = k;
     double best = std::fabs(A[(size_t)k * n + k]);
-    for (int i = k + 1; i < n; ++i) {
+    for (int i = k + 1; i <= last; ++i) {
       const double v = std::fabs(A[(size_t)i * n + k]);
       if (v > best) { best = v; p = i; }
     }
     if (best == 0.0) return false;
-    piv[k] = p;
+    B.piv[k] = p;
     if (p != k)
-      for (int j = 0; j < n; ++j) std::swap(A[(size_t)k * n + j], A[(size_t)p * n + j]);
-    const double inv = 1.0 / A[(size_t)k * n + k];
-    for (int i = k + 1; i < n; ++i) {
-      const double l = A[(size_t)i * n + k] * inv;
-      A[(size_t)i * n + k] = l;
+      for (int j = k; j < n; ++j) std::swap(A[(size_t)k * n + j], A[(size_t)p * n + j]);
+    const double d = A[(size_t)k * n + k];
+    for (int i = k + 1; i <= last; ++i) {
+      const double l = A[(size_t)i * n + k] / d;
+      B.L[(size_t)k * kl + (i - k - 1)] = l;
       if (l != 0.0)
-        for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
+        for (int j = k + 1; j < std::min(n, k + kw); ++j) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
     }
+    B.U[(size_t)k * kw] = 1.0 / d;
+    for (int q = 1; q < kw && k + q < n; ++q) B.U[(size_t)k * kw + q] = A[(size_t)k * n + k + q];
+    for (int j = k + kw; j < n; ++j)
+      if (A[(size_t)k * n + j] != 0.0) return false;  // outside the assumed band
   }
   return true;
 }
 
-void lu_solve(const std::vector<double>& LU, int n, const std::vector<int>& piv, double* b) {
-  for (int k = 0; k < n; ++k)
-    if (piv[k] != k) std::swap(b[k], b[piv[k]]);
-  for (int i = 0; i < n; ++i) {
-    double s = b[i];
-    for (int j = 0; j < i; ++j) s -= LU[(size_t)i * n + j] * b[j];
-    b[i] = s;
+void band_solve(const Band& B, int n, int kl, int kw, double* b) {
+  for (int k = 0; k < n; ++k) {
+    const int p = B.piv[k];
+    if (p != k) std::swap(b[k], b[p]);
+    const double bk = b[k];
+    for (int q = 0; q < kl && k + 1 + q < n; ++q) b[k + 1 + q] -= B.L[(size_t)k * kl + q] * bk;
   }
   for (int i = n - 1; i >= 0; --i) {
     double s = b[i];
-    for (int j = i + 1; j < n; ++j) s -= LU[(size_t)i * n + j] * b[j];
-    b[i] = s / LU[(size_t)i * n + i];
+    for (int q = 1; q < kw && i + q < n; ++q) s -= B.U[(size_t)i * kw + q] * b[i + q];
+    b[i] = s * B.U[(size_t)i * kw];
   }
 }
 
@@ -138,9 +161,23 @@ sp_status sp_build_pipe_plan(sp_ctx* c) {
     }
   }
   const double nu = c->nu, lam = 1.0 / c->dt;
-  const int n3 = 3 * nr, n4 = 4 * nr;
-  c->pop_stride = (size_t)n3 * n3;
-  std::vector<double> ops((size_t)c->n_unique * c->pop_stride, 0.0);
+  // band of the 9-point stencils (both parities): kl below, ku above the diagonal
+  int kl = 0, ku = 0;
+  for (int par = 0; par < 2; ++par)
+    for (int j = 0; j < nr; ++j)
+      for (int q = 0; q < st; ++q) {
+        const int col = c1[((size_t)par * nr + j) * st + q];
+        kl = std::max(kl, j - col);
+        ku = std::max(ku, col - j);
+      }
+  if (kl > kPipeKL || kl + ku + 1 > kPipeKW) return sp_fail(c, SP_EINVAL, "radial stencil band wider than supported");
+  kl = kPipeKL;               // the factors are stored with the fixed widths the kernel is built for
+  const int kw = kPipeKW;     // upper factor after the row interchanges
+  const size_t chunk = (size_t)nr * (kw + kl) * 8 + ((size_t)nr * 4 + 15) / 16 * 16;
+  c->pb_chunk = chunk;
+  const size_t nu4 = (size_t)c->n_unique * 4;
+  std::vector<unsigned char> fac(nu4 * chunk, 0);
+  std::vector<double> uh_all((size_t)c->n_unique * 3 * nr, 0.0), dinv_all(c->n_unique, 0.0);
   auto lapl = [&](int q, int par, double k, std::vector<double>& L) {
     L.assign((size_t)nr * nr, 0.0);
     for (int i = 0; i < nr; ++i) {
@@ -153,95 +190,75 @@ sp_status sp_build_pipe_plan(sp_ctx* c) {
   nthreads = std::max(1, std::min(nthreads, 32));
   std::vector<int> bad(nthreads, 0);
   auto work = [&](int tid) {
-    std::vector<double> L1, L2, L3, A, X;
-    std::vector<int> piv;
+    std::vector<double> Lq, M;
+    Band B[4];
+    auto put = [&](int u, int slot, const Band& b) {
+      unsigned char* o = fac.data() + ((size_t)u * 4 + slot) * chunk;
+      std::memcpy(o, b.U.data(), (size_t)nr * kw * 8);
+      std::memcpy(o + (size_t)nr * kw * 8, b.L.data(), (size_t)nr * kl * 8);
+      std::memcpy(o + (size_t)nr * (kw + kl) * 8, b.piv.data(), (size_t)nr * 4);
+    };
+    // row 0: the wall condition (value 0); rows i >= 1: lam - nu L_q (Helmholtz) or L_q (Poisson)
+    auto build = [&](int q, int par, double k, bool helm, Band& b) -> bool {
+      lapl(q, par, k, Lq);
+      M.assign((size_t)nr * nr, 0.0);
+      M[0] = 1.0;
+      for (int i = 1; i < nr; ++i)
+        for (int j = 0; j < nr; ++j)
+          M[(size_t)i * nr + j] = helm ? (i == j ? lam : 0.0) - nu * Lq[(size_t)i * nr + j] : Lq[(size_t)i * nr + j];
+      return band_factor(M, nr, kl, kw, b);
+    };
+    auto ident = [&](Band& b) {
+      b.piv.resize(nr);
+      std::iota(b.piv.begin(), b.piv.end(), 0);
+      b.L.assign((size_t)nr * kl, 0.0);
+      b.U.assign((size_t)nr * kw, 0.0);
+      for (int i = 0; i < nr; ++i) b.U[(size_t)i * kw] = 1.0;
+    };
     for (int u = tid; u < c->n_unique; u += nthreads) {
       int pos, iz;
       sp_unique_mode(c, u, &pos, &iz);
       const int kzi = pos <= c->Kx ? pos : pos - c->MX;
       const double k = c->alpha * kzi;
       const int m = (int)std::lround(c->beta) * iz;
-      double* out = ops.data() + (size_t)u * c->pop_stride;
       if (pos == 0 && iz == 0) {
-        // mean flow: u_theta (L_1, odd parity) and u_z (L_0, even parity)
-        for (int blk = 0; blk < 2; ++blk) {
-          const int q = blk == 0 ? 1 : 0, par = blk == 0 ? 1 : 0;
-          lapl(q, par, 0.0, L1);
-          A.assign((size_t)nr * nr, 0.0);
-          for (int i = 1; i < nr; ++i)
-            for (int j = 0; j < nr; ++j) A[(size_t)i * nr + j] = (i == j ? lam : 0.0) - nu * L1[(size_t)i * nr + j];
-          A[0] = 1.0;
-          if (!lu_factor(A, nr, piv)) { bad[tid] = 1; continue; }
-          std::vector<double> b(nr);
-          for (int col = 1; col < nr; ++col) {
-            std::fill(b.begin(), b.end(), 0.0);
-            b[col] = 1.0;
-            lu_solve(A, nr, piv, b.data());
-            for (int i = 0; i < nr; ++i) out[(size_t)blk * nr * nr + (size_t)col * nr + i] = b[i];
-          }
-        }
+        // mean flow: u_theta (L_1, odd parity) and u_z (L_0, even parity); no pressure
+        ident(B[0]);
+        ident(B[3]);
+        if (!build(1, 1, 0.0, true, B[1]) || !build(0, 0, 0.0, true, B[2])) { bad[tid] = 1; continue; }
+        for (int s = 0; s < 4; ++s) put(u, s, B[s]);
         continue;
       }
       const int pe = (m + 1) & 1, pz = m & 1;
-      lapl(m + 1, pe, k, L1);
-      lapl(m - 1, pe, k, L2);
-      lapl(m, pz, k, L3);
+      if (!build(m, pz, k, false, B[0]) || !build(m + 1, pe, k, true, B[1]) || !build(m - 1, pe, k, true, B[2]) ||
+          !build(m, pz, k, true, B[3])) {
+        bad[tid] = 1;
+        continue;
+      }
+      for (int s = 0; s < 4; ++s) put(u, s, B[s]);
+      // p_h: interior Laplacian zero, unit wall value; u_h: the velocity it drives
+      std::vector<double> ph(nr, 0.0);
+      ph[0] = 1.0;
+      band_solve(B[0], nr, kl, kw, ph.data());
       const std::vector<double>& Dp = D[pz][0];
       const std::vector<double>& Du = D[pe][0];
-      A.assign((size_t)n4 * n4, 0.0);
-      std::vector<double> B((size_t)n4 * n3, 0.0);
-      auto a = [&](int row, int col) -> double& { return A[(size_t)row * n4 + col]; };
-      auto bb = [&](int row, int col) -> double& { return B[(size_t)row * n3 + col]; };
-      const int U1 = 0, U2 = nr, U3 = 2 * nr, PP = 3 * nr;
-      for (int blk = 0; blk < 3; ++blk) {
-        const std::vector<double>& L = blk == 0 ? L1 : blk == 1 ? L2 : L3;
-        const int base = blk * nr;
-        a(base, base) = 1.0;  // no-slip
+      double* uh = uh_all.data() + (size_t)u * 3 * nr;
+      for (int comp = 0; comp < 3; ++comp) {
+        std::vector<double> b(nr, 0.0);
         for (int i = 1; i < nr; ++i) {
-          for (int j = 0; j < nr; ++j) a(base + i, base + j) = (i == j ? lam : 0.0) - nu * L[(size_t)i * nr + j];
-          if (blk < 2) {
-            for (int j = 0; j < nr; ++j) a(base + i, PP + j) = Dp[(size_t)i * nr + j];
-            a(base + i, PP + i) += (blk == 0 ? -1.0 : 1.0) * m / r[i];
-          } else {
-            a(base + i, PP + i) = k;
-          }
-          bb(base + i, base + i) = 1.0;
+          double g = 0.0;
+          for (int j = 0; j < nr; ++j) g += Dp[(size_t)i * nr + j] * ph[j];
+          const double gp = comp == 0 ? g - m / r[i] * ph[i] : comp == 1 ? g + m / r[i] * ph[i] : k * ph[i];
+          b[i] = -gp;
         }
+        band_solve(B[comp + 1], nr, kl, kw, b.data());
+        std::copy(b.begin(), b.end(), uh + (size_t)comp * nr);
       }
-      // divergence rows: continuity at the wall, Poisson right-hand side inside
-      for (int i = 0; i < nr; ++i) {
-        const int row = PP + i;
-        if (i == 0) {
-          for (int j = 0; j < nr; ++j) {
-            a(row, U1 + j) = 0.5 * Du[j];
-            a(row, U2 + j) = 0.5 * Du[j];
-          }
-          a(row, U1) += 0.5 * (1 + m) / r[0];
-          a(row, U2) += 0.5 * (1 - m) / r[0];
-          a(row, U3) = -k;
-        } else {
-          for (int j = 0; j < nr; ++j) a(row, PP + j) = L3[(size_t)i * nr + j];
-          for (int j = 0; j < nr; ++j) {
-            bb(row, U1 + j) = 0.5 * Du[(size_t)i * nr + j];
-            bb(row, U2 + j) = 0.5 * Du[(size_t)i * nr + j];
-          }
-          bb(row, U1 + i) += 0.5 * (1 + m) / r[i];
-          bb(row, U2 + i) += 0.5 * (1 - m) / r[i];
-          bb(row, U3 + i) = -k;
-        }
-      }
-      if (!lu_factor(A, n4, piv)) { bad[tid] = 1; continue; }
-      std::vector<double> col(n4);
-      for (int cc = 0; cc < n3; ++cc) {
-        bool any = false;
-        for (int i = 0; i < n4; ++i) {
-          col[i] = B[(size_t)i * n3 + cc];
-          any = any || col[i] != 0.0;
-        }
-        if (!any) continue;  // wall entries of f do not enter
-        lu_solve(A, n4, piv, col.data());
-        for (int i = 0; i < n3; ++i) out[(size_t)cc * n3 + i] = col[i];
-      }
+      // wall divergence of u_h (its wall values are zero, so only D1 of u+ + u- remains)
+      double den = 0.0;
+      for (int j = 0; j < nr; ++j) den += 0.5 * Du[j] * (uh[j] + uh[nr + j]);
+      if (den == 0.0 || !std::isfinite(den)) { bad[tid] = 1; continue; }
+      dinv_all[u] = 1.0 / den;
     }
   };
   std::vector<std::thread> th;
@@ -259,7 +276,9 @@ sp_status sp_build_pipe_plan(sp_ctx* c) {
     if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
     return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
   };
-  const bool ok = up((void**)&c->pops, ops.data(), ops.size() * 8) && up((void**)&c->yv, r.data(), r.size() * 8) &&
+  const bool ok = up((void**)&c->pb_fac, fac.data(), fac.size()) &&
+                  up((void**)&c->pb_uh, uh_all.data(), uh_all.size() * 8) &&
+                  up((void**)&c->pb_dinv, dinv_all.data(), dinv_all.size() * 8) && up((void**)&c->yv, r.data(), r.size() * 8) &&
                   up((void**)&c->lam6, lam6.data(), lam6.size() * 8) &&
                   up((void**)&c->fd_w1, w1.data(), w1.size() * 8) && up((void**)&c->fd_c1, c1.data(), c1.size() * 4);
   if (!ok) return sp_fail(c, SP_ENOMEM, "device allocation of the pipe plan failed");

@@ -52,6 +52,12 @@ struct FftPlan {
 // problems with the O(N) chains (one thread per mode, parity and direction)
 constexpr int kChainMinBatch = 32;
 
+// band of the pipe's radial factors: the 9-point stencils reach 6 rows below and 8 above the
+// diagonal (wall rows one-sided, axis rows folded onto their mirror points), and the row
+// interchanges of partial pivoting widen the upper band to 6 + 8
+constexpr int kPipeKL = 6;
+constexpr int kPipeKW = 15;
+
 // ------------------------------------------------------------------ context
 struct sp_ctx {
   sp_config cfg;
@@ -102,8 +108,14 @@ struct sp_ctx {
   double* chain = nullptr;       // [n_unique][2 parities][chain_par]
   double* omega = nullptr;       // [NY][3] right-hand-side weights of the tridiagonal rows
   // pipe: per-mode dense operators (3 NY x 3 NY, column-major), radial FD band (D1) tables
-  double* pops = nullptr;
-  size_t pop_stride = 0;
+  // pipe: banded LU factors of the per-mode radial problems (plan_pipe.cpp), matrices
+  // 0 pressure, 1 u+, 2 u-, 3 u~z (mean mode: 1 u_theta, 2 u_z); one chunk of pb_chunk bytes
+  // per (mode, matrix): U [NR][kPipeKW] (entry 0 = 1 / diagonal), L [NR][kPipeKL] multipliers,
+  // row interchanges [NR] int32, zero-padded to a multiple of 16 bytes
+  unsigned char* pb_fac = nullptr;  // [n_unique][4][pb_chunk]
+  size_t pb_chunk = 0;
+  double* pb_uh = nullptr;    // [n_unique][3][NR] (u+, u-, u~z) driven by the unit wall pressure
+  double* pb_dinv = nullptr;  // [n_unique] 1 / (wall divergence of pb_uh)
   double* fd_w1 = nullptr;       // [2 parities][NY][9] weights of the first derivative
   int* fd_c1 = nullptr;          // [2][NY][9] columns
   double* dzU = nullptr;         // d/dz of the (projected) linearisation point, one state
