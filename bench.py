@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--single-prec", action="store_true", help="time only the --prec precision")
     p.add_argument("--no-newton", action="store_true", help="skip the time-to-converge block")
     p.add_argument("--ndir", type=int, default=256)
+    p.add_argument("--pipe-ndir", type=int, default=64, help="directions per tangent launch of --config3")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--newton", action="store_true",
@@ -837,7 +838,7 @@ def run_config3(args):
     torch.cuda.set_device(0)
     import paper_1804_05087_gb300 as sp
     import seeded_inputs as si
-    nd = 64
+    nd = args.pipe_ndir
     out = {"metric": "config 3: pipe traveling-wave tangent throughput and Newton", "unit": "JVP/s",
            "config": {"workload": "pipe Re=2500, alpha=1.25, sym 2, Nr=64, m'<=12, |kz|<=24, 48x96, dt=50",
                       "directions": nd}, "throughput": {}}
@@ -866,7 +867,7 @@ def run_config3(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         out["throughput"][name] = {"ms_per_step": ms, "jvp_per_s": nd / (ms * 1e-3)}
-        if prec == sp.SP_MIXED:
+        if prec == sp.SP_MIXED and not args.no_newton:
             U0 = U.clone()
             G = ctx.zeros()
             ctx.sp_step(U0, G)
