@@ -361,13 +361,17 @@ static sp_status pipe_phase(sp_ctx* c, const double* du, double* out, int n_dir,
 
 // The tangent's per-mode solve of one pass: the O(N) chains (k_rhs, then k_chain) on
 // contexts built for large batches, else the dense per-mode operators (k_solve).
-sp_status sp_tangent_solve(sp_ctx* c, bool f32, const void* vals, const double* du, double* out, void* work,
-                           int nb, cudaStream_t st) {
-  if (c->use_chain) {
+// bytes of the context's ws3 (max_batch planes of three complex fields)
+static size_t ws3_bytes(const sp_ctx* c) { return (size_t)c->cfg.max_batch * 3 * c->NY * c->Mm * 16; }
+
+sp_status sp_tangent_solve(sp_ctx* c, bool f32, void* vals, size_t vals_bytes, const double* du, double* out,
+                           void* work, int nb, cudaStream_t st) {
+  // the O(N) chains use vals (consumed by their right-hand-side launch) as their scratch
+  if (c->use_chain && chain_scratch_bytes(c, nb) <= vals_bytes) {
     sp_status s = sp_cuda(c, traced(c, SP_STAGE_RHS, st, [&] { return launch_chain_rhs(c, f32, vals, du, work, nb, st); }),
                           "rhs");
     if (s != SP_OK) return s;
-    return sp_cuda(c, traced(c, SP_STAGE_SOLVE, st, [&] { return launch_chain_solve(c, du, out, work, nb, st); }),
+    return sp_cuda(c, traced(c, SP_STAGE_SOLVE, st, [&] { return launch_chain_solve(c, du, out, work, vals, nb, st); }),
                    "chain solve");
   }
   return sp_cuda(c, traced(c, SP_STAGE_SOLVE, st, [&] { return launch_solve(c, f32, vals, du, out, nb, st); }), "solve");
@@ -400,7 +404,7 @@ extern "C" sp_status sp_jvp(sp_ctx* c, const double* du, double* Jdu, int n_dir,
     }
     if ((s = sp_cuda(c, traced(c, SP_STAGE_YINV, st, [&] { return launch_yinv(c, f32, u, c->ws6, nb, st); }), "yinv")) != SP_OK) return s;
     if ((s = sp_cuda(c, traced(c, SP_STAGE_XZ, st, [&] { return launch_xz(c, f32, XZ_TANGENT, c->ws6, c->ws3, nb, st); }), "xz tangent")) != SP_OK) return s;
-    if ((s = sp_tangent_solve(c, f32, c->ws3, u, g, c->ws6, nb, st)) != SP_OK) return s;
+    if ((s = sp_tangent_solve(c, f32, c->ws3, ws3_bytes(c), u, g, c->ws6, nb, st)) != SP_OK) return s;
   }
   return SP_OK;
 }
@@ -674,7 +678,7 @@ extern "C" sp_status sp_jvp_n(sp_ctx* c, const double* du, double* Jdu, int n_di
       if ((s = sp_cuda(c, traced(c, SP_STAGE_XZ, st, [&] { return launch_xz(c, f32, XZ_TANGENT, c->ws6, c->ws3, nb, st); }),
                        "xz tangent")) != SP_OK)
         return s;
-      if ((s = sp_tangent_solve(c, f32, c->ws3, g, c->tmp, c->ws6, nb, st)) != SP_OK) return s;
+      if ((s = sp_tangent_solve(c, f32, c->ws3, ws3_bytes(c), g, c->tmp, c->ws6, nb, st)) != SP_OK) return s;
       if ((s = sp_cuda(c, launch_axpby(g, 1.0, g, 1.0, c->tmp, (size_t)nb * L, st), "axpby")) != SP_OK) return s;
     }
     if ((s = sp_cuda(c, launch_axpby(g, 1.0, g, -1.0, u, (size_t)nb * L, st), "axpby")) != SP_OK) return s;

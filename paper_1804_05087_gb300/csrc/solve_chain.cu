@@ -180,6 +180,7 @@ struct ChainArgs {
   int n_unique, n_dir, dirs_fast;
   int Mm, MX, MZ, Kx, NY, N, NH, par, stride;
   double alpha, beta;
+  double2* S2g;            // second work vector of every thread: entry i of thread t at S2g[i * T + t]
 };
 
 constexpr int kChainWarps = 2;  // threads per block = 32 kChainWarps (warp pairs: parity 0, 1)
@@ -232,9 +233,13 @@ __device__ __forceinline__ double2 tri_sweep(const double* __restrict__ r4, doub
 
 __global__ void __launch_bounds__(32 * kChainWarps) k_chain(ChainArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // two work vectors of NH entries per thread: S1 in shared memory, S2 in global scratch (one thread
+  // per column, consecutive threads adjacent: coalesced, mostly L2-resident). Shared memory per thread
+  // is then one vector, which doubles the warps an SM holds for the dependent sweeps.
   const int st = blockDim.x;
   double2* S1 = reinterpret_cast<double2*>(smem_raw) + threadIdx.x;  // [NH][blockDim]
-  double2* S2 = S1 + (size_t)a.NH * st;
+  const int st2 = gridDim.x * blockDim.x;
+  double2* S2 = a.S2g + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int P = gw & 1, Q = 1 - P;
   const int item = (gw >> 1) * 32 + (threadIdx.x & 31);
@@ -280,13 +285,13 @@ __global__ void __launch_bounds__(32 * kChainWarps) k_chain(ChainArgs a) {
     const double* rP = rec + P * a.par;
     const double gH = rP[10 * NH];
     tri_sweep(rP, gH, om, N, P, [&](int n) { return fval(0, n); }, zero, S1, st);
-    tri_sweep(rP, gH, om, N, P, [&](int n) { return fval(2, n); }, zero, S2, st);
+    tri_sweep(rP, gH, om, N, P, [&](int n) { return fval(2, n); }, zero, S2, st2);
     const int m = (N - P) / 2;
     for (int i = 0; i <= m; ++i) {
       const int n = 2 * i + P;
       put(0, n, csub(S1[i * st], duv(0, n)));
       put(1, n, csub(zero, duv(1, n)));
-      put(2, n, csub(S2[i * st], duv(2, n)));
+      put(2, n, csub(S2[i * st2], duv(2, n)));
     }
     return;
   }
@@ -320,12 +325,12 @@ __global__ void __launch_bounds__(32 * kChainWarps) k_chain(ChainArgs a) {
   const double2 wtop = tri_sweep(rP, rP[10 * NH], om, N, P, gneg, zero, S1, st);
   // (2) v_A: (D^2 - k^2) v = w_A on the rows <= N-2 of parity P, v(+-1) = 0
   const double2 vtop = tri_sweep(rP + 4 * NH, rP[10 * NH + 1], om, N, P,
-                                 [&](int n) { return n <= N - 2 ? S1[((n - P) >> 1) * st] : zero; }, zero, S2, st);
+                                 [&](int n) { return n <= N - 2 ? S1[((n - P) >> 1) * st] : zero; }, zero, S2, st2);
   // (3) influence correction: sigma psi + tau h fixes w_top = -k^2 v_top and Dv(+-1) = 0
   double2 e2 = zero;
   for (int i = 0; i <= m; ++i) {
     const double n = 2.0 * i + P;
-    e2 = caxpy(e2, S2[i * st], n * n);
+    e2 = caxpy(e2, S2[i * st2], n * n);
   }
   const double2 e1 = caxpy(wtop, vtop, k2);
   const double* sc = rP + 10 * NH;
@@ -337,14 +342,14 @@ __global__ void __launch_bounds__(32 * kChainWarps) k_chain(ChainArgs a) {
   double2 Sa = zero;
   for (int i = m; i >= 0; --i) {
     const int n = 2 * i + P;
-    double2 v = S2[i * st];
+    double2 v = S2[i * st2];
     v = caxpy(v, sig, v2[2 * i]);
     v = caxpy(v, tau, v2[2 * i + 1]);
     put(1, n, csub(v, duv(1, n)));
     Sa = caxpy(Sa, v, (double)n);
     if (n >= 1) {
       const double f = (n - 1 == 0 ? 1.0 : 2.0) * ik;  // (i/k)(2/c_{n-1}) Sa
-      S2[i * st] = make_double2(-Sa.y * f, Sa.x * f);
+      S2[i * st2] = make_double2(-Sa.y * f, Sa.x * f);
     }
   }
   // (5) b of parity Q: (lam - nu D^2) b = f_b, b(+-1) = 0; then u = cx a - cz b,
@@ -355,7 +360,7 @@ __global__ void __launch_bounds__(32 * kChainWarps) k_chain(ChainArgs a) {
   for (int i = 0; i <= mq; ++i) {
     const int n = 2 * i + Q;
     const int ia = P == 0 ? i + 1 : i;  // slot of a_n in S2
-    const double2 an = (ia <= m) ? S2[ia * st] : zero;
+    const double2 an = (ia <= m) ? S2[ia * st2] : zero;
     const double2 bn = S1[i * st];
     put(0, n, csub(cmix(an, cx, bn, -cz), duv(0, n)));
     put(2, n, csub(cmix(an, cz, bn, cx), duv(2, n)));
@@ -410,12 +415,21 @@ cudaError_t launch_chain_rhs(const sp_ctx* c, bool fp32, const void* in3, const 
   return cudaGetLastError();
 }
 
-size_t chain_smem(const sp_ctx* c) { return sizeof(double2) * 2 * (size_t)c->NH * 32 * kChainWarps; }
+size_t chain_smem(const sp_ctx* c) { return sizeof(double2) * (size_t)c->NH * 32 * kChainWarps; }
 
-cudaError_t launch_chain_solve(const sp_ctx* c, const double* du, double* out, const void* work, int n_dir,
-                               cudaStream_t st) {
+// global scratch of k_chain for n_dir directions (the second work vector of every thread)
+size_t chain_scratch_bytes(const sp_ctx* c, int n_dir) {
+  const long long items = (long long)c->n_unique * n_dir;
+  const long long warps = 2 * ((items + 31) / 32);
+  const long long blocks = (warps + kChainWarps - 1) / kChainWarps;
+  return sizeof(double2) * (size_t)c->NH * (size_t)(blocks * 32 * kChainWarps);
+}
+
+cudaError_t launch_chain_solve(const sp_ctx* c, const double* du, double* out, const void* work, void* scratch,
+                               int n_dir, cudaStream_t st) {
   if (n_dir <= 0) return cudaSuccess;
   ChainArgs a;
+  a.S2g = static_cast<double2*>(scratch);
   chain_strides(c, n_dir, &a.su, &a.sd, &a.sn);
   a.W = static_cast<const double2*>(work);
   a.du = reinterpret_cast<const double2*>(du);

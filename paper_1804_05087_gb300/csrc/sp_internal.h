@@ -267,14 +267,17 @@ cudaError_t launch_xz_reg64(const sp_ctx* c, int mode, const void* in, void* out
 // launch_solve. chain_smem: dynamic shared memory of k_chain (0 if it does not fit).
 cudaError_t launch_chain_rhs(const sp_ctx* c, bool fp32, const void* in3, const double* du, void* work, int n_dir,
                              cudaStream_t st);
-cudaError_t launch_chain_solve(const sp_ctx* c, const double* du, double* out, const void* work, int n_dir,
-                               cudaStream_t st);
+cudaError_t launch_chain_solve(const sp_ctx* c, const double* du, double* out, const void* work, void* scratch,
+                               int n_dir, cudaStream_t st);
 size_t chain_smem(const sp_ctx* c);
+size_t chain_scratch_bytes(const sp_ctx* c, int n_dir);
 // the tangent's per-mode solve of one pass (abi.cu): chains or dense operators by the
 // context's choice (use_chain); work: scratch of n_unique x 3 x (N-1) complex doubles
-// per direction (the chains' right-hand sides; ws6 suffices)
-sp_status sp_tangent_solve(sp_ctx* c, bool f32, const void* vals, const double* du, double* out, void* work,
-                           int nb, cudaStream_t st);
+// per direction (the chains' right-hand sides; ws6 suffices); vals (vals_bytes long) is
+// read by the right-hand-side launch and then serves as the chains' second scratch
+// (chain_scratch_bytes); if it is too small the dense operators solve instead
+sp_status sp_tangent_solve(sp_ctx* c, bool f32, void* vals, size_t vals_bytes, const double* du, double* out,
+                           void* work, int nb, cudaStream_t st);
 // shape: index into the tile-shape table (sp_solve_shapes); -1 = the context's tangent choice
 cudaError_t launch_solve(const sp_ctx* c, bool fp32, const void* in3, const double* du,
                          double* out, int n_dir, cudaStream_t st, int shape = -1);
