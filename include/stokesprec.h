@@ -301,6 +301,17 @@ sp_status sp_autotune(sp_ctx* ctx, int n_dir, sp_tune_report* report, void* stre
  * memory makes the later call fail with SP_ECUDA. */
 sp_status sp_set_solve_shape(sp_ctx* ctx, int tangent_shape, int step_shape);
 
+/* Choose the tensor-core forms of the mixed tangent's Chebyshev transforms
+ * (Sec. 3.2; tcgen05 MMAs in split TF32, FP32 accumulation): inverse = 1 puts
+ * the inverse transform and curl (values at the Gauss-Lobatto points) on the
+ * tensor cores, forward = 1 the forward transform of the batched O(N) solve's
+ * right-hand sides. They apply to plane Couette contexts in mixed precision
+ * with 41 <= Ny <= 72 (elsewhere the CUDA-core kernels run regardless).
+ * Defaults: inverse 1, forward 0 (the forward one measured slower than its
+ * CUDA-core counterpart). The results agree with the CUDA-core kernels to
+ * float accuracy, not bit for bit. SP_EINVAL for a null context. */
+sp_status sp_set_tensor_cores(sp_ctx* ctx, int inverse, int forward);
+
 /* ---- Newton-GMRES-hookstep ------------------------------------------------ */
 
 typedef struct {

@@ -95,6 +95,7 @@ def _load():
         "sp_trace_enable": ([P, I], I),
         "sp_trace_read": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), I], I),
         "sp_autotune": ([P, I, ctypes.POINTER(_TuneReport), V], I),
+        "sp_set_tensor_cores": ([P, I, I], I),
         "sp_step_n": ([P, P, P, I, V], I),
         "sp_jvp_host": ([P, P, P, I, I, V], I),
         "sp_set_base_n": ([P, P, I, V], I),
@@ -130,7 +131,7 @@ EXPORTS = ("sp_create", "sp_destroy", "sp_last_error", "sp_state_len", "sp_dims"
            "sp_group_state_len", "sp_group_offset", "sp_group_member", "sp_group_step", "sp_group_set_base",
            "sp_group_jvp", "sp_group_inner", "sp_group_newton_gmres", "sp_autotune",
            "sp_set_solve_shape", "sp_step_n", "sp_set_base_n", "sp_jvp_n",
-           "sp_jvp_host", "sp_krylov_solve", "sp_probe_fp64_fma")
+           "sp_jvp_host", "sp_krylov_solve", "sp_probe_fp64_fma", "sp_set_tensor_cores")
 STAGES = ("k_yinv", "k_xz", "k_solve", "step", "vector", "k_rhs")
 
 
@@ -348,6 +349,10 @@ class Context:
         out = (ctypes.c_double * n)()
         self._check(_lib.sp_inner(self._h, pa, pb, n, out, _stream(stream)))
         return list(out)
+
+    def sp_set_tensor_cores(self, inverse=True, forward=False):
+        """Choose the tensor-core forms of the mixed tangent's Chebyshev transforms (see the header)."""
+        self._check(_lib.sp_set_tensor_cores(self._h, int(bool(inverse)), int(bool(forward))))
 
     def sp_autotune(self, n_dir=1, stream=None):
         """Time the solve kernel's tile shapes and keep the fastest (see include/stokesprec.h)."""

@@ -300,6 +300,7 @@ extern "C" sp_status sp_group_create(const sp_config* cfgs, int n, sp_group** ou
     // so that they compute exactly what the group computes for it
     g->mem[i]->use_xz_reg64 = 0;
     g->mem[i]->use_yinv_tc = 0;
+    g->mem[i]->use_rhs_tc = 0;
     g->off[i] = pos;
     pos += (sp_state_len(g->mem[i]) + kAlign - 1) / kAlign * kAlign;
   }

@@ -638,6 +638,19 @@ sp_status sp_build_plan(sp_ctx* c) {
     const std::vector<float> img = yinv_tc_image(th.data(), td.data(), n1);
     if (!up((void**)&c->yinv_tc_mat, img.data(), img.size() * 4))
       return sp_fail(c, SP_ENOMEM, "device allocation of plan tables failed");
+    // the forward transform's: C[n][j] = 2 T_n(y_j) / (N cbar_n cbar_j) on the tau rows n <= N - 2
+    const int NR = N - 1;
+    std::vector<double> cf((size_t)NR * n1);
+    for (int n = 0; n < NR; ++n) {
+      const double cbn = n == 0 ? 2.0 : 1.0;
+      for (int j = 0; j < n1; ++j) {
+        const double cbj = (j == 0 || j == N) ? 2.0 : 1.0;
+        cf[(size_t)n * n1 + j] = 2.0 / (N * cbn) * cospi_frac((long)j * n, N) / cbj;
+      }
+    }
+    const std::vector<float> imf = rhs_tc_image(cf.data(), n1, NR);
+    if (!up((void**)&c->rhs_tc_mat, imf.data(), imf.size() * 4))
+      return sp_fail(c, SP_ENOMEM, "device allocation of plan tables failed");
   }
   if (q2) {
     std::vector<float> Tpf(Tp.begin(), Tp.end()), TDpf(TDp.begin(), TDp.end()), tqf(tq.begin(), tq.end()),

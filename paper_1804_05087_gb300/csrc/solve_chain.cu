@@ -387,6 +387,8 @@ cudaError_t launch_chain_rhs(const sp_ctx* c, bool fp32, const void* in3, const 
   if (n_dir <= 0) return cudaSuccess;
   RhsArgs r;
   chain_strides(c, n_dir, &r.su, &r.sd, &r.sn);
+  if (fp32 && c->use_rhs_tc && sp_rhs_tc_supported(c))  // forward transform on the tensor cores
+    return launch_rhs_tc(c, in3, du, work, n_dir, r.su, r.sd, r.sn, st);
   r.Cfh_d = c->Cfh;
   r.Cfh_f = c->Cfh_f;
   r.Cq_d = c->Cq;

@@ -99,6 +99,8 @@ struct sp_ctx {
   // tensor-core inverse transform (41 <= NY <= 72): shared-memory image of T and T' split into
   // TF32 hi and lo parts (yinv_tc.cu)
   float* yinv_tc_mat = nullptr;
+  // forward transform on the tensor cores: C_hi, C_lo (yinv_tc.cu)
+  float* rhs_tc_mat = nullptr;
   double* yv = nullptr;          // [NY] wall-normal points: cos(pi j / N) (Couette), r_j (pipe)
   double* lam6 = nullptr;        // [NY][6] laminar (U, Omega) per plane: (y,0,0,0,0,-1) / (0,0,1-r^2,0,2r,0)
   float *Th_f = nullptr, *TDh_f = nullptr, *Cfh_f = nullptr;
@@ -135,6 +137,7 @@ struct sp_ctx {
   int has_base = 0;
   int use_xz_reg = 1;            // float plane stage: register FFT kernel when the size allows
   int use_xz_reg64 = 1;          // FP64 tangent/adjoint plane stage: register FFT kernel (xz_reg64.cu)
+  int use_rhs_tc = 0;             // float forward transform of the chains on the tensor cores (yinv_tc.cu)
   int use_yinv_tc = 1;           // float inverse Chebyshev transform on the tensor cores (yinv_tc.cu)
   int solve_shape_tan = 0;       // k_solve tile shape of the tangent (sp_autotune)
   int solve_shape_step = 0;      // k_solve tile shape of the FP64 step
@@ -257,6 +260,12 @@ cudaError_t launch_xz_reg(const sp_ctx* c, int mode, const void* in, void* out, 
 bool sp_yinv_tc_supported(const sp_ctx* c);
 cudaError_t launch_yinv_tc(const sp_ctx* c, const double* in, void* out6, int n_dir, cudaStream_t st);
 std::vector<float> yinv_tc_image(const double* th, const double* td, int NY);
+// float forward transform + u/dt of the chains' right-hand sides on the tensor cores (yinv_tc.cu):
+// same inputs and outputs as launch_chain_rhs with fp32; W strides su, sd, sn
+bool sp_rhs_tc_supported(const sp_ctx* c);
+cudaError_t launch_rhs_tc(const sp_ctx* c, const void* in3, const double* du, void* work, int n_dir, long long su,
+                          long long sd, long long sn, cudaStream_t st);
+std::vector<float> rhs_tc_image(const double* cf, int NY, int NR);
 size_t yinv_tc_smem(int NY);
 // FP64 plane stage with register-resident FFTs (xz_reg64.cu), square grids 16..48
 bool sp_xz_reg64_supported(const sp_ctx* c);

@@ -92,3 +92,10 @@ extern "C" sp_status sp_set_solve_shape(sp_ctx* c, int tangent_shape, int step_s
   if (step_shape >= 0) c->solve_shape_step = step_shape;
   return SP_OK;
 }
+
+extern "C" sp_status sp_set_tensor_cores(sp_ctx* c, int inverse, int forward) {
+  if (!c) return SP_EINVAL;
+  c->use_yinv_tc = inverse ? 1 : 0;
+  c->use_rhs_tc = forward ? 1 : 0;
+  return SP_OK;
+}

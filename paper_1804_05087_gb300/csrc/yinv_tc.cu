@@ -306,7 +306,225 @@ cudaError_t launch_tc(const TcArgs& a, int grid, size_t sm, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Forward Chebyshev transform of the mixed tangent on the tensor cores (row a6 of the step, Sec. 3.2):
+// the right-hand sides of the per-mode tau rows n <= N-2,
+//   W[n][col] = sum_j C[n][j] f_j(col) + u_n(col) / dt,   C[n][j] = 2 T_n(y_j) / (N cbar_n cbar_j),
+// for the columns (field, direction, mode, re/im) of a tile of 4 unique modes x 4 directions. The same
+// split-TF32 MMAs as the inverse transform (M = 128 rows n, zero past N-2; N = 96 columns; K = NY
+// rounded up to 8), the constants C_hi, C_lo brought in by one bulk TMA copy. The epilogue adds the
+// FP64 state u/dt (Hermitian-projected on the kz = 0 plane) and writes the chains' right-hand sides.
+struct RhsTcArgs {
+  const float2* in;       // [dir][3][NY][Mm] float complex values
+  const double2* du;      // [dir][3][Mm][NY] the directions (FP64)
+  double2* W;             // right-hand sides (u, d, row c NR + n) at u su + d sd + row sn
+  long long su, sd, sn;
+  const float* amat;      // shared-memory image of C_hi, C_lo
+  int NY, Mm, MX, MZ, Kx, NR, n_unique, n_dir, mtiles, ntiles;  // tiles: 4 modes x 4 directions
+  double inv_dt;
+};
+
+__device__ __forceinline__ void unique_mode_tc(int u, int Kx, int MZ, int* pos, int* iz) {
+  const int first = (Kx + 1) * MZ;
+  if (u < first) {
+    *pos = u / MZ;
+    *iz = u - *pos * MZ;
+  } else {
+    const int v = u - first;
+    *pos = Kx + 1 + v / (MZ - 1);
+    *iz = 1 + v % (MZ - 1);
+  }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(kTcThreads, 1) k_rhs_tc(RhsTcArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar_mma, bar_load;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_m[4], s_pos[4], s_iz[4];
+  const int NY = a.NY;
+  constexpr uint32_t abytes = (uint32_t)kTcM * KP * 4;     // one A matrix
+  constexpr uint32_t bbytes = (uint32_t)(KP / 4) * kLboB;  // one B matrix
+  constexpr int kCols = 128;                               // tensor-memory columns (96 used)
+  unsigned char* sB = smem;                  // B_hi, B_lo
+  unsigned char* sA = smem + 2 * bbytes;     // C_hi, C_lo, then kTcPad bytes
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t ub_mma = smem_u32(&bar_mma), ub_load = smem_u32(&bar_load);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ub_mma));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ub_load));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    const uint32_t bytes = 2 * abytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ub_load), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(sA)),
+                 "l"(a.amat), "r"(bytes), "r"(ub_load)
+                 : "memory");
+  }
+  ok = mbar_wait(ub_load, 0);
+  constexpr uint32_t sbo = 128;
+  constexpr uint32_t id_w = idesc_tf32(kTcM, kTcCols);
+  uint32_t phase = 0;
+  // A tile is 4 unique modes x 4 directions. B columns: c 32 + 2 (4 dl + ml) + re/im for field c,
+  // direction dl, mode ml; K rows >= NY zero. Loaded into registers one tile ahead; a warp takes the 4
+  // modes of one direction (one 32-byte sector of the values) at 8 consecutive K, which the padded K
+  // stride spreads over the 32 banks.
+  constexpr int kItems = (3 * kTcModes * KP + kTcThreads - 1) / kTcThreads;
+  float2 pre[kItems];
+  auto prefetch = [&](int tile) {
+    const int dg = tile / a.mtiles, u0 = (tile - dg * a.mtiles) * 4;
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      const int it = threadIdx.x + r * kTcThreads;
+      const int ml = it & 3, kr = it >> 2, k = kr % KP, rest = kr / KP, dl = rest & 3, c = rest >> 2;
+      pre[r] = make_float2(0.0f, 0.0f);
+      const int u = u0 + ml, dir = dg * 4 + dl;
+      if (c < 3 && k < NY && u < a.n_unique && dir < a.n_dir) {
+        int pos, iz;
+        unique_mode_tc(u, a.Kx, a.MZ, &pos, &iz);
+        pre[r] = __ldg(a.in + (size_t)dir * 3 * NY * a.Mm + ((size_t)c * NY + k) * a.Mm + pos * a.MZ + iz);
+      }
+    }
+  };
+  int tile = blockIdx.x;
+  if (tile < a.ntiles) prefetch(tile);
+  while (tile < a.ntiles && ok) {
+    const int dg = tile / a.mtiles, u0 = (tile - dg * a.mtiles) * 4;
+    if (threadIdx.x < 4) {
+      const int u = u0 + threadIdx.x;
+      int pos = 0, iz = 0;
+      if (u < a.n_unique) unique_mode_tc(u, a.Kx, a.MZ, &pos, &iz);
+      s_m[threadIdx.x] = u;
+      s_pos[threadIdx.x] = pos;
+      s_iz[threadIdx.x] = iz;
+    }
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      const int it = threadIdx.x + r * kTcThreads;
+      const int ml = it & 3, kr = it >> 2, k = kr % KP, rest = kr / KP, dl = rest & 3, c = rest >> 2;
+      if (c >= 3) continue;
+      float h0, l0, h1, l1;
+      tf32_split(pre[r].x, h0, l0);
+      tf32_split(pre[r].y, h1, l1);
+      const uint32_t off = kmajor_off(c * 32 + 2 * (4 * dl + ml), k, kLboB);
+      *reinterpret_cast<float*>(sB + off) = h0;
+      *reinterpret_cast<float*>(sB + off + 16) = h1;
+      *reinterpret_cast<float*>(sB + bbytes + off) = l0;
+      *reinterpret_cast<float*>(sB + bbytes + off + 16) = l1;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (threadIdx.x == 0) {
+      const uint32_t aC = smem_u32(sA), aCl = aC + abytes;
+      const uint32_t bh = smem_u32(sB), bl = bh + bbytes;
+      const uint32_t pa[3] = {aC, aC, aCl}, pb[3] = {bh, bl, bh};  // hi*hi, hi*lo, lo*hi
+#pragma unroll
+      for (int pass = 0; pass < 3; ++pass) {
+#pragma unroll
+        for (int ks = 0; ks < KP / 8; ++ks) {
+          const uint32_t ka = (uint32_t)ks * 2 * kLboA, kb = (uint32_t)ks * 2 * kLboB;
+          const uint32_t acc = (pass > 0 || ks > 0) ? 1u : 0u;
+          mma_tf32(tmem, smem_desc(pa[pass] + ka, kLboA, sbo), smem_desc(pb[pass] + kb, kLboB, sbo), id_w, acc);
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(ub_mma)
+                   : "memory");
+    }
+    const int next = tile + gridDim.x;
+    if (next < a.ntiles) prefetch(next);
+    ok = mbar_wait(ub_mma, phase);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // epilogue: warp w reads rows n = 32 (w mod 4) .. + 31 (lane = n) for the directions 2 (w / 4) and
+    // 2 (w / 4) + 1 (quarter = direction), adds u_n / dt and writes the right-hand sides of the rows
+    // n <= N - 2: a thread writes two adjacent directions of each (mode, field, row)
+    const int sub = warp & 3, n = sub * 32 + lane;
+    for (int quarter = 2 * (warp >> 2); quarter < 2 * (warp >> 2) + 2 && ok; ++quarter) {
+      const int dir = dg * 4 + quarter;
+      const double2* dsrc = a.du + (size_t)dir * 3 * a.Mm * NY;
+      uint32_t r[3][8];
+      const uint32_t base = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(quarter * 8);
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[f][0]), "=r"(r[f][1]), "=r"(r[f][2]), "=r"(r[f][3]), "=r"(r[f][4]), "=r"(r[f][5]),
+                       "=r"(r[f][6]), "=r"(r[f][7])
+                     : "r"(base + (uint32_t)(32 * f)));
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (n < a.NR && dir < a.n_dir) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int ml = q, u = s_m[ml];
+          if (u >= a.n_unique) continue;
+          const int pos = s_pos[ml], iz = s_iz[ml];
+          const int mpos = pos == 0 ? 0 : a.MX - pos;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            double2 d = __ldg(dsrc + ((size_t)c * a.Mm + pos * a.MZ + iz) * NY + n);
+            if (iz == 0) {
+              const double2 w = __ldg(dsrc + ((size_t)c * a.Mm + mpos * a.MZ) * NY + n);
+              d = make_double2(0.5 * (d.x + w.x), 0.5 * (d.y - w.y));
+            }
+            double2 fo = make_double2((double)__uint_as_float(r[c][2 * q]) + d.x * a.inv_dt,
+                                      (double)__uint_as_float(r[c][2 * q + 1]) + d.y * a.inv_dt);
+            if (pos == 0 && iz == 0) fo.y = 0.0;
+            a.W[u * a.su + dir * a.sd + (long long)(c * a.NR + n) * a.sn] = fo;
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    tile = next;
+  }
+  if (!ok) {
+    // a wait ran out: poison this block's right-hand sides so that the caller sees non-finite values
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+      const int dg = t / a.mtiles, u0 = (t - dg * a.mtiles) * 4;
+      for (int it = threadIdx.x; it < 16 * 3 * a.NR; it += blockDim.x) {
+        const int ml = it & 3, dl = (it >> 2) & 3, row = it >> 4, u = u0 + ml, dir = dg * 4 + dl;
+        if (u < a.n_unique && dir < a.n_dir)
+          a.W[u * a.su + dir * a.sd + (long long)row * a.sn] = make_double2(nan, nan);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+  }
+}
+
+template <int KP>
+cudaError_t launch_rtc(const RhsTcArgs& a, int grid, size_t sm, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_rhs_tc<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_rhs_tc<KP><<<grid, kTcThreads, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t rhs_tc_smem(int NY) {
+  const int Kp = (NY + 7) / 8 * 8;
+  return (size_t)2 * kTcM * Kp * 4 + (size_t)2 * (Kp / 4) * kLboB + kTcPad;
+}
 
 size_t yinv_tc_smem(int NY) {
   const int Kp = (NY + 7) / 8 * 8;
@@ -367,6 +585,63 @@ cudaError_t launch_yinv_tc(const sp_ctx* c, const double* in, void* out6, int n_
     case 56: return launch_tc<56>(a, grid, sm, st);
     case 64: return launch_tc<64>(a, grid, sm, st);
     case 72: return launch_tc<72>(a, grid, sm, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Host image of C_hi, C_lo for the forward transform: 128 rows n (the tau rows n < NR, then zero) x Kp
+// (K-major canonical), cf[n][j] = C[n][j] for n < NR, j < NY (row-major, FP64).
+std::vector<float> rhs_tc_image(const double* cf, int NY, int NR) {
+  const int Kp = (NY + 7) / 8 * 8;
+  const size_t one = (size_t)kTcM * Kp;
+  std::vector<float> img(2 * one, 0.0f);
+  for (int n = 0; n < NR; ++n)
+    for (int j = 0; j < NY; ++j) {
+      const float xf = (float)cf[(size_t)n * NY + j];
+      uint32_t u;
+      std::memcpy(&u, &xf, 4);
+      const uint32_t hiu = (u + 0x1000u) & 0xFFFFE000u;  // round to TF32 as cvt.rna.tf32.f32 does
+      float hi;
+      std::memcpy(&hi, &hiu, 4);
+      img[kmajor_off(n, j, kLboA) / 4] = hi;
+      img[one + kmajor_off(n, j, kLboA) / 4] = xf - hi;
+    }
+  return img;
+}
+
+bool sp_rhs_tc_supported(const sp_ctx* c) {
+  return c->geom == 0 && c->rhs_tc_mat != nullptr && c->NY >= 41 && c->NY <= 72 && c->N - 1 <= kTcM;
+}
+
+cudaError_t launch_rhs_tc(const sp_ctx* c, const void* in3, const double* du, void* work, int n_dir, long long su,
+                          long long sd, long long sn, cudaStream_t st) {
+  if (n_dir <= 0) return cudaSuccess;
+  RhsTcArgs a;
+  a.in = static_cast<const float2*>(in3);
+  a.du = reinterpret_cast<const double2*>(du);
+  a.W = static_cast<double2*>(work);
+  a.su = su;
+  a.sd = sd;
+  a.sn = sn;
+  a.amat = c->rhs_tc_mat;
+  a.NY = c->NY;
+  a.Mm = c->Mm;
+  a.MX = c->MX;
+  a.MZ = c->MZ;
+  a.Kx = c->Kx;
+  a.NR = c->N - 1;
+  a.n_unique = c->n_unique;
+  a.n_dir = n_dir;
+  a.mtiles = (c->n_unique + 3) / 4;
+  a.ntiles = a.mtiles * ((n_dir + 3) / 4);
+  a.inv_dt = 1.0 / c->dt;
+  const size_t sm = rhs_tc_smem(c->NY);
+  const int grid = std::min(a.ntiles, c->sm_count);
+  switch ((c->NY + 7) / 8 * 8) {
+    case 48: return launch_rtc<48>(a, grid, sm, st);
+    case 56: return launch_rtc<56>(a, grid, sm, st);
+    case 64: return launch_rtc<64>(a, grid, sm, st);
+    case 72: return launch_rtc<72>(a, grid, sm, st);
     default: return cudaErrorInvalidValue;
   }
 }

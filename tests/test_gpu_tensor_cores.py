@@ -31,3 +31,45 @@ def test_tensor_core_transform_tangent(grid):
         tol = 1e-4 if i == 2 else 1e-5
         for c in range(3):
             assert rel(got[i, c], ref[c]) < tol
+
+
+@pytest.mark.parametrize("grid", [(16, 41, 16), (18, 49, 24), (16, 71, 16)])
+@pytest.mark.parametrize("n_dir", [3, 20])
+def test_tensor_core_forward_transform_chains(grid, n_dir):
+    """Contexts with max_batch >= 32 solve the batched tangent by the O(N) chains, whose right-hand
+    sides (forward transform of the plane-stage output plus u/dt, row a6) come from the tcgen05
+    kernel as well; 20 directions write them directions fastest, 3 directions modes fastest."""
+    ctx, orc = make(*grid, prec=1, max_batch=32)
+    ctx.sp_set_tensor_cores(inverse=True, forward=True)
+    u = seeded(orc, 1001, 0.1)
+    ctx.sp_set_base(dev(u))
+    base = orc.base(u)
+    ds = np.stack([seeded(orc, 90 + i, 1.0) for i in range(n_dir - 1)] + [si.couette_random_full(89, *grid)])
+    out = ctx.zeros(n_dir)
+    ctx.sp_jvp(dev(ds), out)
+    got = host(out)
+    assert np.all(np.isfinite(got))
+    for i in (0, n_dir // 2, n_dir - 1):
+        ref = orc.jvp(base, ds[i])
+        tol = 1e-4 if i == n_dir - 1 else 1e-5
+        for c in range(3):
+            assert rel(got[i, c], ref[c]) < tol
+
+
+def test_tensor_core_forms_agree_with_cuda_core_kernels():
+    """The same batched mixed tangent with every tensor-core form off and on: agreement to float
+    accuracy (each is checked against the oracle above)."""
+    grid = (18, 49, 24)
+    ctx, orc = make(*grid, prec=1, max_batch=32)
+    u = seeded(orc, 1002, 0.1)
+    ctx.sp_set_base(dev(u))
+    ds = np.stack([seeded(orc, 120 + i, 1.0) for i in range(20)])
+    outs = []
+    for inv, fwd in ((False, False), (True, True)):
+        ctx.sp_set_tensor_cores(inverse=inv, forward=fwd)
+        out = ctx.zeros(20)
+        ctx.sp_jvp(dev(ds), out)
+        outs.append(host(out))
+    for i in range(20):
+        for c in range(3):
+            assert rel(outs[1][i, c], outs[0][i, c]) < 1e-5
