@@ -227,7 +227,15 @@ def kernel_traffic(stage, n_dir, prec, lam_adv):
     """DRAM bytes of one launch from an ncu capture of the current kernel, or None."""
     if stage == "k_solve" and prec == "mixed" and not lam_adv and not chain(n_dir):
         return solve_traffic(n_dir)
+    if stage == "k_xz" and prec == "fp64" and not lam_adv and (NX, NY, NZ) == (48, 65, 48):
+        rd, wr = K_XZ64_DRAM_64  # every byte scales with the directions (one plane per block)
+        return (rd + wr) * n_dir / 64
     return None
+
+
+# DRAM bytes of one FP64 tangent launch of the register plane stage k_xz_reg64<48, 48> at
+# 48x65x48 with 64 directions (dram__bytes_read.sum, dram__bytes_write.sum of that launch)
+K_XZ64_DRAM_64 = (205562368, 68731392)
 
 
 # DRAM bytes of one mixed-precision k_solve tangent launch at 48x65x48 with 64 directions, from
