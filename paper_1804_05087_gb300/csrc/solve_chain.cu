@@ -207,10 +207,13 @@ __device__ __forceinline__ double2 tri_sweep(const double* __restrict__ r4, doub
   const int m = (N - Q) / 2;
   double2 Rhi = make_double2(0.0, 0.0);              // R_{n+2}
   double2 Rmid = rhs(2 * m + Q);                     // R_n (zero when n > N-2)
+  double2 Rlo = rhs(2 * m + Q - 2);                  // R_{n-2}, fetched one step ahead
   double2 bnext = make_double2(0.0, 0.0), acc = make_double2(0.0, 0.0);
   for (int i = m; i >= 1; --i) {
     const int n = 2 * i + Q;
-    const double2 Rlo = rhs(n - 2);
+    // the next step's right-hand side (same descending order of calls): its loads are in flight
+    // while this step's dependent arithmetic runs
+    const double2 Rnext = i >= 2 ? rhs(n - 4) : make_double2(0.0, 0.0);
     const double* w = om + 3 * n;
     double2 r = cmix(Rlo, w[0], Rmid, w[1]);
     r = caxpy(r, Rhi, w[2]);
@@ -221,6 +224,7 @@ __device__ __forceinline__ double2 tri_sweep(const double* __restrict__ r4, doub
     bnext = b;
     Rhi = Rmid;
     Rmid = Rlo;
+    Rlo = Rnext;
   }
   double2 x = cscl(csub(bc, acc), g);
   X[0] = x;
