@@ -195,10 +195,11 @@ def kernel_flops(stage, n_dir, prec="mixed"):
         return n_dir * n_unique() * per
     if stage == "k_solve" and chain(n_dir):
         # O(N) chains, FP64, per (mode, parity) thread and coefficient: the w_A sweep with the
-        # reduced right-hand side (40 flops), the v_A sweep (24), the influence correction,
+        # reduced right-hand side (38 flops), the v_A sweep (22), the influence correction,
         # G_v and the continuity suffix sum (20), the b sweep with the back-rotation and
-        # G_u, G_w (46): 130 flops per coefficient, NH coefficients per parity
-        return n_dir * n_unique() * 2 * nh * 130
+        # G_u, G_w (44): 124 flops per coefficient, NH coefficients per parity. A sweep step
+        # is 18 flops (the row weights folded into the records) and a substitution step 4.
+        return n_dir * n_unique() * 2 * nh * 124
     if stage == "k_solve":
         # FP64 work: the per-mode operators (real matrices on complex right-hand sides,
         # 4 flops per entry), the reduced right-hand side g (one complex FMA and one complex

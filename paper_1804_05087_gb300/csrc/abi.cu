@@ -91,7 +91,7 @@ static void free_ctx(sp_ctx* c) {
   void* ptrs[] = {c->Th, c->TDh, c->Cfh, c->yv, c->lam6, c->Th_f, c->TDh_f, c->Cfh_f, c->twx, c->twz, c->base32t,
                   c->twx_f, c->twz_f, c->ops, c->ws6, c->ws3, c->base64, c->base32, c->U0,
                   c->G0, c->tmp, c->red, c->kry, c->wsG, c->pb_fac, c->pb_uh, c->pb_dinv, c->fd_w1, c->fd_c1, c->dzU,
-                  c->traj, c->nbuf, c->traj_base, c->chain, c->omega, c->Tp, c->TDp, c->tq,
+                  c->traj, c->nbuf, c->traj_base, c->chain, c->Tp, c->TDp, c->tq,
                   c->Tp_f, c->TDp_f, c->tq_f, c->Cq, c->Cq_f, c->yinv_tc_mat, c->rhs_tc_mat};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -71,5 +71,6 @@ extern "C" sp_status sp_jvp_static(sp_ctx* c, const double* du, double* Jdu, voi
   // contents left by an earlier call need no clearing
   if ((s = sp_cuda(c, launch_yinv(c, f32, du, ws6, 1, st), "yinv")) != SP_OK) return s;
   if ((s = sp_cuda(c, launch_xz(c, f32, XZ_TANGENT, ws6, ws3, 1, st), "xz tangent")) != SP_OK) return s;
-  return sp_tangent_solve(c, f32, ws3, b3, du, Jdu, ws6, 1, st);
+  // the second part runs to the end of the array: the chains' scratch may use all of it
+  return sp_tangent_solve(c, f32, ws3, kStaticScratchBytes - b6, du, Jdu, ws6, 1, st);
 }

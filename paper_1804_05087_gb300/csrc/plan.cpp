@@ -332,9 +332,12 @@ bool build_hop_la(const ChebOps& C, double kx, double lam, double nu, double* ou
 // an invertible recombination of the tau rows (so the solution is the tau
 // solution), which together with the boundary row is solved by one elimination
 // sweep from the top and one substitution sweep from the bottom. Per unknown
-// i = 1..m (n = 2i + Q) the record holds (q, p, psi, alpha): the sweep
-// beta_i = r_i q_i - p_i beta_{i+1}, the boundary-row weights psi_i with
-// x_0 = (bc - sum_i psi_i beta_i) g, and the substitution x_i = alpha_i x_{i-1} + beta_i.
+// i = 1..m (n = 2i + Q) the sweep is beta_i = r_i q_i - p_i beta_{i+1} with r_i the
+// right-hand side of row n above, the boundary-row weights psi_i give
+// x_0 = (bc - sum_i psi_i beta_i) g, and the substitution is x_i = alpha_i x_{i-1} + beta_i.
+// The device record of unknown i holds (q w_0, q w_1, q w_2, p, psi, alpha), w_k the
+// weights of f_{n-2}, f_n, f_{n+2} in r_i: the sweep then costs one product and three
+// fused multiply-adds per real component.
 // H uses (l', n') = (lam, nu); K uses (-k^2, -1), i.e. (D^2 - k^2) x = f.
 //
 // The coupled (v, a, p) problem of parity P is the fourth-order tau problem
@@ -410,30 +413,33 @@ std::vector<double> tri_solve(int N, int Q, const TriOp& t, const std::vector<do
   return x;
 }
 
-// the record of one parity: [H (q,p,psi,alpha) x NH][K x NH][(v_psi, v_h) x NH][8 scalars]
+// the sweep record of one tridiagonal operator (6 doubles per unknown i = 1..m, see above)
+void put_sweep_record(int N, int Q, const TriOp& t, double* r6) {
+  const int m = (N - Q) / 2;
+  for (int i = 1; i <= m; ++i) {
+    double w[3];
+    chain_weights(N, 2 * i + Q, w);
+    r6[6 * i + 0] = t.q[i] * w[0];
+    r6[6 * i + 1] = t.q[i] * w[1];
+    r6[6 * i + 2] = t.q[i] * w[2];
+    r6[6 * i + 3] = t.p[i];
+    r6[6 * i + 4] = t.psi[i];
+    r6[6 * i + 5] = t.alpha[i];
+  }
+}
+
+// the record of one parity: [H x 6 NH][K x 6 NH][(v_psi, v_h) x NH][8 scalars]
 void build_chain_parity(int N, int P, double k, double lam, double nu, bool mean, double* out) {
   const int NH = N / 2 + 1, m = (N - P) / 2;
   const TriOp H = tri_factor(N, P, lam, nu);
-  double* h4 = out;
-  double* k4 = out + 4 * NH;
-  double* v2 = out + 8 * NH;
-  double* sc = out + 10 * NH;
-  for (int i = 1; i <= m; ++i) {
-    h4[4 * i + 0] = H.q[i];
-    h4[4 * i + 1] = H.p[i];
-    h4[4 * i + 2] = H.psi[i];
-    h4[4 * i + 3] = H.alpha[i];
-  }
+  double* v2 = out + 12 * NH;
+  double* sc = out + 14 * NH;
+  put_sweep_record(N, P, H, out);
   sc[0] = H.g;
   if (mean) return;
   const double k2 = k * k;
   const TriOp K = tri_factor(N, P, -k2, -1.0);
-  for (int i = 1; i <= m; ++i) {
-    k4[4 * i + 0] = K.q[i];
-    k4[4 * i + 1] = K.p[i];
-    k4[4 * i + 2] = K.psi[i];
-    k4[4 * i + 3] = K.alpha[i];
-  }
+  put_sweep_record(N, P, K, out + 6 * NH);
   sc[1] = K.g;
   const int n1 = N + 1;
   std::vector<double> zero(n1, 0.0), h(n1, 0.0);
@@ -588,10 +594,11 @@ sp_status sp_build_plan(sp_ctx* c) {
     if (b) return sp_fail(c, SP_EINVAL, "singular per-mode Stokes system");
 
   // O(N) chain records and the universal row weights (the batched tangent's solve)
-  c->use_chain = (c->cfg.max_batch >= kChainMinBatch && !la && chain_smem(c) <= 227 * 1024) ? 1 : 0;
-  std::vector<double> chain, omega;
+  c->use_chain =
+      (c->cfg.max_batch >= kChainMinBatch && !la && N < kChainMaxRows) ? 1 : 0;
+  std::vector<double> chain;
   if (c->use_chain) {
-    c->chain_par = 10 * NH + 8;
+    c->chain_par = 14 * NH + 8;
     c->chain_stride = 2 * c->chain_par;
     chain.assign((size_t)c->n_unique * c->chain_stride, 0.0);
     for (int u = 0; u < c->n_unique; ++u) {
@@ -603,8 +610,6 @@ sp_status sp_build_plan(sp_ctx* c) {
       for (int P = 0; P < 2; ++P)
         build_chain_parity(N, P, k, lam, c->nu, u == 0, chain.data() + (size_t)u * c->chain_stride + P * c->chain_par);
     }
-    omega.assign((size_t)3 * n1, 0.0);
-    for (int n = 2; n <= N; ++n) chain_weights(N, n, omega.data() + 3 * n);
   }
 
   // float copies
@@ -620,8 +625,7 @@ sp_status sp_build_plan(sp_ctx* c) {
             up((void**)&c->TDh_f, TDhf.data(), TDhf.size() * 4) && up((void**)&c->Cfh_f, Cfhf.data(), Cfhf.size() * 4) &&
             up((void**)&c->ops, ops.data(), ops.size() * 8) && up((void**)&c->yv, yv.data(), yv.size() * 8) &&
             up((void**)&c->lam6, lam6.data(), lam6.size() * 8) &&
-            (!c->use_chain || (up((void**)&c->chain, chain.data(), chain.size() * 8) &&
-                               up((void**)&c->omega, omega.data(), omega.size() * 8)));
+            (!c->use_chain || up((void**)&c->chain, chain.data(), chain.size() * 8));
   if (!ok) return sp_fail(c, SP_ENOMEM, "device allocation of plan tables failed");
   // the tensor-core inverse transform's constant operands: the full T and T' (all NY points)
   if (c->geom == 0 && c->NY >= 41 && c->NY <= 72) {

@@ -175,15 +175,16 @@ struct ChainArgs {
   const double2* du;       // [dir][3][Mm][NY]
   double2* out;            // same layout
   const double* rec;       // [n_unique][2][par]
-  const double* omega;     // [NY][3]
   long long su, sd, sn;
   int n_unique, n_dir, dirs_fast;
   int Mm, MX, MZ, Kx, NY, N, NH, par, stride;
   double alpha, beta;
-  double2* S2g;            // second work vector of every thread: entry i of thread t at S2g[i * T + t]
+  double2* Sg;             // work vectors of every thread: entry i of thread t at Sg[i * T + t] (the
+                           // second vector) and Sg[(NH + i) * T + t] (the first), T threads in all
 };
 
 constexpr int kChainWarps = 2;  // threads per block = 32 kChainWarps (warp pairs: parity 0, 1)
+constexpr int kChainBlocksPerSM = 12;  // register budget: 24 warps per SM (80 registers a thread)
 constexpr int kDirsFastMin = 16;  // batches of this many directions put lanes over directions
 
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
@@ -197,13 +198,29 @@ __device__ __forceinline__ double2 caxpy(double2 a, double2 b, double s) {
   return make_double2(fma(b.x, s, a.x), fma(b.y, s, a.y));
 }
 
+// The row indices n and n^2 as doubles: a warp-uniform table read instead of an
+// integer-to-FP64 conversion, which would take the FP64 pipe.
+struct RowTable {
+  double n[kChainMaxRows];
+  double n2[kChainMaxRows];
+};
+constexpr RowTable make_row_table() {
+  RowTable t{};
+  for (int i = 0; i < kChainMaxRows; ++i) {
+    t.n[i] = (double)i;
+    t.n2[i] = (double)i * (double)i;
+  }
+  return t;
+}
+__constant__ RowTable kRow = make_row_table();
+
 // One Dirichlet Helmholtz tau solve of parity Q in the tridiagonal form (records of
-// plan.cpp): rhs(n) gives the right-hand side of tau row n (zero above N-2), bc the
-// boundary value; X (shared memory, stride st) receives x_i, i = 0..m; the return
-// value is x_m.
+// plan.cpp: per unknown i, (q w_0, q w_1, q w_2, p, psi, alpha)): rhs(n) gives the
+// right-hand side of tau row n (zero above N-2), bc the boundary value; X (stride st)
+// receives x_i, i = 0..m; the return value is x_m.
 template <class Rhs>
-__device__ __forceinline__ double2 tri_sweep(const double* __restrict__ r4, double g, const double* __restrict__ om,
-                                             int N, int Q, Rhs rhs, double2 bc, double2* X, int st) {
+__device__ __forceinline__ double2 tri_sweep(const double* __restrict__ r6, double g, int N, int Q, Rhs rhs,
+                                             double2 bc, double2* X, int st) {
   const int m = (N - Q) / 2;
   double2 Rhi = make_double2(0.0, 0.0);              // R_{n+2}
   double2 Rmid = rhs(2 * m + Q);                     // R_n (zero when n > N-2)
@@ -214,12 +231,11 @@ __device__ __forceinline__ double2 tri_sweep(const double* __restrict__ r4, doub
     // the next step's right-hand side (same descending order of calls): its loads are in flight
     // while this step's dependent arithmetic runs
     const double2 Rnext = i >= 2 ? rhs(n - 4) : make_double2(0.0, 0.0);
-    const double* w = om + 3 * n;
-    double2 r = cmix(Rlo, w[0], Rmid, w[1]);
-    r = caxpy(r, Rhi, w[2]);
-    const double* t = r4 + 4 * i;  // q, p, psi, alpha
-    const double2 b = cmix(r, t[0], bnext, -t[1]);
-    acc = caxpy(acc, b, t[2]);
+    const double* t = r6 + 6 * i;
+    double2 b;
+    b.x = fma(-t[3], bnext.x, fma(t[2], Rhi.x, fma(t[1], Rmid.x, t[0] * Rlo.x)));
+    b.y = fma(-t[3], bnext.y, fma(t[2], Rhi.y, fma(t[1], Rmid.y, t[0] * Rlo.y)));
+    acc = caxpy(acc, b, t[4]);
     X[i * st] = b;
     bnext = b;
     Rhi = Rmid;
@@ -229,21 +245,19 @@ __device__ __forceinline__ double2 tri_sweep(const double* __restrict__ r4, doub
   double2 x = cscl(csub(bc, acc), g);
   X[0] = x;
   for (int i = 1; i <= m; ++i) {
-    x = caxpy(X[i * st], x, r4[4 * i + 3]);
+    x = caxpy(X[i * st], x, r6[6 * i + 5]);
     X[i * st] = x;
   }
   return x;
 }
 
-__global__ void __launch_bounds__(32 * kChainWarps) k_chain(ChainArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  // two work vectors of NH entries per thread: S1 in shared memory, S2 in global scratch (one thread
-  // per column, consecutive threads adjacent: coalesced, mostly L2-resident). Shared memory per thread
-  // is then one vector, which doubles the warps an SM holds for the dependent sweeps.
-  const int st = blockDim.x;
-  double2* S1 = reinterpret_cast<double2*>(smem_raw) + threadIdx.x;  // [NH][blockDim]
-  const int st2 = gridDim.x * blockDim.x;
-  double2* S2 = a.S2g + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * kChainWarps, kChainBlocksPerSM) k_chain(ChainArgs a) {
+  // two work vectors of NH entries per thread, both in global scratch (one thread per column,
+  // consecutive threads adjacent: coalesced, mostly L2-resident). Without shared memory the
+  // registers alone bound the warps an SM holds for the dependent sweeps.
+  const int st2 = gridDim.x * blockDim.x, st = st2;
+  double2* S2 = a.Sg + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double2* S1 = S2 + (size_t)a.NH * st2;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int P = gw & 1, Q = 1 - P;
   const int item = (gw >> 1) * 32 + (threadIdx.x & 31);
@@ -280,16 +294,15 @@ __global__ void __launch_bounds__(32 * kChainWarps) k_chain(ChainArgs a) {
     if (iz == 0 && pos != 0) dst[((size_t)c * Mm + mpos * MZ) * NY + n] = make_double2(g.x, -g.y);
   };
   const double* rec = a.rec + (size_t)u * a.stride;
-  const double* om = a.omega;
   const int NH = a.NH;
   const double2 zero = make_double2(0.0, 0.0);
 
   if (u == 0) {
     // mean flow: (1/dt - nu D^2) u_00 = f_x, the same for w_00, v_00 = 0 (parity P rows)
     const double* rP = rec + P * a.par;
-    const double gH = rP[10 * NH];
-    tri_sweep(rP, gH, om, N, P, [&](int n) { return fval(0, n); }, zero, S1, st);
-    tri_sweep(rP, gH, om, N, P, [&](int n) { return fval(2, n); }, zero, S2, st2);
+    const double gH = rP[14 * NH];
+    tri_sweep(rP, gH, N, P, [&](int n) { return fval(0, n); }, zero, S1, st);
+    tri_sweep(rP, gH, N, P, [&](int n) { return fval(2, n); }, zero, S2, st2);
     const int m = (N - P) / 2;
     for (int i = 0; i <= m; ++i) {
       const int n = 2 * i + P;
@@ -303,6 +316,7 @@ __global__ void __launch_bounds__(32 * kChainWarps) k_chain(ChainArgs a) {
   const double kx = a.alpha * (pos <= a.Kx ? pos : pos - a.MX), kz = a.beta * iz;
   const double k2 = kx * kx + kz * kz, k = sqrt(k2), ik = 1.0 / k;
   const double cx = kx * ik, cz = kz * ik;
+  const double ik2 = 2.0 * ik;  // (2 / c_n) / k for n >= 1
   const double* rP = rec + P * a.par;
   const double* rQ = rec + Q * a.par;
   const int m = (N - P) / 2;
@@ -318,31 +332,28 @@ __global__ void __launch_bounds__(32 * kChainWarps) k_chain(ChainArgs a) {
       if (next_add <= N - 2) {
         const double2 fx = fval(0, next_add), fz = fval(2, next_add);
         const double2 fa = cmix(fx, cx, fz, cz);
-        S = caxpy(S, make_double2(fa.y, -fa.x), (double)next_add);
+        S = caxpy(S, make_double2(fa.y, -fa.x), kRow.n[next_add]);
       }
       next_add -= 2;
     }
     const double2 fv = fval(1, n);
-    const double2 g = caxpy(fv, S, -(n == 0 ? 1.0 : 2.0) * ik);
+    const double2 g = caxpy(fv, S, n == 0 ? -ik : -ik2);
     return cscl(g, -k2);
   };
-  const double2 wtop = tri_sweep(rP, rP[10 * NH], om, N, P, gneg, zero, S1, st);
+  const double2 wtop = tri_sweep(rP, rP[14 * NH], N, P, gneg, zero, S1, st);
   // (2) v_A: (D^2 - k^2) v = w_A on the rows <= N-2 of parity P, v(+-1) = 0
-  const double2 vtop = tri_sweep(rP + 4 * NH, rP[10 * NH + 1], om, N, P,
+  const double2 vtop = tri_sweep(rP + 6 * NH, rP[14 * NH + 1], N, P,
                                  [&](int n) { return n <= N - 2 ? S1[((n - P) >> 1) * st] : zero; }, zero, S2, st2);
   // (3) influence correction: sigma psi + tau h fixes w_top = -k^2 v_top and Dv(+-1) = 0
   double2 e2 = zero;
-  for (int i = 0; i <= m; ++i) {
-    const double n = 2.0 * i + P;
-    e2 = caxpy(e2, S2[i * st2], n * n);
-  }
+  for (int i = 0; i <= m; ++i) e2 = caxpy(e2, S2[i * st2], kRow.n2[2 * i + P]);
   const double2 e1 = caxpy(wtop, vtop, k2);
-  const double* sc = rP + 10 * NH;
+  const double* sc = rP + 14 * NH;
   const double2 sig = cmix(e1, -sc[2], e2, -sc[3]);
   const double2 tau = cmix(e1, -sc[4], e2, -sc[5]);
   // (4) v = v_A + sigma v_psi + tau v_h, G_v on the rows of parity P; a = (i/k) D v on the
   // rows of parity Q by a suffix sum, stored in S2 (slot i holds a_{2i+P-1})
-  const double* v2 = rP + 8 * NH;
+  const double* v2 = rP + 12 * NH;
   double2 Sa = zero;
   for (int i = m; i >= 0; --i) {
     const int n = 2 * i + P;
@@ -350,15 +361,15 @@ __global__ void __launch_bounds__(32 * kChainWarps) k_chain(ChainArgs a) {
     v = caxpy(v, sig, v2[2 * i]);
     v = caxpy(v, tau, v2[2 * i + 1]);
     put(1, n, csub(v, duv(1, n)));
-    Sa = caxpy(Sa, v, (double)n);
+    Sa = caxpy(Sa, v, kRow.n[n]);
     if (n >= 1) {
-      const double f = (n - 1 == 0 ? 1.0 : 2.0) * ik;  // (i/k)(2/c_{n-1}) Sa
+      const double f = n - 1 == 0 ? ik : ik2;  // (i/k)(2/c_{n-1}) Sa
       S2[i * st2] = make_double2(-Sa.y * f, Sa.x * f);
     }
   }
   // (5) b of parity Q: (lam - nu D^2) b = f_b, b(+-1) = 0; then u = cx a - cz b,
   // w = cz a + cx b and G_u, G_w on the rows of parity Q
-  tri_sweep(rQ, rQ[10 * NH], om, N, Q,
+  tri_sweep(rQ, rQ[14 * NH], N, Q,
             [&](int n) { return cmix(fval(0, n), -cz, fval(2, n), cx); }, zero, S1, st);
   const int mq = (N - Q) / 2;
   for (int i = 0; i <= mq; ++i) {
@@ -421,27 +432,24 @@ cudaError_t launch_chain_rhs(const sp_ctx* c, bool fp32, const void* in3, const 
   return cudaGetLastError();
 }
 
-size_t chain_smem(const sp_ctx* c) { return sizeof(double2) * (size_t)c->NH * 32 * kChainWarps; }
-
-// global scratch of k_chain for n_dir directions (the second work vector of every thread)
+// global scratch of k_chain for n_dir directions (the two work vectors of every thread)
 size_t chain_scratch_bytes(const sp_ctx* c, int n_dir) {
   const long long items = (long long)c->n_unique * n_dir;
   const long long warps = 2 * ((items + 31) / 32);
   const long long blocks = (warps + kChainWarps - 1) / kChainWarps;
-  return sizeof(double2) * (size_t)c->NH * (size_t)(blocks * 32 * kChainWarps);
+  return 2 * sizeof(double2) * (size_t)c->NH * (size_t)(blocks * 32 * kChainWarps);
 }
 
 cudaError_t launch_chain_solve(const sp_ctx* c, const double* du, double* out, const void* work, void* scratch,
                                int n_dir, cudaStream_t st) {
   if (n_dir <= 0) return cudaSuccess;
   ChainArgs a;
-  a.S2g = static_cast<double2*>(scratch);
+  a.Sg = static_cast<double2*>(scratch);
   chain_strides(c, n_dir, &a.su, &a.sd, &a.sn);
   a.W = static_cast<const double2*>(work);
   a.du = reinterpret_cast<const double2*>(du);
   a.out = reinterpret_cast<double2*>(out);
   a.rec = c->chain;
-  a.omega = c->omega;
   a.n_unique = c->n_unique;
   a.n_dir = n_dir;
   a.dirs_fast = n_dir >= kDirsFastMin ? 1 : 0;
@@ -456,13 +464,9 @@ cudaError_t launch_chain_solve(const sp_ctx* c, const double* du, double* out, c
   a.stride = c->chain_stride;
   a.alpha = c->alpha;
   a.beta = c->beta;
-  const size_t sm = chain_smem(c);
-  if (sm > 227 * 1024) return cudaErrorNotSupported;
-  cudaError_t e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
   const long long items = (long long)c->n_unique * n_dir;
   const long long warps = 2 * ((items + 31) / 32);
   const long long blocks = (warps + kChainWarps - 1) / kChainWarps;
-  k_chain<<<(unsigned)blocks, 32 * kChainWarps, sm, st>>>(a);
+  k_chain<<<(unsigned)blocks, 32 * kChainWarps, 0, st>>>(a);
   return cudaGetLastError();
 }

@@ -51,6 +51,7 @@ struct FftPlan {
 // contexts whose batches reach this many directions solve the tangent's per-mode
 // problems with the O(N) chains (one thread per mode, parity and direction)
 constexpr int kChainMinBatch = 32;
+constexpr int kChainMaxRows = 512;  // the chains' table of row indices as doubles covers N < 512
 
 // band of the pipe's radial factors: the 9-point stencils reach 6 rows below and 8 above the
 // diagonal (wall rows one-sided, axis rows folded onto their mirror points), and the row
@@ -108,7 +109,6 @@ struct sp_ctx {
   float2 *twx_f = nullptr, *twz_f = nullptr;
   double* ops = nullptr;
   double* chain = nullptr;       // [n_unique][2 parities][chain_par]
-  double* omega = nullptr;       // [NY][3] right-hand-side weights of the tridiagonal rows
   // pipe: per-mode dense operators (3 NY x 3 NY, column-major), radial FD band (D1) tables
   // pipe: banded LU factors of the per-mode radial problems (plan_pipe.cpp), matrices
   // 0 pressure, 1 u+, 2 u-, 3 u~z (mean mode: 1 u_theta, 2 u_z); one chunk of pb_chunk bytes
@@ -273,17 +273,16 @@ cudaError_t launch_xz_reg64(const sp_ctx* c, int mode, const void* in, void* out
 // batched tangent solve by O(N) chains (solve_chain.cu), two launches: k_rhs (values ->
 // right-hand sides in work, n_unique x 3 x (N-1) complex per direction), then k_chain
 // (one thread per mode, parity and direction); together the same inputs and outputs as
-// launch_solve. chain_smem: dynamic shared memory of k_chain (0 if it does not fit).
+// launch_solve.
 cudaError_t launch_chain_rhs(const sp_ctx* c, bool fp32, const void* in3, const double* du, void* work, int n_dir,
                              cudaStream_t st);
 cudaError_t launch_chain_solve(const sp_ctx* c, const double* du, double* out, const void* work, void* scratch,
                                int n_dir, cudaStream_t st);
-size_t chain_smem(const sp_ctx* c);
 size_t chain_scratch_bytes(const sp_ctx* c, int n_dir);
 // the tangent's per-mode solve of one pass (abi.cu): chains or dense operators by the
 // context's choice (use_chain); work: scratch of n_unique x 3 x (N-1) complex doubles
 // per direction (the chains' right-hand sides; ws6 suffices); vals (vals_bytes long) is
-// read by the right-hand-side launch and then serves as the chains' second scratch
+// read by the right-hand-side launch and then serves as the chains' scratch
 // (chain_scratch_bytes); if it is too small the dense operators solve instead
 sp_status sp_tangent_solve(sp_ctx* c, bool f32, void* vals, size_t vals_bytes, const double* du, double* out,
                            void* work, int nb, cudaStream_t st);
