@@ -108,11 +108,20 @@ __device__ __forceinline__ void dif_blocks(C2<T> (&x)[NT], std::integer_sequence
   (dif<T, NT, M, OFF + D * M, SGN, Pr...>(x), ...);
 }
 
-// multiply by w_N^{SGN k} (a compile-time constant; k = 0 is the identity)
+// multiply by w_N^{SGN k} (a compile-time constant; k = 0 is the identity). Quarter turns
+// (w = -1, +-i) are sign changes and swaps: written as products with 0 and 1 they would
+// still cost two FMAs, since x * 0 cannot be dropped under IEEE rules.
 template <typename T, int N, int SGN, long K>
 __device__ __forceinline__ C2<T> twiddle(C2<T> y) {
-  if constexpr (K % N == 0) {
+  constexpr long Kr = ((K % N) + N) % N;
+  if constexpr (Kr == 0) {
     return y;
+  } else if constexpr (4 * Kr == 2 * N) {  // w = -1
+    return mk(-y.x, -y.y);
+  } else if constexpr (4 * Kr == N || 4 * Kr == 3 * N) {  // w = i s, s = +-1
+    constexpr int s = (4 * Kr == N ? 1 : -1) * SGN;
+    if constexpr (s > 0) return mk(-y.y, y.x);
+    else return mk(y.y, -y.x);
   } else {
     constexpr T wc = (T)cos2pi(K, N);
     constexpr T ws = (T)(SGN * sin2pi(K, N));
