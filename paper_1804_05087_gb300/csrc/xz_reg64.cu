@@ -100,23 +100,20 @@ struct SrcX {
   }
 };
 
-// phase 2a: two real x-rows packed as real + i imag, their z-spectra from G
+// phase 2a: two real x-rows packed as real + i imag; phase 1 stored the packed z-spectrum
+// (kz = 0..KZ in the first row's slots, the mirrored frequencies NZ - kz in the second's)
 template <int NZ>
-struct SrcZ2 {
+struct SrcZP {
   static constexpr int KZ = (NZ - 1) / 3;
-  const cd* g0;  // row 2q, kz = 0..KZ
-  const cd* g1;  // row 2q + 1
+  const cd* g0;  // first row of the pair
+  const cd* g1;  // second row of the pair
   __host__ __device__ static constexpr bool zero(int e) { return e > KZ && e < NZ - KZ; }
-  __device__ __forceinline__ cd operator()(int e) const {
-    if (e == 0) return mk(g0[0].x, g1[0].x);
-    if (e <= KZ) {
-      const cd A = g0[e], B = g1[e];
-      return mk(A.x - B.y, A.y + B.x);
-    }
-    const cd A = g0[NZ - e], B = g1[NZ - e];
-    return mk(A.x + B.y, B.x - A.y);
-  }
+  __device__ __forceinline__ cd operator()(int e) const { return e <= KZ ? g0[e] : g1[NZ - e]; }
 };
+
+// row pair q of the z transforms: rows 4 (q >> 1) + (q & 1) and that + 2, both held by one
+// half of a phase-1 transform (half h holds the rows 2k + h)
+__device__ __forceinline__ int pair_row(int q) { return 4 * (q >> 1) + (q & 1); }
 
 // phases 2c and 3: a dense row of shared memory with a stride
 struct SrcDense {
@@ -168,6 +165,7 @@ __device__ __forceinline__ void xz64_body(const Xz64Args& a, int bx, int by) {
   constexpr int MX = 2 * KX + 1, MZ = KZ + 1;
   constexpr int FS = MZ + 1, RS = 6 * FS + 1;  // G: [NX rows][6 fields][FS], row stride RS
   constexpr int NQ = NX / 2, NZP = NZ + 1;      // Ph: [6][NQ][NZP], z fastest
+  static_assert(NX % 4 == 0, "row pairs (pair_row) need NX divisible by 4");
   constexpr int MXH = NX / 2, MZH = NZ / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cd* G = reinterpret_cast<cd*>(smem_raw);
@@ -190,21 +188,33 @@ __device__ __forceinline__ void xz64_body(const Xz64Args& a, int bx, int by) {
       SrcX<NX> src{in + (size_t)f * planeMm + iz, MZ, sc};
       cd y[MXH];
       half_fft_rt<NX, 1>(h, y, src);
+      // rows 2k + h in pairs (k = 2p, 2p + 1), stored as the packed z-spectrum of phase 2a:
+      // A + iB at kz (the real parts only at kz = 0) and conj(A) + i conj(B) at NZ - kz
+      cd* g = G + f * FS + iz;
 #pragma unroll
-      for (int k = 0; k < MXH; ++k) G[(2 * k + h) * RS + f * FS + iz] = y[out_pos<MXH>(k)];
+      for (int p = 0; p < MXH / 2; ++p) {
+        const cd A = y[out_pos<MXH>(2 * p)], B = y[out_pos<MXH>(2 * p + 1)];
+        cd* g1 = g + (4 * p + h) * RS;
+        if (iz == 0) {
+          g1[0] = mk(A.x, B.x);
+        } else {
+          g1[0] = mk(A.x - B.y, A.y + B.x);
+          g1[2 * RS] = mk(A.x + B.y, B.x - A.y);
+        }
+      }
     }
   }
   __syncthreads();
 
-  // phase 2a: c2r along z of row pairs (2q, 2q+1), output z-points 2k + h
+  // phase 2a: c2r along z of row pairs (pair_row(q), pair_row(q) + 2), output z-points 2k + h
   {
     constexpr int ntr = NIN * NQ, ngrp = (ntr + 31) / 32;
     for (int w2 = warp; w2 < 2 * ngrp; w2 += nwarps) {
       const int h = w2 & 1, tr = (w2 >> 1) * 32 + lane;
       if (tr >= ntr) continue;
       const int f = tr / NQ, q = tr - f * NQ;
-      const cd* g0 = G + (2 * q) * RS + f * FS;
-      SrcZ2<NZ> src{g0, g0 + RS};
+      const cd* g0 = G + pair_row(q) * RS + f * FS;
+      SrcZP<NZ> src{g0, g0 + 2 * RS};
       cd y[MZH];
       half_fft_rt<NZ, 1>(h, y, src);
       cd* dst = Ph + (f * NQ + q) * NZP;
@@ -226,6 +236,7 @@ __device__ __forceinline__ void xz64_body(const Xz64Args& a, int bx, int by) {
     }
     for (int it = threadIdx.x; it < NQ * NZ; it += blockDim.x) {
       const int q = it / NZ, k = it - q * NZ;
+      const int r0 = pair_row(q);
       cd fv[NIN];
 #pragma unroll
       for (int f = 0; f < NIN; ++f) fv[f] = Ph[(f * NQ + q) * NZP + k];
@@ -236,7 +247,7 @@ __device__ __forceinline__ void xz64_body(const Xz64Args& a, int bx, int by) {
 #pragma unroll
         for (int f = 0; f < NIN; ++f) F[f] = r ? fv[f].y : fv[f].x;
         if constexpr (MODE == XZ_TANGENT || MODE == XZ_ADJOINT) {
-          const size_t gi = (size_t)(2 * q + r) * NZ + k;
+          const size_t gi = (size_t)(r0 + 2 * r) * NZ + k;
 #pragma unroll
           for (int f = 0; f < 6; ++f) B[f] = __ldg(bj + (size_t)f * a.NY * nxz + gi);
         }
@@ -246,7 +257,7 @@ __device__ __forceinline__ void xz64_body(const Xz64Args& a, int bx, int by) {
 #pragma unroll
           for (int f = 0; f < 6; ++f) Tt[f] = F[f] + lamj[f];
           if constexpr (MODE == XZ_STEP_BASE) {
-            const size_t gi = (size_t)(2 * q + r) * NZ + k;
+            const size_t gi = (size_t)(r0 + 2 * r) * NZ + k;
 #pragma unroll
             for (int f = 0; f < 6; ++f) a.base[(size_t)f * a.NY * nxz + (size_t)j * nxz + gi] = Tt[f];
           }
@@ -280,9 +291,9 @@ __device__ __forceinline__ void xz64_body(const Xz64Args& a, int bx, int by) {
       if (tr >= ntr) continue;
       const int c = tr / NQ, q = tr - c * NQ;
       SrcDense src{Ph + (c * NQ + q) * NZP, 1};
-      cd* g0 = G + (2 * q) * RS + c * FS;
-      if (h == 0) sep_half<NZ, 0>(src, g0, g0 + RS);
-      else sep_half<NZ, 1>(src, g0, g0 + RS);
+      cd* g0 = G + pair_row(q) * RS + c * FS;
+      if (h == 0) sep_half<NZ, 0>(src, g0, g0 + 2 * RS);
+      else sep_half<NZ, 1>(src, g0, g0 + 2 * RS);
     }
   }
   __syncthreads();
