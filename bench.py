@@ -235,8 +235,9 @@ def kernel_traffic(stage, n_dir, prec, lam_adv):
 
 
 # DRAM bytes of one FP64 tangent launch of the register plane stage k_xz_reg64<48, 48> at
-# 48x65x48 with 64 directions (dram__bytes_read.sum, dram__bytes_write.sum of that launch)
-K_XZ64_DRAM_64 = (205562368, 68731392)
+# 48x65x48 with 64 directions (dram__bytes_read.sum, dram__bytes_write.sum of that launch;
+# the kernel with the packed row pairs of phase 1 and the quarter-turn twiddles)
+K_XZ64_DRAM_64 = (205629696, 68856832)
 
 
 # DRAM bytes of one mixed-precision k_solve tangent launch at 48x65x48 with 64 directions, from
