@@ -19,58 +19,113 @@ struct TrustRegion {
 
   void setup(const double* R, int ld, int k_, const double* g) {
     k = k_;
-    std::vector<double> M((size_t)k * k, 0.0), b(k, 0.0);
-    for (int i = 0; i < k; ++i)
-      for (int j = i; j < k; ++j) {
-        double acc = 0;
-        for (int l = 0; l <= i; ++l) acc += R[(size_t)i * ld + l] * R[(size_t)j * ld + l];
-        M[(size_t)i * k + j] = M[(size_t)j * k + i] = acc;
+    // M = R^T R, stored in full (row-major, symmetric), and b = R^T g. Every O(k^3) loop below is
+    // an axpy over a contiguous row (no reductions), which the compiler vectorises without
+    // reassociating sums: M accumulates the rank-one terms of the rows of R, and the product
+    // M v of the tridiagonalisation is the sum of the rows of M weighted by v.
+    std::vector<double> M((size_t)k * k, 0.0), b(k, 0.0), row(k);
+    for (int l = 0; l < k; ++l) {
+      for (int i = l; i < k; ++i) row[i] = R[(size_t)i * ld + l];  // row l of R: entries i >= l
+      for (int i = l; i < k; ++i) {
+        double* Mi = M.data() + (size_t)i * k;
+        const double ri = row[i];
+        for (int j = l; j < k; ++j) Mi[j] += ri * row[j];
       }
-    for (int j = 0; j < k; ++j) {
+    }
+    for (int i = 0; i < k; ++i) {
       double acc = 0;
-      for (int l = 0; l <= j; ++l) acc += R[(size_t)j * ld + l] * g[l];
-      b[j] = acc;
+      for (int l = 0; l <= i; ++l) acc += R[(size_t)i * ld + l] * g[l];
+      b[i] = acc;
     }
     V.assign((size_t)k * k, 0.0);
     beta.assign(k, 0.0);
-    std::vector<double> p(k), wv(k);
-    for (int col = 0; col + 2 < k; ++col) {
-      // reflector zeroing M[col+2.., col]
-      double alpha = 0;
-      for (int i = col + 1; i < k; ++i) alpha += M[(size_t)i * k + col] * M[(size_t)i * k + col];
-      alpha = std::sqrt(alpha);
-      if (alpha == 0.0) continue;
-      const double x0 = M[(size_t)(col + 1) * k + col];
-      const double s = x0 >= 0 ? -alpha : alpha;
-      double* v = V.data() + (size_t)col * k;
-      for (int i = 0; i < k; ++i) v[i] = 0.0;
-      v[col + 1] = x0 - s;
-      for (int i = col + 2; i < k; ++i) v[i] = M[(size_t)i * k + col];
-      double vv = 0;
-      for (int i = col + 1; i < k; ++i) vv += v[i] * v[i];
-      if (vv == 0.0) continue;
-      const double bt = 2.0 / vv;
-      beta[col] = bt;
-      // M <- H M H with H = I - bt v v^T (symmetric rank-2 update)
-      for (int i = col; i < k; ++i) {
-        double acc = 0;
-        for (int j = col + 1; j < k; ++j) acc += M[(size_t)i * k + j] * v[j];
-        p[i] = bt * acc;
-      }
-      double vp = 0;
-      for (int i = col + 1; i < k; ++i) vp += v[i] * p[i];
-      const double kk = 0.5 * bt * vp;
-      for (int i = col; i < k; ++i) wv[i] = p[i] - kk * (i > col ? v[i] : 0.0);
-      for (int i = col; i < k; ++i)
-        for (int j = col; j < k; ++j) {
-          const double vi = i > col ? v[i] : 0.0, vj = j > col ? v[j] : 0.0;
-          M[(size_t)i * k + j] -= vi * wv[j] + wv[i] * vj;
-        }
-    }
     d.assign(k, 0.0);
     e.assign(k, 0.0);
+    std::vector<double> p(k), wv(k);
+    // Householder reflector of step col from row col of M (= its column below the diagonal):
+    // H = I - bt v v^T, H M[col+1.., col] = s e_1; returns false when the column is already reduced
+    auto reflector = [&](int col) -> bool {
+      const int c1 = col + 1;
+      const double* x = M.data() + (size_t)col * k;
+      double alpha = 0;
+      for (int i = c1; i < k; ++i) alpha += x[i] * x[i];
+      alpha = std::sqrt(alpha);
+      const double x0 = x[c1];
+      e[col] = x0;
+      if (alpha == 0.0) return false;
+      const double s = x0 >= 0 ? -alpha : alpha;
+      double* v = V.data() + (size_t)col * k;
+      v[c1] = x0 - s;
+      for (int i = c1 + 1; i < k; ++i) v[i] = x[i];
+      double vv = 0;
+      for (int i = c1; i < k; ++i) vv += v[i] * v[i];
+      if (vv == 0.0) return false;
+      beta[col] = 2.0 / vv;
+      e[col] = s;
+      return true;
+    };
+    // p = bt A v on the trailing block A = M[c1.., c1..] of step col (rows weighted by v)
+    auto product = [&](int col) {
+      const int c1 = col + 1;
+      const double* v = V.data() + (size_t)col * k;
+      for (int j = c1; j < k; ++j) p[j] = 0.0;
+      for (int i = c1; i < k; ++i) {
+        const double* Mi = M.data() + (size_t)i * k;
+        const double vi = beta[col] * v[i];
+        for (int j = c1; j < k; ++j) p[j] += vi * Mi[j];
+      }
+    };
+    // Step col: A <- H A H = A - v w^T - w v^T with w = p - (bt v.p / 2) v. The product of the
+    // next step is accumulated in the same pass over the rows: row c1 is updated first, which
+    // gives the next reflector, and every later row, once updated, adds its share of the next p.
+    bool have = k >= 3 && reflector(0);
+    if (have) product(0);
+    for (int col = 0; col + 2 < k; ++col) {
+      const int c1 = col + 1;
+      const bool next = c1 + 2 < k;
+      if (!have) {  // nothing to apply at this step; set up the next one
+        have = next && reflector(c1);
+        if (have) product(c1);
+        continue;
+      }
+      const double* v = V.data() + (size_t)col * k;
+      const double bt = beta[col];
+      double vp = 0;
+      for (int i = c1; i < k; ++i) vp += v[i] * p[i];
+      const double kk = 0.5 * bt * vp;
+      for (int i = c1; i < k; ++i) wv[i] = p[i] - kk * v[i];
+      {
+        double* Mi = M.data() + (size_t)c1 * k;
+        const double vi = v[c1], wi = wv[c1];
+        for (int j = c1; j < k; ++j) Mi[j] -= vi * wv[j] + wi * v[j];
+      }
+      const bool have_next = next && reflector(c1);
+      const int c2 = c1 + 1;
+      if (have_next) {
+        const double* vn = V.data() + (size_t)c1 * k;
+        const double btn = beta[c1];
+        for (int j = c2; j < k; ++j) p[j] = 0.0;
+        for (int i = c2; i < k; ++i) {
+          double* Mi = M.data() + (size_t)i * k;
+          const double vi = v[i], wi = wv[i], ui = btn * vn[i];
+          Mi[c1] -= vi * wv[c1] + wi * v[c1];
+          for (int j = c2; j < k; ++j) {
+            const double m = Mi[j] - (vi * wv[j] + wi * v[j]);
+            Mi[j] = m;
+            p[j] += ui * m;
+          }
+        }
+      } else {
+        for (int i = c2; i < k; ++i) {
+          double* Mi = M.data() + (size_t)i * k;
+          const double vi = v[i], wi = wv[i];
+          for (int j = c1; j < k; ++j) Mi[j] -= vi * wv[j] + wi * v[j];
+        }
+      }
+      have = have_next;
+    }
     for (int i = 0; i < k; ++i) d[i] = M[(size_t)i * k + i];
-    for (int i = 0; i + 1 < k; ++i) e[i] = M[(size_t)(i + 1) * k + i];
+    if (k >= 2) e[k - 2] = M[(size_t)(k - 1) * k + (k - 2)];
     // c = Q^T b, Q = H_0 H_1 ... (apply H_0 first)
     c = b;
     for (int col = 0; col + 2 < k; ++col) apply(col, c);
