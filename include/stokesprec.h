@@ -172,7 +172,7 @@ sp_status sp_jvp(sp_ctx* ctx, const double* du, double* Jdu, int n_dir, void* st
 /* sp_jvp for directions in HOST memory: du and Jdu are host arrays of n_dir
  * states (page-locked memory lets the copies overlap; pageable memory works
  * but serialises them). The directions are processed in chunks of `chunk`
- * (<= 0: n_dir/8 rounded up, at most cfg.max_batch): chunk i is copied in on
+ * (<= 0: n_dir/4 rounded up, at most cfg.max_batch): chunk i is copied in on
  * an internal stream while chunk i-1 is computed on `stream` and chunk i-2 is
  * copied out on another internal stream (two device slots held by the
  * context). Asynchronous: Jdu is complete once `stream` has reached this point
