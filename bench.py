@@ -133,8 +133,10 @@ def chain(n_dir):
 
 
 def chain_record_doubles():
+    """Doubles of one mode's chain records: per parity the two sweep records (6 per unknown),
+    the influence vectors (2 per unknown) and 8 scalars."""
     nh = (NY - 1) // 2 + 1
-    return 2 * (10 * nh + 8)
+    return 2 * (14 * nh + 8)
 
 
 def kernel_bytes(stage, n_dir, esz):
