@@ -41,6 +41,16 @@ constexpr uint32_t kLboA = (kTcM / 8) * 128;
 // address stays inside this allocation for 48 <= K <= 72, even if the hardware read the two strides
 // of the descriptor the other way round (the padding covers the last tile's reach).
 constexpr uint32_t kTcPad = 26880;
+constexpr uint32_t kSbo = 128;  // stride between the 8-row core-matrix groups of a K-major tile
+
+// End (exclusive, counted from the descriptor's start address) of what one MMA with K = 8 can
+// address in a K-major operand of `rows` rows: two core matrices of 128 bytes along K and rows / 8
+// along the rows, with the two strides read as written (lbo along K, sbo along the rows) or swapped.
+__host__ __device__ constexpr uint32_t mma_reach(int rows, uint32_t lbo, uint32_t sbo) {
+  const uint32_t as_written = lbo + (uint32_t)(rows / 8 - 1) * sbo + 128;
+  const uint32_t swapped = sbo + (uint32_t)(rows / 8 - 1) * lbo + 128;
+  return as_written > swapped ? as_written : swapped;
+}
 
 struct TcArgs {
   const double2* in;     // [dir][3][Mm][NY] complex double (the state layout)
@@ -114,6 +124,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_yinv_tc(TcArgs a) {
   const int NY = a.NY;
   constexpr uint32_t abytes = (uint32_t)kTcM * KP * 4;   // one A matrix
   constexpr uint32_t bbytes = (uint32_t)(KP / 4) * kLboB;  // one B matrix
+  // the last MMA on the last A matrix and on the second B matrix stays inside the allocation
+  static_assert(3 * abytes + (KP / 8 - 1) * 2 * kLboA + mma_reach(kTcM, kLboA, kSbo) <= 4 * abytes + kTcPad,
+                "an MMA on T'_lo could address past the shared-memory allocation");
+  static_assert(bbytes + (KP / 8 - 1) * 2 * kLboB + mma_reach(kTcCols, kLboB, kSbo) <= 2 * bbytes + 4 * abytes + kTcPad,
+                "an MMA on B_lo could address past the shared-memory allocation");
   unsigned char* sB = smem;                  // B_hi, B_lo
   unsigned char* sA = smem + 2 * bbytes;     // T_hi, T_lo, T'_hi, T'_lo, then kTcPad bytes
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -145,7 +160,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_yinv_tc(TcArgs a) {
   }
   ok = mbar_wait(ub_load, 0);
 
-  constexpr uint32_t sbo = 128;
+  constexpr uint32_t sbo = kSbo;
   constexpr uint32_t id_v = idesc_tf32(kTcM, kTcCols), id_d = idesc_tf32(kTcM, 64);
   const size_t planeMm = (size_t)NY * a.Mm;
   uint32_t phase = 0;
@@ -344,6 +359,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rhs_tc(RhsTcArgs a) {
   const int NY = a.NY;
   constexpr uint32_t abytes = (uint32_t)kTcM * KP * 4;     // one A matrix
   constexpr uint32_t bbytes = (uint32_t)(KP / 4) * kLboB;  // one B matrix
+  static_assert(abytes + (KP / 8 - 1) * 2 * kLboA + mma_reach(kTcM, kLboA, kSbo) <= 2 * abytes + kTcPad,
+                "an MMA on C_lo could address past the shared-memory allocation");
+  static_assert(bbytes + (KP / 8 - 1) * 2 * kLboB + mma_reach(kTcCols, kLboB, kSbo) <= 2 * bbytes + 2 * abytes + kTcPad,
+                "an MMA on B_lo could address past the shared-memory allocation");
   constexpr int kCols = 128;                               // tensor-memory columns (96 used)
   unsigned char* sB = smem;                  // B_hi, B_lo
   unsigned char* sA = smem + 2 * bbytes;     // C_hi, C_lo, then kTcPad bytes
@@ -372,7 +391,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rhs_tc(RhsTcArgs a) {
                  : "memory");
   }
   ok = mbar_wait(ub_load, 0);
-  constexpr uint32_t sbo = 128;
+  constexpr uint32_t sbo = kSbo;
   constexpr uint32_t id_w = idesc_tf32(kTcM, kTcCols);
   uint32_t phase = 0;
   // A tile is 4 unique modes x 4 directions. B columns: c 32 + 2 (4 dl + ml) + re/im for field c,
